@@ -1,0 +1,409 @@
+#!/usr/bin/env python3
+"""Benchmark of the ACA minimal-solver hot path on GB300.
+
+Headline (one JSON line on rank 0): batched ACA minimal solve over 2^26
+synthetic minimal sets (16 float32 in, 9 out per set), H/s, with inputs
+resident in HBM; a step is one aca_solve over the whole batch.  The same line
+carries the roofline of that kernel, the FP64 oracle timed on the host cores,
+an end-to-end number through the C ABI with host buffers, the SM clocks seen
+during the measurement, and the other rows of the hot path measured in the
+same run: SKS on the same sets, fused RANSAC on one image pair (N = 2000,
+4096 hypotheses), batched uneven RANSAC (512 pairs) against 512 separate
+per-problem launches, and the differentiable rectangle ACA (forward +
+backward, batch 65536) against the plain solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank solving its own 2^26
+sets (weak scaling, no collective on the data path).  --impl reference times
+the FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+N_LOG2 = 26
+BYTES_PER_SET = 64 + 36          # 16 float32 in, 9 float32 out
+FLOPS_PER_TEST = 21              # one hypothesis x point test, FMA = 2
+RANSAC_THR = 3.0
+SEED = 0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-log2", type=int, default=N_LOG2)
+    ap.add_argument("--no-rows", action="store_true", help="headline only")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured", sm_max_mhz=float(d.get("sm_max_mhz", 2070)))
+    except Exception:
+        return dict(hbm_gbs=6800.0, source="fallback", sm_max_mhz=2070.0)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling (200 ms) around a measured region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        load = [r for r in rows if (num(r[4]) or 0) > 0] or rows
+        sm = [num(r[1]) for r in load if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i in range(4) if r[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(load[0][2]),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load),
+                "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+def sync_all(torch, dist_on):
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def time_region(torch, fn, steps, stream):
+    """Average ms per call of fn over `steps` calls, CUDA events on `stream`."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_baseline_aca(pts16, seconds):
+    """The FP64 oracle's ACA over chunks of the same sets on the host cores."""
+    import oracle
+    n = pts16.shape[1]
+    chunk = min(n, 1 << 21)
+    done, t0, k = 0, time.perf_counter(), 0
+    aos = oracle.sets_aos(pts16[:, :chunk])
+    while True:
+        t = time.perf_counter()
+        oracle.lib().oracle_aca(aos.ctypes.data_as(oracle._d), np.empty((chunk, 9)).ctypes.data_as(oracle._d), chunk)
+        done += chunk
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "H/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{k} passes of the FP64 C oracle (OpenMP) over the first {chunk} of the 2^{int(np.log2(n))} "
+                      f"sets ({el:.1f} s)"}
+
+
+def error_stats(H_planes_np, flags_np, pts16, n, rng):
+    import oracle
+    idx = np.sort(rng.choice(n, size=min(n, 1 << 16), replace=False))
+    ref = oracle.aca(pts16[:, idx])
+    a = H_planes_np[:, idx].T.astype(np.float64)
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    b = ref / np.linalg.norm(ref, axis=1, keepdims=True)
+    a *= np.sign(np.sum(a * b, axis=1, keepdims=True))
+    e = np.abs(a - b).max(axis=1)
+    flagged = (flags_np[idx] & 7) > 0
+    ok = ~flagged
+    return {"sample_sets": int(idx.size), "max_err": float(e[ok].max()), "median_err": float(np.median(e[ok])),
+            "frac_above_1e-4": float(np.mean(e[ok] > 1e-4)), "flagged_sets": int(flagged.sum()),
+            "flagged_max_err": float(e[flagged].max()) if flagged.any() else None,
+            "metric": "max |H_gpu - H_fp64| with both at unit Frobenius norm, sign aligned; "
+                      "flagged = a triple within 1 px of collinear (excluded from max_err)"}
+
+
+def run_reference(args, rank):
+    """The FP64 CPU oracle on the host cores, same metric and workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = 1 << args.n_log2
+    sample = 1 << 20
+    ms = workloads.minimal_sets(sample, seed=SEED, degenerate_frac=0.01, keep_truth=False, workers=os.cpu_count())
+    aos = oracle.sets_aos(ms.pts)
+    out = np.empty((sample, 9))
+    run = lambda: oracle.lib().oracle_aca(aos.ctypes.data_as(oracle._d), out.ctypes.data_as(oracle._d), sample)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    el = time.perf_counter() - t0
+    v = sample * args.steps / el
+    line = {"metric": "ACA minimal solves per second (config 1: 2^26 sets, FP32 SoA 16 in / 9 out)", "value": v,
+            "unit": "H/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"aca_solve, 2^{args.n_log2} minimal sets (a {sample}-set sample per step)",
+                       "sets": n, "sample_sets_per_step": sample},
+            "cpu_baseline": {"value": v, "unit": "H/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"the first {sample} sets of the workload per step"},
+            "e2e": {"value": v, "unit": "H/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    n = 1 << args.n_log2
+    # host-side generation first (process pool before any CUDA call)
+    ms = workloads.minimal_sets(n, seed=SEED + rank, degenerate_frac=0.01, keep_truth=False,
+                                workers=max(1, os.cpu_count() or 1))
+    rows_on = not args.no_rows and world == 1
+    if rows_on:
+        rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=SEED)
+        rb = workloads.ransac_batch(512, seed=SEED)
+        rect = workloads.rect_batch(65536, seed=SEED)
+
+    import torch
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2402_18008_gb300 import _lib, api
+    _lib.load()
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    pts = torch.from_numpy(ms.pts).to(dev)
+    H = torch.empty((9, n), dtype=torch.float32, device=dev)
+    flags = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    solve = lambda: _lib.aca_solve(pts, H, None, n=n)
+    res = {}
+    with ClockSampler(local) as clocks:
+        for _ in range(args.warmup):
+            solve()
+        sync_all(torch, dist_on)
+        ms_step = time_region(torch, solve, args.steps, stream)
+        sync_all(torch, dist_on)
+        if dist_on:
+            t = torch.tensor([ms_step], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_step = float(t.item())
+        # errors vs the FP64 oracle on a sample (flags from a flags-on solve)
+        _lib.aca_solve(pts, H, flags, n=n)
+        torch.cuda.synchronize()
+        if rank == 0:
+            res["err"] = error_stats(H.cpu().numpy(), flags.cpu().numpy(), ms.pts, n, np.random.default_rng(1))
+        if rows_on:
+            res.update(run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev))
+    clk = clocks.summary()
+    if rank != 0:
+        if dist_on:
+            dist.destroy_process_group()
+        return
+
+    # end to end through the C ABI with host buffers: H2D of the sets, the
+    # solve, D2H of the homographies, every step
+    e2e_steps = max(3, min(args.steps, 10))
+    pts_h = torch.from_numpy(ms.pts).pin_memory()
+    H_h = torch.empty((9, n), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        pts.copy_(pts_h, non_blocking=True)
+        _lib.aca_solve(pts, H, None, n=n)
+        H_h.copy_(H, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = time_region(torch, e2e_step, e2e_steps, stream)
+
+    cpu = cpu_baseline_aca(ms.pts, args.cpu_seconds)
+    value = n * world / (ms_step * 1e-3)
+    achieved = BYTES_PER_SET * n / (ms_step * 1e-3) / 1e9
+    line = {
+        "metric": "ACA minimal solves per second (config 1: 2^26 sets, FP32 SoA 16 in / 9 out)",
+        "value": value, "unit": "H/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"aca_solve over 2^{args.n_log2} minimal sets per GPU (1% near-degenerate)",
+                   "sets_per_gpu": n, "bytes_per_set": BYTES_PER_SET, "norm": "none",
+                   "l2": "inputs (4 GiB) larger than L2, no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peaks["source"], "kernel": "solve_vec4_kernel<ACA, NONE, no flags>",
+                     "algorithmic_bytes_per_launch": BYTES_PER_SET * n},
+        "cpu_baseline": cpu,
+        "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "H/s", "h2d_bytes_per_step": 64 * n,
+                "d2h_bytes_per_step": 36 * n, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "max_err_vs_fp64": res.get("err"),
+        "sms": sms,
+    }
+    if rows_on:
+        line["rows"] = {k: v for k, v in res.items() if k != "err"}
+    print(json.dumps(line), flush=True)
+    if dist_on:
+        dist.destroy_process_group()
+
+
+def fp32_peak_tflops(sms, mhz):
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev):
+    out = {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps = max(20, args.steps // 4)
+    # SKS on the same sets
+    sks = lambda: _lib.sks_solve(pts, H, None, n=n)
+    for _ in range(3):
+        sks()
+    t = time_region(torch, sks, reps, stream)
+    out["sks_solve"] = {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
+                        "achieved_gbs": BYTES_PER_SET * n / (t * 1e-3) / 1e9}
+    fl = lambda: _lib.aca_solve(pts, H, flags, n=n)
+    for _ in range(3):
+        fl()
+    t = time_region(torch, fl, reps, stream)
+    out["aca_solve_with_flags"] = {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
+                                   "achieved_gbs": (BYTES_PER_SET + 1) * n / (t * 1e-3) / 1e9}
+
+    # fused RANSAC, one pair (config 2), graph-replayed
+    corr = torch.from_numpy(rp.corr).to(dev)
+    plan2 = api.RansacPlan(corr, torch.tensor([0, 2000], dtype=torch.int64, device=dev),
+                           torch.tensor([4096], dtype=torch.int32, device=dev), RANSAC_THR, SEED, 4096,
+                           tile_points=256, hyps_per_thread=1, block_warps=4).capture()
+    for _ in range(5):
+        plan2.replay()
+    t = time_region(torch, plan2.replay, 200, stream)
+    tests = 4096 * 2000
+    out["ransac_fused_one_pair"] = {"value": tests / (t * 1e-3), "unit": "hyp*pts/s", "ms_per_ransac": t,
+                                    "tflops_fp32": tests * FLOPS_PER_TEST / (t * 1e-3) / 1e12,
+                                    "config": "N=2000, 60% inliers, 4096 hypotheses, thr 3 px, graph replay"}
+
+    # batched uneven RANSAC (config 3) vs 512 separate per-problem launches
+    tot = int(rb.n_hyp.sum())
+    Ns = rb.offsets[1:] - rb.offsets[:-1]
+    tests3 = float(np.sum(rb.n_hyp.astype(np.float64) * Ns))
+    corr3 = torch.from_numpy(rb.corr).to(dev)
+    off3 = torch.from_numpy(rb.offsets).to(dev)
+    k3 = torch.from_numpy(rb.n_hyp).to(dev)
+    plan3 = api.RansacPlan(corr3, off3, k3, RANSAC_THR, SEED, tot).capture()
+    for _ in range(3):
+        plan3.replay()
+    t3 = time_region(torch, plan3.replay, 20, stream)
+    plains = []
+    for p in range(len(rb.n_hyp)):
+        a, b = int(rb.offsets[p]), int(rb.offsets[p + 1])
+        plains.append(api.RansacPlan(corr3[a:b], torch.tensor([0, b - a], dtype=torch.int64, device=dev),
+                                     k3[p:p + 1], RANSAC_THR, SEED, int(rb.n_hyp[p]), problem_base=p))
+
+    def run_plain():
+        for pl in plains:
+            pl.run()
+    run_plain()
+    tp = time_region(torch, run_plain, 3, stream)
+    # check: batched == plain (best hypothesis per problem)
+    same = all(int(pl.best_hyp.item()) == int(plan3.best_hyp[p].item()) for p, pl in enumerate(plains))
+    out["ransac_batched_512"] = {"value": tests3 / (t3 * 1e-3), "unit": "hyp*pts/s", "ms_batched": t3,
+                                 "ms_512_plain_launches": tp, "speedup_vs_plain": tp / t3,
+                                 "tflops_fp32": tests3 * FLOPS_PER_TEST / (t3 * 1e-3) / 1e12,
+                                 "tests": tests3, "hypotheses": tot, "points": int(rb.offsets[-1]),
+                                 "batched_equals_plain": same,
+                                 "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9], "
+                                           "adaptive hypotheses (99%, cap 16384), one graph replay"}
+
+    # differentiable rectangle ACA (config 4): forward + backward vs plain solve
+    B = rect.tgt.shape[1]
+    tgt = torch.from_numpy(rect.tgt).to(dev)
+    Hr = torch.empty((9, B), dtype=torch.float32, device=dev)
+    gH = torch.randn((9, B), dtype=torch.float32, device=dev)
+    gT = torch.empty((8, B), dtype=torch.float32, device=dev)
+
+    def fwd_bwd():
+        _lib.aca_rect_solve(tgt, rect.rect, Hr)
+        _lib.aca_rect_backward(tgt, rect.rect, gH, gT)
+    src = np.repeat(rect.src_corners.reshape(8, 1), B, axis=1).astype(np.float32)
+    pts4 = torch.from_numpy(np.concatenate([src, rect.tgt], axis=0)).to(dev)
+    Hg = torch.empty((9, B), dtype=torch.float32, device=dev)
+    plain = lambda: _lib.aca_solve(pts4, Hg, None, n=B)
+    for f in (fwd_bwd, plain):
+        for _ in range(5):
+            f()
+    tfb = time_region(torch, fwd_bwd, 200, stream)
+    tpl = time_region(torch, plain, 200, stream)
+    out["diff_aca_rect_65536"] = {"value": B / (tfb * 1e-3), "unit": "sets/s (fwd+bwd)", "ms_fwd_bwd": tfb,
+                                  "ms_plain_aca_solve": tpl, "ratio_vs_plain": tfb / tpl}
+    return out
+
+
+if __name__ == "__main__":
+    main()

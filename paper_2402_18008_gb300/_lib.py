@@ -1,0 +1,210 @@
+"""ctypes binding of the C ABI in include/aca.h (argument marshalling only).
+
+Every function here takes torch CUDA tensors, checks dtype / device / shape,
+and passes raw device pointers plus the current CUDA stream to the library;
+all computation happens in the CUDA kernels.  There is no CPU fallback: if
+the shared library is missing or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+ACA_NORM_NONE, ACA_NORM_H33, ACA_NORM_FROB = 0, 1, 2
+ACA_FLAG_SRC_ANCHORS, ACA_FLAG_TGT_ANCHORS, ACA_FLAG_OTHER_TRIPLE, ACA_FLAG_NON_FINITE = 1, 2, 4, 8
+_STATUS = {0: "ACA_OK", -1: "ACA_ERR_INVALID_ARG", -2: "ACA_ERR_CUDA", -3: "ACA_ERR_WORKSPACE", -4: "ACA_ERR_TIMEOUT"}
+
+EXPORTED = ("aca_solve", "sks_solve", "aca_rect_solve", "aca_backward", "aca_rect_backward",
+            "ransac_aca_workspace_size", "ransac_aca", "aca_sample_indices", "aca_last_error", "aca_version")
+
+
+class AcaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class RansacParams(ctypes.Structure):
+    _fields_ = [("threshold_px", ctypes.c_float), ("problem_base", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("block_warps", ctypes.c_int32), ("hyps_per_thread", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("tile_points", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the shared library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise OSError(f"CUDA library not built: {path}")
+            _build.build()
+        L = ctypes.CDLL(path)
+        vp, i64, i32, f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+        for name in ("aca_solve", "sks_solve"):
+            getattr(L, name).argtypes = [vp, vp, vp, i64, i64, i32, vp]
+        L.aca_rect_solve.argtypes = [vp, f32, f32, f32, f32, vp, i64, i64, vp]
+        L.aca_backward.argtypes = [vp, vp, vp, i64, i64, vp]
+        L.aca_rect_backward.argtypes = [vp, f32, f32, f32, f32, vp, vp, i64, i64, vp]
+        L.ransac_aca_workspace_size.argtypes = [i32, i64]
+        L.ransac_aca_workspace_size.restype = ctypes.c_size_t
+        L.ransac_aca.argtypes = [vp, vp, vp, i32, ctypes.POINTER(RansacParams), vp, vp, vp, vp, vp, vp,
+                                 ctypes.c_size_t, vp]
+        L.aca_sample_indices.argtypes = [i64, i32, ctypes.c_uint64, ctypes.c_uint32, vp, vp]
+        for name in EXPORTED:
+            if name not in ("ransac_aca_workspace_size", "aca_last_error", "aca_version"):
+                getattr(L, name).restype = ctypes.c_int
+        L.aca_last_error.restype = ctypes.c_char_p
+        L.aca_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(st: int):
+    if st != 0:
+        raise AcaError(st, load().aca_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, name, dtype, rows=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if rows is not None:
+        if t.dim() != 2 or t.shape[0] != rows or t.stride(1) != 1:
+            raise ValueError(f"{name} must be ({rows}, ld) with unit stride along ld")
+
+
+def _ld(*ts):
+    lds = {t.stride(0) for t in ts if t is not None}
+    if len(lds) != 1:
+        raise ValueError("all planes must share one leading dimension (row stride)")
+    ld = lds.pop()
+    for t in ts:
+        if t is not None and t.shape[1] > ld:
+            raise ValueError("row length exceeds the leading dimension")
+    return ld
+
+
+def aca_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
+    """C ABI aca_solve on (16, ld) float32 planes -> (9, ld) float32."""
+    _need(pts, "pts", torch.float32, 16)
+    _need(H, "H", torch.float32, 9)
+    if flags is not None:
+        _need(flags, "flags", torch.uint8)
+    ld = _ld(pts, H)
+    n = pts.shape[1] if n is None else n
+    _check(load().aca_solve(_ptr(pts), _ptr(H), _ptr(flags), n, ld, norm, ctypes.c_void_p(_stream(stream))))
+
+
+def sks_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
+    """C ABI sks_solve on (16, ld) float32 planes -> (9, ld) float32."""
+    _need(pts, "pts", torch.float32, 16)
+    _need(H, "H", torch.float32, 9)
+    if flags is not None:
+        _need(flags, "flags", torch.uint8)
+    ld = _ld(pts, H)
+    n = pts.shape[1] if n is None else n
+    _check(load().sks_solve(_ptr(pts), _ptr(H), _ptr(flags), n, ld, norm, ctypes.c_void_p(_stream(stream))))
+
+
+def aca_rect_solve(tgt, rect, H, n=None, stream=None):
+    """C ABI aca_rect_solve: rect = (x0, y0, w, r)."""
+    _need(tgt, "tgt", torch.float32, 8)
+    _need(H, "H", torch.float32, 9)
+    ld = _ld(tgt, H)
+    n = tgt.shape[1] if n is None else n
+    x0, y0, w, r = (float(v) for v in rect)
+    _check(load().aca_rect_solve(_ptr(tgt), x0, y0, w, r, _ptr(H), n, ld, ctypes.c_void_p(_stream(stream))))
+
+
+def aca_backward(pts, grad_H, grad_tgt, n=None, stream=None):
+    """C ABI aca_backward: (16, ld) sets, (9, ld) dL/dH -> (8, ld) dL/dtgt."""
+    _need(pts, "pts", torch.float32, 16)
+    _need(grad_H, "grad_H", torch.float32, 9)
+    _need(grad_tgt, "grad_tgt", torch.float32, 8)
+    ld = _ld(pts, grad_H, grad_tgt)
+    n = pts.shape[1] if n is None else n
+    _check(load().aca_backward(_ptr(pts), _ptr(grad_H), _ptr(grad_tgt), n, ld, ctypes.c_void_p(_stream(stream))))
+
+
+def aca_rect_backward(tgt, rect, grad_H, grad_tgt, n=None, stream=None):
+    """C ABI aca_rect_backward."""
+    _need(tgt, "tgt", torch.float32, 8)
+    _need(grad_H, "grad_H", torch.float32, 9)
+    _need(grad_tgt, "grad_tgt", torch.float32, 8)
+    ld = _ld(tgt, grad_H, grad_tgt)
+    n = tgt.shape[1] if n is None else n
+    x0, y0, w, r = (float(v) for v in rect)
+    _check(load().aca_rect_backward(_ptr(tgt), x0, y0, w, r, _ptr(grad_H), _ptr(grad_tgt), n, ld,
+                                    ctypes.c_void_p(_stream(stream))))
+
+
+def ransac_aca_workspace_size(P: int, total_hyps: int) -> int:
+    return int(load().ransac_aca_workspace_size(P, total_hyps))
+
+
+def ransac_aca(corr, offsets, n_hyp, params: RansacParams, best_H, best_count, best_hyp, workspace,
+               hyp_counts=None, inlier_mask=None, stream=None):
+    """C ABI ransac_aca.  corr (total, 4) float32; offsets (P+1,) int64;
+    n_hyp (P,) int32; outputs best_H (P, 9) float32, best_count / best_hyp
+    (P,) int32; workspace uint8 of ransac_aca_workspace_size bytes."""
+    _need(corr, "corr", torch.float32)
+    _need(offsets, "offsets", torch.int64)
+    _need(n_hyp, "n_hyp", torch.int32)
+    _need(best_H, "best_H", torch.float32)
+    _need(best_count, "best_count", torch.int32)
+    _need(best_hyp, "best_hyp", torch.int32)
+    _need(workspace, "workspace", torch.uint8)
+    if corr.dim() != 2 or corr.shape[1] != 4 or not corr.is_contiguous():
+        raise ValueError("corr must be a contiguous (total, 4) tensor")
+    P = n_hyp.numel()
+    if offsets.numel() != P + 1:
+        raise ValueError("offsets must have P+1 entries")
+    for t, nm in ((offsets, "offsets"), (n_hyp, "n_hyp"), (best_H, "best_H"), (best_count, "best_count"),
+                  (best_hyp, "best_hyp")):
+        if not t.is_contiguous():
+            raise ValueError(f"{nm} must be contiguous")
+    if best_H.numel() < 9 * P or best_count.numel() < P or best_hyp.numel() < P:
+        raise ValueError("output tensors too small")
+    if hyp_counts is not None:
+        _need(hyp_counts, "hyp_counts", torch.int32)
+    if inlier_mask is not None:
+        _need(inlier_mask, "inlier_mask", torch.uint8)
+        if inlier_mask.numel() < corr.shape[0]:
+            raise ValueError("inlier_mask too small")
+    _check(load().ransac_aca(_ptr(corr), _ptr(offsets), _ptr(n_hyp), P, ctypes.byref(params), _ptr(best_H),
+                             _ptr(best_count), _ptr(best_hyp), _ptr(hyp_counts), _ptr(inlier_mask),
+                             _ptr(workspace), workspace.numel(), ctypes.c_void_p(_stream(stream))))
+
+
+def aca_sample_indices(N: int, n_hyp: int, seed: int, problem: int, idx, stream=None):
+    """C ABI aca_sample_indices into idx (n_hyp, 4) int32."""
+    _need(idx, "idx", torch.int32)
+    if not idx.is_contiguous() or idx.numel() < 4 * n_hyp:
+        raise ValueError("idx must be a contiguous (n_hyp, 4) int32 tensor")
+    _check(load().aca_sample_indices(int(N), int(n_hyp), int(seed), int(problem), _ptr(idx),
+                                     ctypes.c_void_p(_stream(stream))))

@@ -1,0 +1,132 @@
+"""Convenience layer over the C ABI: allocates outputs and workspaces with
+torch, keeps RANSAC launch plans and CUDA graphs.  No arithmetic of the
+method runs here; every step is a kernel of the CUDA library.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import ACA_NORM_FROB, ACA_NORM_H33, ACA_NORM_NONE, RansacParams
+
+_SOLVERS = {"aca": _lib.aca_solve, "sks": _lib.sks_solve}
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device (the library has no CPU path)")
+
+
+def solve(pts: torch.Tensor, norm: int = ACA_NORM_NONE, solver: str = "aca", with_flags: bool = False,
+          n: int | None = None, out: torch.Tensor | None = None, flags_out: torch.Tensor | None = None):
+    """Batched minimal solve.  pts: (16, ld) float32 CUDA planes.  Returns H
+    (9, ld) and, if requested, per-set flags (ld,) uint8."""
+    _require_cuda(pts, "pts")
+    ld = pts.stride(0)
+    H = out if out is not None else torch.empty((9, ld), dtype=torch.float32, device=pts.device)
+    fl = None
+    if with_flags:
+        fl = flags_out if flags_out is not None else torch.empty(ld, dtype=torch.uint8, device=pts.device)
+    _SOLVERS[solver](pts, H, fl, n=pts.shape[1] if n is None else n, norm=norm)
+    return (H, fl) if with_flags else H
+
+
+def rect_solve(tgt: torch.Tensor, rect, out: torch.Tensor | None = None):
+    """Rectangle-source ACA (Eq. 42).  tgt: (8, ld) float32; rect = (x0, y0, w, r)."""
+    _require_cuda(tgt, "tgt")
+    H = out if out is not None else torch.empty((9, tgt.stride(0)), dtype=torch.float32, device=tgt.device)
+    _lib.aca_rect_solve(tgt, rect, H)
+    return H
+
+
+def to_planes(src: torch.Tensor, tgt: torch.Tensor, ld: int | None = None) -> torch.Tensor:
+    """(B, 4, 2) source and target corners (M, N, P, Q order) -> (16, ld) planes."""
+    B = src.shape[0]
+    ld = B if ld is None else ld
+    pts = torch.zeros((16, ld), dtype=torch.float32, device=src.device)
+    pts[:8, :B] = src.reshape(B, 8).t()
+    pts[8:, :B] = tgt.reshape(B, 8).t()
+    return pts
+
+
+def planes_to_mats(H: torch.Tensor, n: int) -> torch.Tensor:
+    """(9, ld) planes -> (n, 3, 3)."""
+    return H[:, :n].t().reshape(n, 3, 3)
+
+
+@dataclass
+class RansacResult:
+    best_H: torch.Tensor      # (P, 9) float32, unit Frobenius, sign fixed
+    best_count: torch.Tensor  # (P,) int32
+    best_hyp: torch.Tensor    # (P,) int32
+    hyp_counts: torch.Tensor | None
+    inlier_mask: torch.Tensor | None
+
+
+class RansacPlan:
+    """Buffers and launch parameters for repeated ransac_aca calls on one
+    batch layout (P problems, total_hyps hypotheses, total points).
+
+    ``run()`` enqueues one full RANSAC (prep, scoring, argmax) on the current
+    stream; ``capture()`` records it into a CUDA graph and ``replay()``
+    launches that graph.
+    """
+
+    def __init__(self, corr: torch.Tensor, offsets: torch.Tensor, n_hyp: torch.Tensor, threshold_px: float,
+                 seed: int, total_hyps: int, problem_base: int = 0, block_warps: int = 0,
+                 hyps_per_thread: int = 0, tile_points: int = 0, grid_blocks: int = 0,
+                 want_counts: bool = False, want_mask: bool = False):
+        _require_cuda(corr, "corr")
+        dev = corr.device
+        self.corr, self.offsets, self.n_hyp = corr, offsets, n_hyp
+        self.P = n_hyp.numel()
+        self.params = RansacParams(threshold_px=float(threshold_px), problem_base=int(problem_base),
+                                   seed=int(seed), block_warps=int(block_warps),
+                                   hyps_per_thread=int(hyps_per_thread), grid_blocks=int(grid_blocks),
+                                   tile_points=int(tile_points))
+        ws = _lib.ransac_aca_workspace_size(self.P, int(total_hyps))
+        self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+        self.best_H = torch.empty((self.P, 9), dtype=torch.float32, device=dev)
+        self.best_count = torch.empty(self.P, dtype=torch.int32, device=dev)
+        self.best_hyp = torch.empty(self.P, dtype=torch.int32, device=dev)
+        self.hyp_counts = torch.empty(max(int(total_hyps), 1), dtype=torch.int32, device=dev) if want_counts else None
+        self.inlier_mask = torch.empty(max(corr.shape[0], 1), dtype=torch.uint8, device=dev) if want_mask else None
+        self.graph = None
+
+    def run(self) -> RansacResult:
+        _lib.ransac_aca(self.corr, self.offsets, self.n_hyp, self.params, self.best_H, self.best_count,
+                        self.best_hyp, self.workspace, hyp_counts=self.hyp_counts, inlier_mask=self.inlier_mask)
+        return self.result()
+
+    def capture(self, warmup: int = 1) -> "RansacPlan":
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return self
+
+    def replay(self) -> RansacResult:
+        self.graph.replay()
+        return self.result()
+
+    def result(self) -> RansacResult:
+        return RansacResult(self.best_H, self.best_count, self.best_hyp, self.hyp_counts, self.inlier_mask)
+
+
+def ransac(corr: torch.Tensor, offsets: torch.Tensor, n_hyp: torch.Tensor, threshold_px: float, seed: int,
+           total_hyps: int | None = None, want_counts: bool = False, want_mask: bool = False,
+           **tuning) -> RansacResult:
+    """One-shot RANSAC over CSR problems (see include/aca.h, ransac_aca)."""
+    if total_hyps is None:
+        total_hyps = int(n_hyp.sum().item())
+    plan = RansacPlan(corr, offsets, n_hyp, threshold_px, seed, total_hyps, want_counts=want_counts,
+                      want_mask=want_mask, **tuning)
+    return plan.run()

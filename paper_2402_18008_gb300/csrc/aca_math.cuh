@@ -1,0 +1,353 @@
+// FP32 minimal-solver arithmetic shared by the CUDA kernels of this library.
+//
+// ACA (Affine-Core-Affine, Sec. 4 of arXiv 2402.18008, Eq. 20-29) and SKS
+// (Similarity-Kernel-Similarity, Sec. 3, Eq. 4-14) for one set of four
+// correspondences M, N, P, Q (source side 1, target side 2), plus the
+// rectangle-source form of Sec. 5.3 (Eq. 39-42).
+//
+// Numerical formulation (same H as the paper's, up to rounding):
+//  * everything is computed in local frames anchored at M1 / M2 (ACA) or at
+//    the midpoints O1 / O2 (SKS) and translated back at the end, i.e.
+//    H = T(M2) * H_local * T(-M1); this is Eq. 24 regrouped by associativity;
+//  * every 2x2 cross product uses Kahan's FMA determinant (fp32.cuh);
+//  * t1 = f_A1 - Q3.x - Q3.y (Eq. 27) is evaluated as cross(N1P1, N1Q1), its
+//    exact value (twice the signed area of N1 P1 Q1), so the sum does not
+//    cancel; likewise t2;
+//  * the core product (Eq. 28) is grouped so that each entry is one Kahan
+//    determinant (plus one FMA for the third row).
+// Unnormalised output (ACA_NORM_NONE) is the paper's division-free H of
+// Eq. 24 with the scale of Eq. 28-29, the function the backward kernels
+// differentiate.
+#pragma once
+#include <stdint.h>
+
+#include "fp32.cuh"
+
+namespace aca {
+
+struct Set {
+    float M1x, M1y, N1x, N1y, P1x, P1y, Q1x, Q1y;
+    float M2x, M2y, N2x, N2y, P2x, P2y, Q2x, Q2y;
+};
+
+// Per-set flag bits (see include/aca.h).
+enum : uint8_t {
+    kFlagSrcAnchors = 1,   // source anchor triple M1 N1 P1 within 1 px of collinear
+    kFlagTgtAnchors = 2,   // target anchor triple M2 N2 P2 within 1 px of collinear
+    kFlagOtherTriple = 4,  // a triple containing Q within 1 px of collinear (either side)
+    kFlagNonFinite = 8,    // a non-finite input or output
+};
+
+// Intermediates of the ACA chain kept for the flags and the backward pass.
+struct AcaParts {
+    float MN1x, MN1y, MP1x, MP1y, NP1x, NP1y;
+    float MN2x, MN2y, MP2x, MP2y, MQ2x, MQ2y, NP2x, NP2y, NQ2x, NQ2y;
+    float fA1, fA2, Q3x, Q3y, Q4x, Q4y, t1, t2;
+    float MQ1x, MQ1y, NQ1x, NQ1y;
+};
+
+// Eq. 20-27 (vectors, f_A, Q3, Q4, t1, t2) for one set.  Edge vectors are
+// exact differences (value + remainder) and every cross product takes the
+// remainders into account (cross2x), so f_A, Q3, Q4, t1, t2 are accurate to
+// about one rounding of their exact values for the given inputs.
+ACA_HD void aca_parts(const Set &s, AcaParts &p)
+{
+    const Diff mn1x = diff(s.N1x, s.M1x), mn1y = diff(s.N1y, s.M1y);
+    const Diff mp1x = diff(s.P1x, s.M1x), mp1y = diff(s.P1y, s.M1y);
+    const Diff mq1x = diff(s.Q1x, s.M1x), mq1y = diff(s.Q1y, s.M1y);
+    const Diff np1x = diff(s.P1x, s.N1x), np1y = diff(s.P1y, s.N1y);
+    const Diff nq1x = diff(s.Q1x, s.N1x), nq1y = diff(s.Q1y, s.N1y);
+    const Diff mn2x = diff(s.N2x, s.M2x), mn2y = diff(s.N2y, s.M2y);
+    const Diff mp2x = diff(s.P2x, s.M2x), mp2y = diff(s.P2y, s.M2y);
+    const Diff mq2x = diff(s.Q2x, s.M2x), mq2y = diff(s.Q2y, s.M2y);
+    const Diff np2x = diff(s.P2x, s.N2x), np2y = diff(s.P2y, s.N2y);
+    const Diff nq2x = diff(s.Q2x, s.N2x), nq2y = diff(s.Q2y, s.N2y);
+    p.MN1x = mn1x.h; p.MN1y = mn1y.h; p.MP1x = mp1x.h; p.MP1y = mp1y.h;
+    p.MQ1x = mq1x.h; p.MQ1y = mq1y.h; p.NP1x = np1x.h; p.NP1y = np1y.h;
+    p.NQ1x = nq1x.h; p.NQ1y = nq1y.h;
+    p.MN2x = mn2x.h; p.MN2y = mn2y.h; p.MP2x = mp2x.h; p.MP2y = mp2y.h;
+    p.MQ2x = mq2x.h; p.MQ2y = mq2y.h; p.NP2x = np2x.h; p.NP2y = np2y.h;
+    p.NQ2x = nq2x.h; p.NQ2y = nq2y.h;
+    p.fA1 = cross2x(mn1x, mn1y, mp1x, mp1y);   // Eq. 21
+    p.fA2 = cross2x(mn2x, mn2y, mp2x, mp2y);
+    p.Q3x = cross2x(mq1x, mq1y, mp1x, mp1y);   // Eq. 25
+    p.Q3y = cross2x(mn1x, mn1y, mq1x, mq1y);
+    p.Q4x = cross2x(mq2x, mq2y, mp2x, mp2y);
+    p.Q4y = cross2x(mn2x, mn2y, mq2x, mq2y);
+    p.t1 = cross2x(np1x, np1y, nq1x, nq1y);    // Eq. 27 (exact value)
+    p.t2 = cross2x(np2x, np2y, nq2x, nq2y);
+}
+
+ACA_HD float fmax3_(float a, float b, float c);
+ACA_HD float pow2_inv_scale(float x);
+
+ACA_HD void aca_compose(const Set &s, const AcaParts &p, bool prescale, float H[9])
+{
+    float c11 = F_MUL(F_MUL(p.t1, p.Q3y), p.Q4x);
+    float c22 = F_MUL(F_MUL(p.t1, p.Q3x), p.Q4y);
+    float c33 = F_MUL(F_MUL(p.t2, p.Q3x), p.Q3y);
+    if (prescale) {
+        const float sc = pow2_inv_scale(fmax3_(c11, c22, c33));
+        c11 = F_MUL(c11, sc);
+        c22 = F_MUL(c22, sc);
+        c33 = F_MUL(c33, sc);
+    }
+    // H_C * A1 rows with A1 = [[MP1.y, -MP1.x], [-MN1.y, MN1.x]] (Eq. 20);
+    // third row = c11*a0 + c22*a1 + c33*(-NP1.y, NP1.x, f_A1), which equals
+    // (c11-c33)*a0 + (c22-c33)*a1 + c33*(0, 0, f_A1) of Eq. 28 exactly.
+    // Left factor H_A2^-1 (Eq. 22) in the M2 frame: [[MN2.x, MP2.x], [MN2.y, MP2.y]].
+    const float k0x = F_MUL(c11, p.MN2x), k0y = F_MUL(c11, p.MN2y);
+    const float k1x = F_MUL(c22, p.MP2x), k1y = F_MUL(c22, p.MP2y);
+    const float L00 = det2(k0x, k1x, p.MN1y, p.MP1y);     // k0x*MP1y - k1x*MN1y
+    const float L01 = det2(k1x, k0x, p.MP1x, p.MN1x);     // k1x*MN1x - k0x*MP1x
+    const float L10 = det2(k0y, k1y, p.MN1y, p.MP1y);
+    const float L11 = det2(k1y, k0y, p.MP1x, p.MN1x);
+    const float L20 = F_FMA(-c33, p.NP1y, det2(c11, c22, p.MN1y, p.MP1y));
+    const float L21 = F_FMA(c33, p.NP1x, det2(c22, c11, p.MP1x, p.MN1x));
+    const float L22 = F_MUL(c33, p.fA1);
+    // H = T(M2) * L * T(-M1)
+    const float G02 = -F_FMA(s.M1x, L00, F_MUL(s.M1y, L01));
+    const float G12 = -F_FMA(s.M1x, L10, F_MUL(s.M1y, L11));
+    const float G22 = F_FMA(-s.M1x, L20, F_FMA(-s.M1y, L21, L22));
+    H[0] = F_FMA(s.M2x, L20, L00);
+    H[1] = F_FMA(s.M2x, L21, L01);
+    H[2] = F_FMA(s.M2x, G22, G02);
+    H[3] = F_FMA(s.M2y, L20, L10);
+    H[4] = F_FMA(s.M2y, L21, L11);
+    H[5] = F_FMA(s.M2y, G22, G12);
+    H[6] = L20;
+    H[7] = L21;
+    H[8] = G22;
+}
+
+ACA_HD uint32_t f2u(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return __float_as_uint(x);
+#else
+    uint32_t u;
+    __builtin_memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+
+ACA_HD float u2f(uint32_t u)
+{
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(u);
+#else
+    float x;
+    __builtin_memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+
+// Power of two 2^-e where 2^e <= |x| < 2^(e+1), for normal finite x != 0
+// (exact scale factor); 1 for 0, subnormal or non-finite x.
+ACA_HD float pow2_inv_scale(float x)
+{
+    const int e = (int)((f2u(x) >> 23) & 0xffu) - 127;
+    if (e == -127 || e == 128)
+        return 1.0f;
+    const int b = 127 - e;                 // in [0, 253]
+    return b > 0 ? u2f((uint32_t)b << 23) : 1.0f;
+}
+
+ACA_HD float fabs_(float x) { return x < 0 ? -x : x; }
+
+ACA_HD float fmax3_(float a, float b, float c)
+{
+    a = fabs_(a); b = fabs_(b); c = fabs_(c);
+    const float m = a > b ? a : b;
+    return m > c ? m : c;
+}
+
+// Largest |entry| of H.
+ACA_HD float max_abs9(const float H[9])
+{
+    float m = 0.0f;
+    for (int i = 0; i < 9; ++i) { const float a = fabs_(H[i]); m = a > m ? a : m; }
+    return m;
+}
+
+// Normalisations (Sec. 3.4: "generally based on h33", 1 division + 8 mults).
+ACA_HD void normalize_h33(float H[9])
+{
+    const float r = F_DIV(1.0f, H[8]);
+    for (int i = 0; i < 8; ++i) H[i] = F_MUL(H[i], r);
+    H[8] = 1.0f;
+}
+
+// Unit Frobenius norm, sign so that h33 > 0 (or, when |h33| < 1e-6 |H|, so
+// that the entry of largest magnitude is positive).  Pre-scaled by a power of
+// two so the sum of squares cannot overflow.
+ACA_HD void normalize_frob(float H[9])
+{
+    const float m = max_abs9(H);
+    if (!(m > 0) || !(m < 3.0e38f)) return;
+    const float sc = pow2_inv_scale(m);
+    float h[9];
+    float ss = 0.0f;
+    int big = 0;
+    for (int i = 0; i < 9; ++i) {
+        h[i] = F_MUL(H[i], sc);
+        ss = F_FMA(h[i], h[i], ss);
+        if (fabs_(h[i]) > fabs_(h[big])) big = i;
+    }
+    const float nrm = F_SQRT(ss);
+    const float inv = F_DIV(1.0f, nrm);
+    const bool use33 = fabs_(h[8]) >= F_MUL(1e-6f, nrm);
+    const float sgn = use33 ? (h[8] > 0 ? 1.0f : -1.0f) : (h[big] > 0 ? 1.0f : -1.0f);
+    const float f = F_MUL(sgn, inv);
+    for (int i = 0; i < 9; ++i) H[i] = F_MUL(h[i], f);
+}
+
+ACA_HD float sq2(float x, float y) { return F_FMA(x, x, F_MUL(y, y)); }
+
+// |cross| < 1 px * longest side  <=>  cross^2 < max(|a|^2, |b|^2, |a-b|^2).
+ACA_HD bool near_collinear(float cr, float la, float lb, float lc)
+{
+    float L = la > lb ? la : lb;
+    L = L > lc ? L : lc;
+    return F_MUL(cr, cr) < L;
+}
+
+ACA_HD bool finite_(float x) { return x - x == 0.0f; }
+
+ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
+{
+    uint8_t f = 0;
+    const float lMN1 = sq2(p.MN1x, p.MN1y), lMP1 = sq2(p.MP1x, p.MP1y), lNP1 = sq2(p.NP1x, p.NP1y);
+    const float lMQ1 = sq2(p.MQ1x, p.MQ1y), lNQ1 = sq2(p.NQ1x, p.NQ1y);
+    const float PQ1x = F_SUB(s.Q1x, s.P1x), PQ1y = F_SUB(s.Q1y, s.P1y), lPQ1 = sq2(PQ1x, PQ1y);
+    const float lMN2 = sq2(p.MN2x, p.MN2y), lMP2 = sq2(p.MP2x, p.MP2y), lNP2 = sq2(p.NP2x, p.NP2y);
+    const float lMQ2 = sq2(p.MQ2x, p.MQ2y), lNQ2 = sq2(p.NQ2x, p.NQ2y);
+    const float PQ2x = F_SUB(s.Q2x, s.P2x), PQ2y = F_SUB(s.Q2y, s.P2y), lPQ2 = sq2(PQ2x, PQ2y);
+    if (near_collinear(p.fA1, lMN1, lMP1, lNP1)) f |= kFlagSrcAnchors;
+    if (near_collinear(p.fA2, lMN2, lMP2, lNP2)) f |= kFlagTgtAnchors;
+    if (near_collinear(p.Q3x, lMQ1, lMP1, lPQ1) || near_collinear(p.Q3y, lMN1, lMQ1, lNQ1) ||
+        near_collinear(p.t1, lNP1, lNQ1, lPQ1) || near_collinear(p.Q4x, lMQ2, lMP2, lPQ2) ||
+        near_collinear(p.Q4y, lMN2, lMQ2, lNQ2) || near_collinear(p.t2, lNP2, lNQ2, lPQ2))
+        f |= kFlagOtherTriple;
+    bool fin = true;
+    const float *sv = &s.M1x;
+    for (int i = 0; i < 16; ++i) fin = fin && finite_(sv[i]);
+    for (int i = 0; i < 9; ++i) fin = fin && finite_(H[i]);
+    if (!fin) f |= kFlagNonFinite;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// SKS (Sec. 3, Eq. 4-14), in the frames of the midpoints O1, O2.
+// ---------------------------------------------------------------------------
+ACA_HD void sks_solve(const Set &s, float H[9])
+{
+    // Eq. 4-5: O = (M + N) / 2, ON = N - O = (N - M) / 2 (exact halving)
+    const float ON1x = F_MUL(0.5f, F_SUB(s.N1x, s.M1x)), ON1y = F_MUL(0.5f, F_SUB(s.N1y, s.M1y));
+    const float ON2x = F_MUL(0.5f, F_SUB(s.N2x, s.M2x)), ON2y = F_MUL(0.5f, F_SUB(s.N2y, s.M2y));
+    const float O1x = F_ADD(s.M1x, ON1x), O1y = F_ADD(s.M1y, ON1y);
+    const float O2x = F_ADD(s.M2x, ON2x), O2y = F_ADD(s.M2y, ON2y);
+    const float fS1 = sq2(ON1x, ON1y), fS2 = sq2(ON2x, ON2y);   // Eq. 7
+    // P3 = H_S1 P1, Q3 = H_S1 Q1 (Eq. 6), homogeneous with w = f_S1
+    const float p1x = F_SUB(s.P1x, O1x), p1y = F_SUB(s.P1y, O1y);
+    const float q1x = F_SUB(s.Q1x, O1x), q1y = F_SUB(s.Q1y, O1y);
+    const float p2x = F_SUB(s.P2x, O2x), p2y = F_SUB(s.P2y, O2y);
+    const float q2x = F_SUB(s.Q2x, O2x), q2y = F_SUB(s.Q2y, O2y);
+    const float P3x = det2(ON1x, -ON1y, p1y, p1x), P3y = cross2(ON1x, ON1y, p1x, p1y);
+    const float Q3x = det2(ON1x, -ON1y, q1y, q1x), Q3y = cross2(ON1x, ON1y, q1x, q1y);
+    const float P4x = det2(ON2x, -ON2y, p2y, p2x), P4y = cross2(ON2x, ON2y, p2x, p2y);
+    const float Q4x = det2(ON2x, -ON2y, q2y, q2x), Q4y = cross2(ON2x, ON2y, q2x, q2y);
+    // Eq. 10-11: H_E swaps y and w; dehomogenise; translate by -P5 / -P6
+    const float P5x = F_DIV(P3x, P3y), P5y = F_DIV(fS1, P3y);
+    const float P6x = F_DIV(P4x, P4y), P6y = F_DIV(fS2, P4y);
+    const float Q7x = F_SUB(F_DIV(Q3x, Q3y), P5x), Q7y = F_SUB(F_DIV(fS1, Q3y), P5y);
+    const float Q8x = F_SUB(F_DIV(Q4x, Q4y), P6x), Q8y = F_SUB(F_DIV(fS2, Q4y), P6y);
+    // Eq. 11: [Q8.x, Q8.y] = [[a, b], [b, a]] [Q7.x, Q7.y]
+    const float det = F_MUL(F_SUB(Q7x, Q7y), F_ADD(Q7x, Q7y));
+    const float aK = F_DIV(det2(Q8x, Q8y, Q7y, Q7x), det);   // Q8x Q7x - Q8y Q7y
+    const float bK = F_DIV(det2(Q8y, Q8x, Q7y, Q7x), det);   // Q8y Q7x - Q8x Q7y
+    // Eq. 13
+    const float uK = F_SUB(P6x, F_FMA(aK, P5x, F_MUL(bK, P5y)));
+    const float vK = F_SUB(P6y, F_FMA(bK, P5x, F_MUL(aK, P5y)));
+    // Eq. 14 in the midpoint frames: L = R2^-1 K R1 with
+    // R1 = [[ON1x, ON1y, 0], [-ON1y, ON1x, 0], [0, 0, fS1]],
+    // R2^-1 = [[ON2x, -ON2y, 0], [ON2y, ON2x, 0], [0, 0, 1]],
+    // K = [[aK, uK, bK], [0, 1, 0], [bK, vK, aK]].
+    // K R1:
+    const float A00 = det2(aK, uK, ON1y, ON1x);       // aK*ON1x - uK*ON1y
+    const float A01 = F_FMA(aK, ON1y, F_MUL(uK, ON1x));
+    const float A02 = F_MUL(bK, fS1);
+    const float A10 = -ON1y, A11 = ON1x;
+    const float A20 = det2(bK, vK, ON1y, ON1x);
+    const float A21 = F_FMA(bK, ON1y, F_MUL(vK, ON1x));
+    const float A22 = F_MUL(aK, fS1);
+    // R2^-1 (K R1):
+    const float L00 = det2(ON2x, ON2y, A10, A00), L01 = det2(ON2x, ON2y, A11, A01), L02 = F_MUL(ON2x, A02);
+    const float L10 = F_FMA(ON2y, A00, F_MUL(ON2x, A10)), L11 = F_FMA(ON2y, A01, F_MUL(ON2x, A11));
+    const float L12 = F_MUL(ON2y, A02);
+    const float L20 = A20, L21 = A21, L22 = A22;
+    // H = T(O2) L T(-O1)
+    const float G02 = F_FMA(-O1x, L00, F_FMA(-O1y, L01, L02));
+    const float G12 = F_FMA(-O1x, L10, F_FMA(-O1y, L11, L12));
+    const float G22 = F_FMA(-O1x, L20, F_FMA(-O1y, L21, L22));
+    H[0] = F_FMA(O2x, L20, L00);
+    H[1] = F_FMA(O2x, L21, L01);
+    H[2] = F_FMA(O2x, G22, G02);
+    H[3] = F_FMA(O2y, L20, L10);
+    H[4] = F_FMA(O2y, L21, L11);
+    H[5] = F_FMA(O2y, G22, G12);
+    H[6] = L20;
+    H[7] = L21;
+    H[8] = G22;
+}
+
+// ---------------------------------------------------------------------------
+// Rectangle source (Sec. 5.3, Eq. 39-42): M1 = (x0, y0) upper-left corner,
+// width w, aspect ratio r = width / height; target corners M2 N2 P2 Q2.
+// ---------------------------------------------------------------------------
+struct Rect {
+    float x0, y0, w, r;
+};
+
+struct RectParts {
+    float MN2x, MN2y, MP2x, MP2y, MQ2x, MQ2y, NP2x, NP2y, NQ2x, NQ2y;
+    float fA2, Q4x, Q4y, t2;
+};
+
+ACA_HD void rect_parts(const float t[8], RectParts &p)
+{
+    p.MN2x = F_SUB(t[2], t[0]); p.MN2y = F_SUB(t[3], t[1]);
+    p.MP2x = F_SUB(t[4], t[0]); p.MP2y = F_SUB(t[5], t[1]);
+    p.MQ2x = F_SUB(t[6], t[0]); p.MQ2y = F_SUB(t[7], t[1]);
+    p.NP2x = F_SUB(t[4], t[2]); p.NP2y = F_SUB(t[5], t[3]);
+    p.NQ2x = F_SUB(t[6], t[2]); p.NQ2y = F_SUB(t[7], t[3]);
+    p.fA2 = cross2(p.MN2x, p.MN2y, p.MP2x, p.MP2y);
+    p.Q4x = cross2(p.MQ2x, p.MQ2y, p.MP2x, p.MP2y);
+    p.Q4y = cross2(p.MN2x, p.MN2y, p.MQ2x, p.MQ2y);
+    p.t2 = cross2(p.NP2x, p.NP2y, p.NQ2x, p.NQ2y);
+}
+
+// Eq. 42: H = [[N2x, P2x, M2x], [N2y, P2y, M2y], [1, 1, 1]] * B,
+// B = [[Q4x, 0, -Q4x x0], [0, r Q4y, -r Q4y y0], [t2, r t2, -t2 (x0 + r y0 + w)]].
+ACA_HD void rect_solve(const float t[8], const Rect &R, float H[9])
+{
+    RectParts p;
+    rect_parts(t, p);
+    const float rQ4y = F_MUL(R.r, p.Q4y), rt2 = F_MUL(R.r, p.t2);
+    const float c0x = F_FMA(p.Q4x, t[2], F_MUL(p.t2, t[0]));   // column 1
+    const float c0y = F_FMA(p.Q4x, t[3], F_MUL(p.t2, t[1]));
+    const float c0w = F_ADD(p.Q4x, p.t2);
+    const float c1x = F_FMA(rQ4y, t[4], F_MUL(rt2, t[0]));     // column 2
+    const float c1y = F_FMA(rQ4y, t[5], F_MUL(rt2, t[1]));
+    const float c1w = F_ADD(rQ4y, rt2);
+    // column 3 = -(x0 col1 + y0 col2 + w t2 m2): the t2 m2 parts of x0 col1
+    // and y0 col2 supply the remaining -t2 (x0 + r y0) m2 of Eq. 42
+    const float t2w = F_MUL(p.t2, R.w);
+    H[0] = c0x; H[3] = c0y; H[6] = c0w;
+    H[1] = c1x; H[4] = c1y; H[7] = c1w;
+    H[2] = -F_FMA(R.x0, c0x, F_FMA(R.y0, c1x, F_MUL(t2w, t[0])));
+    H[5] = -F_FMA(R.x0, c0y, F_FMA(R.y0, c1y, F_MUL(t2w, t[1])));
+    H[8] = -F_FMA(R.x0, c0w, F_FMA(R.y0, c1w, t2w));
+}
+
+}  // namespace aca

@@ -1,0 +1,54 @@
+// Host-side plumbing shared by the C-ABI entry points: status codes, the
+// thread-local error message, cached device properties and launch helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <cstdarg>
+
+#include "../../include/aca.h"
+
+namespace aca {
+
+aca_status set_error(aca_status st, const char *fmt, ...);
+
+inline aca_status check_launch(const char *what)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_error(ACA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return ACA_OK;
+}
+
+// SM count of the current device (queried once per device and cached).
+int sm_count();
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Streaming (evict-first) global accesses for data touched exactly once.
+__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream(float4 *p, float4 v) { __stcs(p, v); }
+__device__ __forceinline__ float ld_stream(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream(float *p, float v) { __stcs(p, v); }
+
+inline float4 *as_f4(float *p) { return reinterpret_cast<float4 *>(p); }
+inline const float4 *as_f4(const float *p) { return reinterpret_cast<const float4 *>(p); }
+
+// Persistent-grid size: SMs x resident blocks of `kernel` at `threads`
+// threads and `smem` dynamic bytes, capped by `work_blocks` (>= 1).
+template <typename K>
+int resident_grid(K kernel, int threads, size_t smem, int64_t work_blocks)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)per_sm * sm_count();
+    if (work_blocks < g)
+        g = work_blocks;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace aca

@@ -1,0 +1,511 @@
+// RANSAC with ACA hypotheses, many problems of uneven size per launch
+// (Sec. 2.2: sample a minimal set, solve, verify against all
+// correspondences, keep the best; Sec. 6.2 runs this with the solvers of
+// the paper plugged in).
+//
+// Kernels (all on the caller's stream, no host synchronisation):
+//  1. ransac_prep_kernel    one block: per-problem prefix sums of hypotheses
+//                           and work items, resets the work counter;
+//  2. zero_counts_kernel    clears the per-hypothesis counts;
+//  3. ransac_score_kernel   persistent grid; each block repeatedly takes an
+//                           item (problem p, hypotheses h0..h0+HB-1, points
+//                           i0..i0+T-1) from one atomic counter, samples and
+//                           solves its HB hypotheses (Philox + ACA) into shared
+//                           memory while the whole block stages the point
+//                           slice in shared memory, then scores: lane l of
+//                           every warp holds hypotheses l, l+32, ... in
+//                           registers, each warp walks its share of the slice
+//                           (every lane reads the same point: a shared-memory
+//                           broadcast) and counts inliers with a division-free
+//                           test; warp partials are summed in shared memory and
+//                           added to the global count with one atomic per
+//                           hypothesis;
+//  4. ransac_finish_kernel  one block per problem: argmax (ties to the lowest
+//                           index), re-solve of the winner with the same
+//                           device code (bit-identical H), inlier mask, outputs.
+// There are no inter-block waits: progress only needs the atomics.
+#include "aca_math.cuh"
+#include "common.cuh"
+#include "philox.cuh"
+
+namespace aca {
+
+// Degenerate-sample rule: on either side one of the triples (M,N,P),
+// (M,Q,P), (M,N,Q), (N,P,Q) has |cross(a,b)| <= 1e-3 |a||b| for its edge
+// vectors a, b (sine of the angle at most 1e-3).
+__device__ __forceinline__ bool triple_degenerate(float cr, float ax, float ay, float bx, float by)
+{
+    const float tau2 = 1e-6f;
+    const float la = sq2(ax, ay), lb = sq2(bx, by);
+    return F_MUL(cr, cr) <= F_MUL(F_MUL(tau2, la), lb);
+}
+
+__device__ __forceinline__ bool sample_degenerate(const AcaParts &p)
+{
+    return triple_degenerate(p.fA1, p.MN1x, p.MN1y, p.MP1x, p.MP1y) ||
+           triple_degenerate(p.Q3x, p.MQ1x, p.MQ1y, p.MP1x, p.MP1y) ||
+           triple_degenerate(p.Q3y, p.MN1x, p.MN1y, p.MQ1x, p.MQ1y) ||
+           triple_degenerate(p.t1, p.NP1x, p.NP1y, p.NQ1x, p.NQ1y) ||
+           triple_degenerate(p.fA2, p.MN2x, p.MN2y, p.MP2x, p.MP2y) ||
+           triple_degenerate(p.Q4x, p.MQ2x, p.MQ2y, p.MP2x, p.MP2y) ||
+           triple_degenerate(p.Q4y, p.MN2x, p.MN2y, p.MQ2x, p.MQ2y) ||
+           triple_degenerate(p.t2, p.NP2x, p.NP2y, p.NQ2x, p.NQ2y);
+}
+
+// Hypothesis h of a problem whose N >= 4 correspondences start at `c`:
+// sample, reject degenerate samples, solve by ACA and scale H by a power of
+// two so that its largest entry lies in [1, 2) (exact; keeps the squared
+// residuals of the test far from overflow).  Returns false if degenerate.
+__device__ __forceinline__ bool make_hypothesis(const float4 *__restrict__ c, uint32_t N, uint64_t seed,
+                                                uint32_t prob, uint32_t h, float H[9])
+{
+    uint32_t idx[4];
+    sample4(seed, prob, h, N, idx);
+    const float4 m = c[idx[0]], n = c[idx[1]], p4 = c[idx[2]], q = c[idx[3]];
+    const Set s{m.x, m.y, n.x, n.y, p4.x, p4.y, q.x, q.y, m.z, m.w, n.z, n.w, p4.z, p4.w, q.z, q.w};
+    AcaParts p;
+    aca_parts(s, p);
+    if (sample_degenerate(p))
+        return false;
+    aca_compose(s, p, true, H);
+    const float sc = pow2_inv_scale(max_abs9(H));
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        H[i] = F_MUL(H[i], sc);
+    return true;
+}
+
+// Forward transfer error test without division: with (u, v, w) = H (x, y, 1),
+// inlier iff w != 0 and (u - X w)^2 + (v - Y w)^2 <= (thr w)^2.
+__device__ __forceinline__ int inlier(const float H[9], float4 c, float thr)
+{
+    const float w = F_FMA(H[6], c.x, F_FMA(H[7], c.y, H[8]));
+    const float u = F_FMA(H[0], c.x, F_FMA(H[1], c.y, H[2]));
+    const float v = F_FMA(H[3], c.x, F_FMA(H[4], c.y, H[5]));
+    const float du = F_FMA(-c.z, w, u);
+    const float dv = F_FMA(-c.w, w, v);
+    const float r2 = F_FMA(du, du, F_MUL(dv, dv));
+    const float tw = F_MUL(thr, w);
+    const float d = F_FMA(tw, tw, -r2);
+    return (d >= 0.0f) & (w != 0.0f);
+}
+
+struct Workspace {
+    int64_t *hyp_off;            // [P+1]
+    int64_t *item_off;           // [P+1]
+    unsigned long long *counter; // [1] work counter
+    int32_t *flags;              // [1] 1 = counts capacity exceeded
+    int32_t *counts;             // [capacity]
+    int64_t capacity;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Workspace carve(void *base, int32_t P, size_t bytes)
+{
+    Workspace w;
+    char *b = static_cast<char *>(base);
+    size_t o = 0;
+    w.hyp_off = reinterpret_cast<int64_t *>(b + o);
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));
+    w.item_off = reinterpret_cast<int64_t *>(b + o);
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));
+    w.counter = reinterpret_cast<unsigned long long *>(b + o);
+    w.flags = reinterpret_cast<int32_t *>(b + o + 8);
+    o += 256;
+    w.counts = reinterpret_cast<int32_t *>(b + o);
+    w.capacity = bytes > o ? (int64_t)((bytes - o) / sizeof(int32_t)) : 0;
+    return w;
+}
+
+static size_t header_bytes(int32_t P)
+{
+    return 2 * align256(sizeof(int64_t) * (size_t)(P + 1)) + 256;
+}
+
+// Inclusive block scan of int64 (blockDim.x == 1024).
+__device__ int64_t block_scan_incl(int64_t v, int64_t *warp_tot)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    if (wid > 0) v += warp_tot[wid - 1];
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__restrict__ offsets,
+                                                           const int32_t *__restrict__ n_hyp, int32_t P, int HB,
+                                                           int T, Workspace ws)
+{
+    __shared__ int64_t wt_a[32], wt_b[32];
+    __shared__ int64_t carry_a, carry_b;
+    if (threadIdx.x == 0) {
+        carry_a = 0;
+        carry_b = 0;
+        ws.hyp_off[0] = 0;
+        ws.item_off[0] = 0;
+        *ws.counter = 0ull;
+        *ws.flags = 0;
+    }
+    __syncthreads();
+    for (int32_t base = 0; base < P; base += 1024) {
+        const int32_t p = base + (int32_t)threadIdx.x;
+        int64_t k = 0, items = 0;
+        if (p < P) {
+            k = n_hyp[p] > 0 ? n_hyp[p] : 0;
+            const int64_t N = offsets[p + 1] - offsets[p];
+            if (N >= 4 && k > 0)
+                items = ((k + HB - 1) / HB) * ((N + T - 1) / T);
+        }
+        const int64_t ia = block_scan_incl(k, wt_a);
+        const int64_t ib = block_scan_incl(items, wt_b);
+        if (p < P) {
+            ws.hyp_off[p + 1] = carry_a + ia;
+            ws.item_off[p + 1] = carry_b + ib;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            carry_a += ia;
+            carry_b += ib;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && carry_a > ws.capacity) {
+        *ws.flags = 1;
+        ws.item_off[P] = 0;   // nothing to score
+    }
+}
+
+__global__ void zero_counts_kernel(Workspace ws, int32_t P)
+{
+    const int64_t total = ws.hyp_off[P];
+    const int64_t lim = total < ws.capacity ? total : ws.capacity;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += (int64_t)gridDim.x * blockDim.x)
+        ws.counts[i] = 0;
+}
+
+struct ItemInfo {
+    int64_t item;
+    int32_t p;
+    uint32_t N;
+    int64_t base;   // first correspondence of problem p
+    int64_t hbase;  // first hypothesis slot of problem p
+    int32_t h0, nh; // hypotheses of this item
+    int32_t i0, ni; // points of this item
+    int32_t slice;
+};
+
+// Largest p with item_off[p] <= item (item_off non-decreasing, p < P):
+// 32-way search by one warp.
+__device__ int32_t find_problem(const int64_t *__restrict__ item_off, int32_t P, int64_t item)
+{
+    int32_t lo = 0, hi = P;   // answer in [lo, hi)
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 1) {
+        const int32_t stride = (hi - lo + 31) / 32;
+        const int32_t q = lo + lane * stride;
+        const bool ok = q < hi && item_off[q] <= item;
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        const int last = 31 - __clz((int)b);   // lane 0 always satisfies (item_off[lo] <= item)
+        lo = lo + last * stride;
+        hi = min(hi, lo + stride);
+    }
+    return lo;
+}
+
+template <int HPT>
+__global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restrict__ corr,
+                                                            const int64_t *__restrict__ offsets,
+                                                            const int32_t *__restrict__ n_hyp, int32_t P, float thr,
+                                                            uint64_t seed, uint32_t prob_base, int T, Workspace ws)
+{
+    constexpr int HB = 32 * HPT;
+    extern __shared__ float4 smem4[];
+    const int W = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4 *tile = smem4;                                                   // [T]
+    float *Hs = reinterpret_cast<float *>(smem4 + T);                       // [HB][12]
+    int32_t *red = reinterpret_cast<int32_t *>(Hs + HB * 12);               // [W][HB]
+    __shared__ ItemInfo info;
+
+    const int64_t total = ws.item_off[P];
+    for (;;) {
+        if (wid == 0) {
+            int64_t item = 0;
+            if (lane == 0)
+                item = (int64_t)atomicAdd(ws.counter, 1ull);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item < total) {
+                const int32_t p = find_problem(ws.item_off, P, item);
+                if (lane == 0) {
+                    const int64_t base = offsets[p];
+                    const uint32_t N = (uint32_t)(offsets[p + 1] - base);
+                    const int32_t k = n_hyp[p];
+                    const int64_t r = item - ws.item_off[p];
+                    const int32_t S = (int32_t)((N + T - 1) / T);
+                    const int32_t chunk = (int32_t)(r / S), slice = (int32_t)(r % S);
+                    info.item = item;
+                    info.p = p;
+                    info.N = N;
+                    info.base = base;
+                    info.hbase = ws.hyp_off[p];
+                    info.h0 = chunk * HB;
+                    info.nh = min(HB, k - chunk * HB);
+                    info.i0 = slice * T;
+                    info.ni = (int32_t)min((int64_t)T, (int64_t)N - (int64_t)slice * T);
+                    info.slice = slice;
+                }
+            } else if (lane == 0) {
+                info.item = item;
+            }
+        }
+        __syncthreads();
+        // copy the item to registers now: warp 0 rewrites `info` for the next
+        // item as soon as it has passed this iteration's last barrier
+        if (info.item >= total)
+            break;
+        const int32_t p = info.p, nh = info.nh, h0 = info.h0, ni = info.ni, i0 = info.i0, slice = info.slice;
+        const uint32_t N = info.N;
+        const int64_t hbase = info.hbase;
+        const float4 *cp = corr + info.base;
+
+        // hypotheses of this item -> shared memory
+        if ((int)threadIdx.x < HB) {
+            float H[9];
+            const int t = threadIdx.x;
+            bool valid = false;
+            if (t < nh) {
+                valid = make_hypothesis(cp, N, seed, prob_base + (uint32_t)p, (uint32_t)(h0 + t), H);
+                if (!valid && slice == 0)
+                    ws.counts[hbase + h0 + t] = -1;
+            }
+            if (!valid) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) H[i] = 0.0f;   // scores nothing (w == 0)
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Hs[t * 12 + i] = H[i];
+            Hs[t * 12 + 9] = valid ? 1.0f : 0.0f;
+        }
+        // correspondence slice -> shared memory
+        for (int i = threadIdx.x; i < ni; i += blockDim.x)
+            tile[i] = cp[i0 + i];
+        __syncthreads();
+
+        float h[HPT][9];
+        int cnt[HPT];
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[j][i] = Hs[(lane + 32 * j) * 12 + i];
+            cnt[j] = 0;
+        }
+        int i = wid;
+        for (; i + 3 * W < ni; i += 4 * W) {
+            const float4 c0 = tile[i], c1 = tile[i + W], c2 = tile[i + 2 * W], c3 = tile[i + 3 * W];
+#pragma unroll
+            for (int j = 0; j < HPT; ++j)
+                cnt[j] += inlier(h[j], c0, thr) + inlier(h[j], c1, thr) + inlier(h[j], c2, thr) +
+                          inlier(h[j], c3, thr);
+        }
+        for (; i < ni; i += W) {
+            const float4 c0 = tile[i];
+#pragma unroll
+            for (int j = 0; j < HPT; ++j) cnt[j] += inlier(h[j], c0, thr);
+        }
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) red[wid * HB + lane + 32 * j] = cnt[j];
+        __syncthreads();
+        if ((int)threadIdx.x < nh && Hs[threadIdx.x * 12 + 9] != 0.0f) {
+            int s = 0;
+            for (int w = 0; w < W; ++w) s += red[w * HB + threadIdx.x];
+            if (s)
+                atomicAdd(&ws.counts[hbase + h0 + threadIdx.x], s);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__restrict__ corr,
+                                                            const int64_t *__restrict__ offsets,
+                                                            const int32_t *__restrict__ n_hyp, int32_t P, float thr,
+                                                            uint64_t seed, uint32_t prob_base, Workspace ws,
+                                                            float *__restrict__ best_H, int32_t *__restrict__ best_count,
+                                                            int32_t *__restrict__ best_hyp,
+                                                            int32_t *__restrict__ hyp_counts,
+                                                            uint8_t *__restrict__ mask)
+{
+    const int32_t p = blockIdx.x;
+    const int64_t base = offsets[p];
+    const int64_t N = offsets[p + 1] - base;
+    const int32_t k = n_hyp[p] > 0 ? n_hyp[p] : 0;
+    const int64_t hb = ws.hyp_off[p];
+    const bool overflow = *ws.flags != 0;
+    __shared__ int32_t s_cnt[8], s_idx[8];
+    __shared__ float sH[9];
+    __shared__ int32_t s_best;
+
+    int32_t bc = -1, bi = 0x7fffffff;
+    if (!overflow && N >= 4) {
+        for (int32_t h = threadIdx.x; h < k; h += blockDim.x) {
+            const int32_t c = ws.counts[hb + h];
+            if (hyp_counts) hyp_counts[hb + h] = c;
+            if (c > bc || (c == bc && h < bi)) { bc = c; bi = h; }
+        }
+    } else if (!overflow && hyp_counts) {
+        for (int32_t h = threadIdx.x; h < k; h += blockDim.x) hyp_counts[hb + h] = -1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int32_t c = __shfl_down_sync(0xffffffffu, bc, o), i = __shfl_down_sync(0xffffffffu, bi, o);
+        if (c > bc || (c == bc && i < bi)) { bc = c; bi = i; }
+    }
+    if ((threadIdx.x & 31) == 0) { s_cnt[threadIdx.x >> 5] = bc; s_idx[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bc = s_cnt[0]; bi = s_idx[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (s_cnt[w] > bc || (s_cnt[w] == bc && s_idx[w] < bi)) { bc = s_cnt[w]; bi = s_idx[w]; }
+        if (overflow) { bi = -2; bc = 0; }
+        else if (bc < 0) { bi = -1; bc = 0; }
+        s_best = bi;
+        float H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (bi >= 0)
+            make_hypothesis(corr + base, (uint32_t)N, seed, prob_base + (uint32_t)p, (uint32_t)bi, H);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sH[i] = H[i];
+        best_hyp[p] = bi;
+        best_count[p] = bc;
+        normalize_frob(H);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) best_H[9 * p + i] = H[i];
+    }
+    __syncthreads();
+    if (mask) {
+        float H[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) H[i] = sH[i];
+        const bool any = s_best >= 0;
+        for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+            mask[base + i] = any ? (uint8_t)inlier(H, corr[base + i], thr) : (uint8_t)0;
+    }
+}
+
+__global__ void sample_indices_kernel(uint32_t N, int32_t n_hyp, uint64_t seed, uint32_t prob, int4 *__restrict__ idx)
+{
+    for (int32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n_hyp; h += gridDim.x * blockDim.x) {
+        uint32_t i[4];
+        sample4(seed, prob, (uint32_t)h, N, i);
+        idx[h] = make_int4((int)i[0], (int)i[1], (int)i[2], (int)i[3]);
+    }
+}
+
+}  // namespace aca
+
+using namespace aca;
+
+extern "C" aca_status aca_sample_indices(int64_t N, int32_t n_hyp, uint64_t seed, uint32_t problem, int32_t *idx,
+                                         void *stream)
+{
+    if (N < 4 || N >= (int64_t(1) << 31))
+        return set_error(ACA_ERR_INVALID_ARG, "aca_sample_indices: need 4 <= N < 2^31");
+    if (n_hyp < 0)
+        return set_error(ACA_ERR_INVALID_ARG, "aca_sample_indices: n_hyp < 0");
+    if (n_hyp == 0)
+        return ACA_OK;
+    if (!idx || !aligned16(idx))
+        return set_error(ACA_ERR_INVALID_ARG, "aca_sample_indices: idx must be non-null and 16-byte aligned");
+    const int threads = 256;
+    const int grid = resident_grid(sample_indices_kernel, threads, 0, (n_hyp + threads - 1) / threads);
+    sample_indices_kernel<<<grid, threads, 0, as_stream(stream)>>>((uint32_t)N, n_hyp, seed, problem,
+                                                                  reinterpret_cast<int4 *>(idx));
+    return check_launch("aca_sample_indices");
+}
+
+extern "C" size_t ransac_aca_workspace_size(int32_t P, int64_t total_hyps)
+{
+    if (P < 0 || total_hyps < 0)
+        return 0;
+    return header_bytes(P) + align256(sizeof(int32_t) * (size_t)total_hyps);
+}
+
+extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, const int32_t *n_hyp, int32_t P,
+                                 const aca_ransac_params *params, float *best_H, int32_t *best_count,
+                                 int32_t *best_hyp, int32_t *hyp_counts, uint8_t *inlier_mask, void *workspace,
+                                 size_t workspace_bytes, void *stream)
+{
+    if (P < 0)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: P < 0");
+    if (P == 0)
+        return ACA_OK;
+    if (!corr || !offsets || !n_hyp || !params || !best_H || !best_count || !best_hyp || !workspace)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: null pointer");
+    if (!aligned16(corr))
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: corr must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: workspace must be 256-byte aligned");
+    if (workspace_bytes < header_bytes(P))
+        return set_error(ACA_ERR_WORKSPACE, "ransac_aca: workspace smaller than %zu bytes", header_bytes(P));
+    if (!(params->threshold_px > 0.0f))
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: threshold_px must be > 0");
+    const int W = params->block_warps ? params->block_warps : 8;
+    const int HPT = params->hyps_per_thread ? params->hyps_per_thread : 2;
+    const int T = params->tile_points ? params->tile_points : 1024;
+    if (W < 1 || W > 16)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: block_warps must be in 1..16");
+    if (HPT != 1 && HPT != 2 && HPT != 4)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: hyps_per_thread must be 1, 2 or 4");
+    if (T < 32 || T > 8192 || T % 32 != 0)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: tile_points must be a multiple of 32 in 32..8192");
+    if (32 * HPT > 32 * W)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: need hyps_per_thread <= block_warps");
+    const int HB = 32 * HPT;
+    const cudaStream_t st = as_stream(stream);
+    const Workspace ws = carve(workspace, P, workspace_bytes);
+
+    ransac_prep_kernel<<<1, 1024, 0, st>>>(offsets, n_hyp, P, HB, T, ws);
+    aca_status s = check_launch("ransac_aca (prep)");
+    if (s != ACA_OK) return s;
+    {
+        const int threads = 256;
+        const int grid = resident_grid(zero_counts_kernel, threads, 0, (ws.capacity + threads - 1) / threads);
+        zero_counts_kernel<<<grid, threads, 0, st>>>(ws, P);
+        if ((s = check_launch("ransac_aca (zero)")) != ACA_OK) return s;
+    }
+    const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
+    const int threads = 32 * W;
+    const float4 *c4 = reinterpret_cast<const float4 *>(corr);
+#define ACA_SCORE(HPTV)                                                                                       \
+    {                                                                                                          \
+        auto k = ransac_score_kernel<HPTV>;                                                                    \
+        if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                                     (int)smem) != cudaSuccess)                                \
+            return set_error(ACA_ERR_CUDA, "ransac_aca: cannot reserve %zu bytes of shared memory", smem);    \
+        const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
+        k<<<grid, threads, smem, st>>>(c4, offsets, n_hyp, P, params->threshold_px, params->seed,              \
+                                       params->problem_base, T, ws);                                           \
+    }
+    if (HPT == 1) ACA_SCORE(1)
+    else if (HPT == 2) ACA_SCORE(2)
+    else ACA_SCORE(4)
+#undef ACA_SCORE
+    if ((s = check_launch("ransac_aca (score)")) != ACA_OK) return s;
+    ransac_finish_kernel<<<P, 256, 0, st>>>(c4, offsets, n_hyp, P, params->threshold_px, params->seed,
+                                            params->problem_base, ws, best_H, best_count, best_hyp, hyp_counts,
+                                            inlier_mask);
+    return check_launch("ransac_aca (finish)");
+}

@@ -1,0 +1,250 @@
+// Batched minimal solvers: aca_solve (Sec. 4), sks_solve (Sec. 3) and
+// aca_rect_solve (Sec. 5.3), one set per thread lane in registers.
+//
+// The work is a pure stream (64 B in, 36 B out per set, ~250 FP32
+// instructions), so the kernels are bound by HBM bandwidth: each thread loads
+// four adjacent sets as one float4 from each of the 16 SoA planes, solves them
+// one after another in registers and writes nine float4 planes with streaming
+// (evict-first) stores.  A persistent grid (SMs x resident blocks) strides over
+// the quads.  When the layout does not allow 16-byte accesses a scalar variant
+// (one set per thread, coalesced 4-byte accesses) runs instead.
+#include "aca_math.cuh"
+#include "common.cuh"
+
+namespace aca {
+
+enum Solver { kAca = 0, kSks = 1 };
+
+template <int SOLVER, int NORM, bool FLAGS>
+__device__ __forceinline__ void solve_one(const Set &s, float H[9], uint8_t &flag)
+{
+    if (SOLVER == kAca) {
+        AcaParts p;
+        aca_parts(s, p);
+        aca_compose(s, p, NORM != ACA_NORM_NONE, H);
+        if (NORM == ACA_NORM_H33) normalize_h33(H);
+        if (NORM == ACA_NORM_FROB) normalize_frob(H);
+        if (FLAGS) flag = aca_flags(s, p, H);
+    } else {
+        sks_solve(s, H);
+        if (NORM == ACA_NORM_H33) normalize_h33(H);
+        if (NORM == ACA_NORM_FROB) normalize_frob(H);
+        if (FLAGS) {
+            AcaParts p;
+            aca_parts(s, p);
+            flag = aca_flags(s, p, H);
+        }
+    }
+}
+
+template <int SOLVER, int NORM, bool FLAGS>
+__global__ void __launch_bounds__(256) solve_vec4_kernel(const float *__restrict__ pts, float *__restrict__ Hout,
+                                                          uint8_t *__restrict__ flags, int64_t n, int64_t ld)
+{
+    const int64_t nq = (n + 3) >> 2;
+    const int64_t ldq = ld >> 2;
+    const float4 *in = reinterpret_cast<const float4 *>(pts);
+    float4 *out = reinterpret_cast<float4 *>(Hout);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        float4 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            v[k] = ld_stream(in + k * ldq + q);
+        float4 h[9];
+        uint32_t fl = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Set s;
+            float *sv = &s.M1x;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                sv[k] = (&v[k].x)[j];
+            float H[9];
+            uint8_t f = 0;
+            solve_one<SOLVER, NORM, FLAGS>(s, H, f);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                (&h[k].x)[j] = H[k];
+            fl |= (uint32_t)f << (8 * j);
+        }
+        const int64_t i0 = q << 2;
+        if (i0 + 3 < n) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                st_stream(out + k * ldq + q, h[k]);
+            if (FLAGS)
+                reinterpret_cast<uint32_t *>(flags)[q] = fl;
+        } else {
+            for (int j = 0; j < 4 && i0 + j < n; ++j) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    Hout[k * ld + i0 + j] = (&h[k].x)[j];
+                if (FLAGS)
+                    flags[i0 + j] = (uint8_t)(fl >> (8 * j));
+            }
+        }
+    }
+}
+
+template <int SOLVER, int NORM, bool FLAGS>
+__global__ void __launch_bounds__(256) solve_scalar_kernel(const float *__restrict__ pts, float *__restrict__ Hout,
+                                                            uint8_t *__restrict__ flags, int64_t n, int64_t ld)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Set s;
+        float *sv = &s.M1x;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            sv[k] = ld_stream(pts + k * ld + i);
+        float H[9];
+        uint8_t f = 0;
+        solve_one<SOLVER, NORM, FLAGS>(s, H, f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            st_stream(Hout + k * ld + i, H[k]);
+        if (FLAGS)
+            flags[i] = f;
+    }
+}
+
+template <int SOLVER, int NORM, bool FLAGS>
+static aca_status launch_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int64_t ld, cudaStream_t st)
+{
+    const int threads = 256;
+    const bool vec = (ld % 4 == 0) && aligned16(pts) && aligned16(H) &&
+                     (!FLAGS || (reinterpret_cast<uintptr_t>(flags) & 3u) == 0);
+    if (vec) {
+        auto k = solve_vec4_kernel<SOLVER, NORM, FLAGS>;
+        const int64_t nq = (n + 3) / 4;
+        const int grid = resident_grid(k, threads, 0, (nq + threads - 1) / threads);
+        k<<<grid, threads, 0, st>>>(pts, H, flags, n, ld);
+    } else {
+        auto k = solve_scalar_kernel<SOLVER, NORM, FLAGS>;
+        const int grid = resident_grid(k, threads, 0, (n + threads - 1) / threads);
+        k<<<grid, threads, 0, st>>>(pts, H, flags, n, ld);
+    }
+    return check_launch(SOLVER == kAca ? "aca_solve" : "sks_solve");
+}
+
+template <int SOLVER>
+static aca_status dispatch_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int64_t ld, int32_t norm,
+                                 void *stream)
+{
+    const char *name = SOLVER == kAca ? "aca_solve" : "sks_solve";
+    if (n < 0 || ld < n)
+        return set_error(ACA_ERR_INVALID_ARG, "%s: need 0 <= n <= ld (n=%lld, ld=%lld)", name, (long long)n,
+                         (long long)ld);
+    if (norm < ACA_NORM_NONE || norm > ACA_NORM_FROB)
+        return set_error(ACA_ERR_INVALID_ARG, "%s: unknown norm %d", name, norm);
+    if (n == 0)
+        return ACA_OK;
+    if (!pts || !H)
+        return set_error(ACA_ERR_INVALID_ARG, "%s: null pts or H", name);
+    if (ld > (INT64_MAX / 16))
+        return set_error(ACA_ERR_INVALID_ARG, "%s: ld too large", name);
+    const cudaStream_t st = as_stream(stream);
+#define ACA_CASE(NRM)                                                                              \
+    if (norm == NRM)                                                                               \
+        return flags ? launch_solve<SOLVER, NRM, true>(pts, H, flags, n, ld, st)                   \
+                     : launch_solve<SOLVER, NRM, false>(pts, H, flags, n, ld, st);
+    ACA_CASE(ACA_NORM_NONE)
+    ACA_CASE(ACA_NORM_H33)
+    ACA_CASE(ACA_NORM_FROB)
+#undef ACA_CASE
+    return ACA_ERR_INVALID_ARG;
+}
+
+// --------------------------------------------------------------------------
+// Rectangle source (Eq. 42): 8 target planes in, 9 planes out.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) rect_vec4_kernel(const float *__restrict__ tgt, Rect R, float *__restrict__ Hout,
+                                                         int64_t n, int64_t ld)
+{
+    const int64_t nq = (n + 3) >> 2, ldq = ld >> 2;
+    const float4 *in = reinterpret_cast<const float4 *>(tgt);
+    float4 *out = reinterpret_cast<float4 *>(Hout);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        float4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = ld_stream(in + k * ldq + q);
+        float4 h[9];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float t[8], H[9];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                t[k] = (&v[k].x)[j];
+            rect_solve(t, R, H);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                (&h[k].x)[j] = H[k];
+        }
+        const int64_t i0 = q << 2;
+        if (i0 + 3 < n) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                st_stream(out + k * ldq + q, h[k]);
+        } else {
+            for (int j = 0; j < 4 && i0 + j < n; ++j)
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    Hout[k * ld + i0 + j] = (&h[k].x)[j];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) rect_scalar_kernel(const float *__restrict__ tgt, Rect R,
+                                                           float *__restrict__ Hout, int64_t n, int64_t ld)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float t[8], H[9];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            t[k] = ld_stream(tgt + k * ld + i);
+        rect_solve(t, R, H);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            st_stream(Hout + k * ld + i, H[k]);
+    }
+}
+
+}  // namespace aca
+
+using namespace aca;
+
+extern "C" aca_status aca_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int64_t ld, int32_t norm,
+                                void *stream)
+{
+    return dispatch_solve<kAca>(pts, H, flags, n, ld, norm, stream);
+}
+
+extern "C" aca_status sks_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int64_t ld, int32_t norm,
+                                void *stream)
+{
+    return dispatch_solve<kSks>(pts, H, flags, n, ld, norm, stream);
+}
+
+extern "C" aca_status aca_rect_solve(const float *tgt, float x0, float y0, float w, float r, float *H, int64_t n,
+                                     int64_t ld, void *stream)
+{
+    if (n < 0 || ld < n)
+        return set_error(ACA_ERR_INVALID_ARG, "aca_rect_solve: need 0 <= n <= ld");
+    if (!(w > 0) || !(r > 0))
+        return set_error(ACA_ERR_INVALID_ARG, "aca_rect_solve: width and aspect ratio must be > 0");
+    if (n == 0)
+        return ACA_OK;
+    if (!tgt || !H)
+        return set_error(ACA_ERR_INVALID_ARG, "aca_rect_solve: null tgt or H");
+    const Rect R{x0, y0, w, r};
+    const cudaStream_t st = as_stream(stream);
+    const int threads = 256;
+    if (ld % 4 == 0 && aligned16(tgt) && aligned16(H)) {
+        const int grid = resident_grid(rect_vec4_kernel, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
+        rect_vec4_kernel<<<grid, threads, 0, st>>>(tgt, R, H, n, ld);
+    } else {
+        const int grid = resident_grid(rect_scalar_kernel, threads, 0, (n + threads - 1) / threads);
+        rect_scalar_kernel<<<grid, threads, 0, st>>>(tgt, R, H, n, ld);
+    }
+    return check_launch("aca_rect_solve");
+}

@@ -1,0 +1,132 @@
+"""Parity of the batched solvers (aca_solve, sks_solve, aca_rect_solve) with
+the FP64 oracle, through the C ABI, on the seeded synthetic workloads."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from paper_2402_18008_gb300 import _lib, api
+from tests.gpu_util import H_TOL, cuda, planes_to_rows, unit_aligned_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(pts_np, n, ld, norm=0, solver="aca", flags=False, sentinel=12345.0):
+    pts = torch.zeros((16, ld), dtype=torch.float32, device="cuda")
+    pts[:, :n] = cuda(pts_np[:, :n])
+    H = torch.full((9, ld), sentinel, dtype=torch.float32, device="cuda")
+    fl = torch.full((ld,), 0xEE, dtype=torch.uint8, device="cuda") if flags else None
+    (_lib.aca_solve if solver == "aca" else _lib.sks_solve)(pts, H, fl, n=n, norm=norm)
+    torch.cuda.synchronize()
+    return H, fl
+
+
+def test_aca_config0_parity_within_1e4():
+    ms = workloads.minimal_sets(4096, seed=0)
+    H, _ = _solve(ms.pts, 4096, 4096)
+    err = unit_aligned_err(planes_to_rows(H, 4096), oracle.aca(ms.pts))
+    print(f"aca config0: max {err.max():.3e} median {np.median(err):.3e}")
+    assert err.max() < H_TOL
+
+
+@pytest.mark.parametrize("n,ld", [(1, 1), (1, 4), (3, 4), (3, 3), (4, 4), (5, 8), (5, 5), (31, 32), (1023, 1024),
+                                  (1023, 1023), (4097, 4100), (4097, 4097)])
+def test_aca_ragged_sizes_and_untouched_tail(n, ld):
+    ms = workloads.minimal_sets(n, seed=5)
+    H, _ = _solve(ms.pts, n, ld)
+    err = unit_aligned_err(planes_to_rows(H, n), oracle.aca(ms.pts))
+    assert err.max() < H_TOL
+    if ld > n:
+        assert torch.all(H[:, n:] == 12345.0)
+
+
+def test_vector_and_scalar_paths_agree_bitwise():
+    n = 1000
+    ms = workloads.minimal_sets(n, seed=6)
+    H4, _ = _solve(ms.pts, n, 1000)          # ld % 4 == 0 -> float4 path
+    H1, _ = _solve(ms.pts, n, 1001)          # ld odd -> scalar path
+    assert torch.equal(H4[:, :n], H1[:, :n])
+    # misaligned base pointer also takes the scalar path
+    pts = torch.zeros((16, 1025), dtype=torch.float32, device="cuda")
+    pts[:, 1:1 + n] = cuda(ms.pts)
+    H = torch.empty((9, 1025), dtype=torch.float32, device="cuda")
+    _lib.aca_solve(pts[:, 1:], H[:, 1:], None, n=n)
+    torch.cuda.synchronize()
+    assert torch.equal(H[:, 1:1 + n], H4[:, :n])
+
+
+def test_norm_modes():
+    n = 4096
+    ms = workloads.minimal_sets(n, seed=0)
+    ref = oracle.aca(ms.pts)
+    H33, _ = _solve(ms.pts, n, n, norm=_lib.ACA_NORM_H33)
+    h = planes_to_rows(H33, n)
+    assert np.all(h[:, 8] == 1.0)
+    assert unit_aligned_err(h, ref).max() < H_TOL
+    Hf, _ = _solve(ms.pts, n, n, norm=_lib.ACA_NORM_FROB)
+    f = planes_to_rows(Hf, n)
+    assert np.allclose(np.linalg.norm(f, axis=1), 1.0, atol=1e-6)
+    rf = oracle.normalize_frob(ref)
+    assert np.abs(f - rf).max() < H_TOL       # sign convention identical, no alignment
+
+
+def test_flags_match_near_degenerate_labels_and_nonfinite():
+    n = 1 << 16
+    ms = workloads.minimal_sets(n, seed=7, degenerate_frac=0.01)
+    _, fl = _solve(ms.pts, n, n, flags=True)
+    f = fl.cpu().numpy()
+    assert np.array_equal((f & 1) > 0, ms.near_degenerate)
+    assert not np.any(f[~ms.near_degenerate] & 0x6)
+    assert not np.any(f & 8)
+    bad = ms.pts[:, :8].copy()
+    bad[3, 2] = np.nan
+    bad[12, 5] = np.inf
+    _, fl2 = _solve(bad, 8, 8, flags=True)
+    f2 = fl2.cpu().numpy()
+    assert f2[2] & 8 and f2[5] & 8 and not f2[0] & 8
+
+
+def test_flag_tail_bytes_untouched():
+    ms = workloads.minimal_sets(5, seed=8)
+    _, fl = _solve(ms.pts, 5, 8, flags=True)
+    assert torch.all(fl[5:] == 0xEE)
+
+
+def test_sks_config0_parity():
+    ms = workloads.minimal_sets(4096, seed=0)
+    H, _ = _solve(ms.pts, 4096, 4096, solver="sks")
+    err = unit_aligned_err(planes_to_rows(H, 4096), oracle.sks(ms.pts))
+    print(f"sks config0: max {err.max():.3e} median {np.median(err):.3e} >1e-4: {(err > 1e-4).sum()}")
+    assert np.median(err) < 1e-5
+    assert err.max() < 5e-3
+
+
+def test_rect_solve_matches_eq42_and_general_aca():
+    B = 65536
+    rb = workloads.rect_batch(B, seed=0)
+    tgt = cuda(rb.tgt)
+    H = torch.empty((9, B), dtype=torch.float32, device="cuda")
+    _lib.aca_rect_solve(tgt, rb.rect, H)
+    torch.cuda.synchronize()
+    h = planes_to_rows(H, B)
+    ref = oracle.aca_rect(rb.tgt, rb.rect)
+    err = unit_aligned_err(h, ref)
+    print(f"rect: max {err.max():.3e}")
+    assert err.max() < H_TOL
+    # unnormalised: same sign and scale as Eq. 42 (relative to |H|)
+    rel = np.abs(h - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert rel.max() < 1e-3
+    pts = np.concatenate([np.repeat(rb.src_corners.reshape(8, 1), 64, axis=1), rb.tgt[:, :64]], axis=0)
+    assert unit_aligned_err(h[:64], oracle.aca(pts)).max() < H_TOL
+
+
+def test_api_solve_and_layout_helpers():
+    ms = workloads.minimal_sets(64, seed=9)
+    s = oracle.sets_aos(ms.pts)
+    src = torch.tensor(s[:, :8].reshape(64, 4, 2), dtype=torch.float32, device="cuda")
+    tgt = torch.tensor(s[:, 8:].reshape(64, 4, 2), dtype=torch.float32, device="cuda")
+    pts = api.to_planes(src, tgt, ld=64)
+    H, fl = api.solve(pts, norm=_lib.ACA_NORM_FROB, with_flags=True)
+    M = api.planes_to_mats(H, 64).cpu().numpy().reshape(64, 9)
+    assert np.abs(M - oracle.normalize_frob(oracle.aca(ms.pts))).max() < H_TOL

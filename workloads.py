@@ -132,8 +132,14 @@ class MinimalSets:
     H_true: np.ndarray     # float64 (n, 3, 3)
 
 
+def _chunk_job(args):
+    seed, c, frac = args
+    sx, sy, tx, ty, nr, H = _chunk_sets(seed, c, frac)
+    return (np.concatenate([sx, sy, tx, ty], axis=1).astype(np.float32), nr, H)
+
+
 def minimal_sets(n: int, seed: int = 0, degenerate_frac: float = 0.0, ld: int | None = None,
-                 keep_truth: bool = True) -> MinimalSets:
+                 keep_truth: bool = True, workers: int = 1) -> MinimalSets:
     """n minimal 4-point sets: source U[0,640]x[0,480], target = H(source).
 
     Sets in which any triple of the 4 points (on either side) is within 5 px
@@ -147,20 +153,32 @@ def minimal_sets(n: int, seed: int = 0, degenerate_frac: float = 0.0, ld: int | 
     pts = np.zeros((16, ld), dtype=np.float32)
     near = np.zeros(n, dtype=bool)
     H_true = np.zeros((n, 3, 3)) if keep_truth else np.zeros((0, 3, 3))
-    for c in range((n + CHUNK - 1) // CHUNK):
+    nchunks = (n + CHUNK - 1) // CHUNK
+    jobs = [(seed, c, degenerate_frac) for c in range(nchunks)]
+    if workers > 1 and nchunks > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, nchunks)) as pool:
+            results = pool.imap(_chunk_job, jobs)
+            _fill(results, n, pts, near, H_true, keep_truth)
+    else:
+        _fill(map(_chunk_job, jobs), n, pts, near, H_true, keep_truth)
+    return MinimalSets(pts=pts, n=n, near_degenerate=near, H_true=H_true)
+
+
+def _fill(results, n, pts, near, H_true, keep_truth):
+    # columns of a chunk: src x (4), src y (4), tgt x (4), tgt y (4)
+    for c, (cols, nr, H) in enumerate(results):
         lo = c * CHUNK
         hi = min(n, lo + CHUNK)
         k = hi - lo
-        sx, sy, tx, ty, nr, H = _chunk_sets(seed, c, degenerate_frac)
         for pnt in range(4):
-            pts[2 * pnt, lo:hi] = sx[:k, pnt]
-            pts[2 * pnt + 1, lo:hi] = sy[:k, pnt]
-            pts[8 + 2 * pnt, lo:hi] = tx[:k, pnt]
-            pts[8 + 2 * pnt + 1, lo:hi] = ty[:k, pnt]
+            pts[2 * pnt, lo:hi] = cols[:k, pnt]
+            pts[2 * pnt + 1, lo:hi] = cols[:k, 4 + pnt]
+            pts[8 + 2 * pnt, lo:hi] = cols[:k, 8 + pnt]
+            pts[8 + 2 * pnt + 1, lo:hi] = cols[:k, 12 + pnt]
         near[lo:hi] = nr[:k]
         if keep_truth:
             H_true[lo:hi] = H[:k]
-    return MinimalSets(pts=pts, n=n, near_degenerate=near, H_true=H_true)
 
 
 # --------------------------------------------------------------------------
