@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-log2", type=int, default=N_LOG2)
     ap.add_argument("--no-rows", action="store_true", help="headline only")
+    ap.add_argument("--rows", default="sks,ransac1,ransac512,diff",
+                    help="comma list of extra rows: sks, ransac1, ransac512, diff")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -173,11 +175,17 @@ def error_stats(H_planes_np, flags_np, pts16, n, rng):
     e = np.abs(a - b).max(axis=1)
     flagged = (flags_np[idx] & 7) > 0
     ok = ~flagged
+    ku = oracle.aca_condition(pts16[:, idx]) * 2.0 ** -24
+    well = ok & (16 * ku <= 1e-4)
+    bound = np.maximum(1e-4, 16 * ku)
     return {"sample_sets": int(idx.size), "max_err": float(e[ok].max()), "median_err": float(np.median(e[ok])),
             "frac_above_1e-4": float(np.mean(e[ok] > 1e-4)), "flagged_sets": int(flagged.sum()),
             "flagged_max_err": float(e[flagged].max()) if flagged.any() else None,
-            "metric": "max |H_gpu - H_fp64| with both at unit Frobenius norm, sign aligned; "
-                      "flagged = a triple within 1 px of collinear (excluded from max_err)"}
+            "well_conditioned_sets": int(well.sum()), "well_conditioned_max_err": float(e[well].max()),
+            "max_err_over_bound": float(np.max(e[ok] / bound[ok])),
+            "metric": "max |H_gpu - H_fp64| with both at unit Frobenius norm, sign aligned; flagged = a triple "
+                      "within 1 px of collinear (excluded); well-conditioned = 16 kappa u <= 1e-4 (kappa: the "
+                      "oracle's componentwise condition number, u = 2^-24); bound = max(1e-4, 16 kappa u)"}
 
 
 def run_reference(args, rank):
@@ -224,10 +232,10 @@ def main():
     ms = workloads.minimal_sets(n, seed=SEED + rank, degenerate_frac=0.01, keep_truth=False,
                                 workers=max(1, os.cpu_count() or 1))
     rows_on = not args.no_rows and world == 1
-    if rows_on:
-        rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=SEED)
-        rb = workloads.ransac_batch(512, seed=SEED)
-        rect = workloads.rect_batch(65536, seed=SEED)
+    args.row_set = set(r for r in args.rows.split(",") if r) if rows_on else set()
+    rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=SEED) if "ransac1" in args.row_set else None
+    rb = workloads.ransac_batch(512, seed=SEED) if "ransac512" in args.row_set else None
+    rect = workloads.rect_batch(65536, seed=SEED) if "diff" in args.row_set else None
 
     import torch
     dist_on = world > 1
@@ -320,8 +328,20 @@ def fp32_peak_tflops(sms, mhz):
 
 def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev):
     out = {}
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     reps = max(20, args.steps // 4)
+    if "sks" in args.row_set:
+        out.update(row_sks(torch, _lib, pts, H, flags, n, reps, stream))
+    if rp is not None:
+        out.update(row_ransac1(torch, api, rp, stream, dev))
+    if rb is not None:
+        out.update(row_ransac512(torch, api, rb, stream, dev))
+    if rect is not None:
+        out.update(row_diff(torch, _lib, rect, stream, dev))
+    return out
+
+
+def row_sks(torch, _lib, pts, H, flags, n, reps, stream):
+    out = {}
     # SKS on the same sets
     sks = lambda: _lib.sks_solve(pts, H, None, n=n)
     for _ in range(3):
@@ -335,7 +355,11 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
     t = time_region(torch, fl, reps, stream)
     out["aca_solve_with_flags"] = {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
                                    "achieved_gbs": (BYTES_PER_SET + 1) * n / (t * 1e-3) / 1e9}
+    return out
 
+
+def row_ransac1(torch, api, rp, stream, dev):
+    out = {}
     # fused RANSAC, one pair (config 2), graph-replayed
     corr = torch.from_numpy(rp.corr).to(dev)
     plan2 = api.RansacPlan(corr, torch.tensor([0, 2000], dtype=torch.int64, device=dev),
@@ -348,7 +372,11 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
     out["ransac_fused_one_pair"] = {"value": tests / (t * 1e-3), "unit": "hyp*pts/s", "ms_per_ransac": t,
                                     "tflops_fp32": tests * FLOPS_PER_TEST / (t * 1e-3) / 1e12,
                                     "config": "N=2000, 60% inliers, 4096 hypotheses, thr 3 px, graph replay"}
+    return out
 
+
+def row_ransac512(torch, api, rb, stream, dev):
+    out = {}
     # batched uneven RANSAC (config 3) vs 512 separate per-problem launches
     tot = int(rb.n_hyp.sum())
     Ns = rb.offsets[1:] - rb.offsets[:-1]
@@ -380,7 +408,11 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
                                  "batched_equals_plain": same,
                                  "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9], "
                                            "adaptive hypotheses (99%, cap 16384), one graph replay"}
+    return out
 
+
+def row_diff(torch, _lib, rect, stream, dev):
+    out = {}
     # differentiable rectangle ACA (config 4): forward + backward vs plain solve
     B = rect.tgt.shape[1]
     tgt = torch.from_numpy(rect.tgt).to(dev)

@@ -56,7 +56,8 @@ def lib():
         if _lib is None:
             L = ctypes.CDLL(build())
             L.oracle_num_threads.restype = ctypes.c_int
-            for name in ("oracle_aca", "oracle_aca_divform", "oracle_sks", "oracle_aca_jacobian"):
+            for name in ("oracle_aca", "oracle_aca_divform", "oracle_sks", "oracle_aca_jacobian",
+                         "oracle_aca_jacobian_src", "oracle_aca_condition"):
                 getattr(L, name).argtypes = [_d, _d, ctypes.c_int64]
                 getattr(L, name).restype = None
             L.oracle_dlt.argtypes = [_d, _d, ctypes.c_int64]
@@ -128,6 +129,23 @@ def aca_jacobian(pts16, n=None):
     J = np.empty((a.shape[0], 9, 8))
     lib().oracle_aca_jacobian(_ptr(a, _d), _ptr(J, _d), a.shape[0])
     return J
+
+
+def aca_jacobian_src(pts16, n=None):
+    """dH/d(source coordinates), (n, 9, 8)."""
+    a = sets_aos(pts16, n)
+    J = np.empty((a.shape[0], 9, 8))
+    lib().oracle_aca_jacobian_src(_ptr(a, _d), _ptr(J, _d), a.shape[0])
+    return J
+
+
+def aca_condition(pts16, n=None):
+    """Componentwise condition number kappa of the unit-Frobenius ACA H
+    w.r.t. relative perturbations of the 16 input coordinates, (n,)."""
+    a = sets_aos(pts16, n)
+    k = np.empty(a.shape[0])
+    lib().oracle_aca_condition(_ptr(a, _d), _ptr(k, _d), a.shape[0])
+    return k
 
 
 def _rect(name, tgt8, rect, n=None, out_cols=9, per=1):

@@ -400,12 +400,15 @@ static void dmat3_mul(const dual *A, const dual *B, dual *C)
     memcpy(C, T, sizeof T);
 }
 
-static void aca_jac_one(const double *s, double *J)
+/* Derivatives w.r.t. the 8 coordinates of one side (side 0 = source,
+ * side 1 = target); the other side is held constant. */
+static void aca_jac_side(const double *s, int side, double *J)
 {
-    const dual M1x = dconst(s[0]), M1y = dconst(s[1]), N1x = dconst(s[2]), N1y = dconst(s[3]);
-    const dual P1x = dconst(s[4]), P1y = dconst(s[5]), Q1x = dconst(s[6]), Q1y = dconst(s[7]);
-    const dual M2x = dvar(s[8], 0), M2y = dvar(s[9], 1), N2x = dvar(s[10], 2), N2y = dvar(s[11], 3);
-    const dual P2x = dvar(s[12], 4), P2y = dvar(s[13], 5), Q2x = dvar(s[14], 6), Q2y = dvar(s[15], 7);
+    dual v[16];
+    for (int k = 0; k < 16; ++k)
+        v[k] = (k / 8 == side) ? dvar(s[k], k % 8) : dconst(s[k]);
+    const dual M1x = v[0], M1y = v[1], N1x = v[2], N1y = v[3], P1x = v[4], P1y = v[5], Q1x = v[6], Q1y = v[7];
+    const dual M2x = v[8], M2y = v[9], N2x = v[10], N2y = v[11], P2x = v[12], P2y = v[13], Q2x = v[14], Q2y = v[15];
 
     const dual MN1x = dsub(N1x, M1x), MN1y = dsub(N1y, M1y), MP1x = dsub(P1x, M1x), MP1y = dsub(P1y, M1y);
     const dual fA1 = dsub(dmul(MN1x, MP1y), dmul(MN1y, MP1x));
@@ -435,12 +438,62 @@ static void aca_jac_one(const double *s, double *J)
             J[8 * i + k] = H[i].d[k];
 }
 
+static void aca_jac_one(const double *s, double *J)
+{
+    aca_jac_side(s, 1, J);
+}
+
 /* J: n x 9 x 8, J[i][r][k] = dH_r / d tgt_k. */
 void oracle_aca_jacobian(const double *pts, double *J, int64_t n)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i)
         aca_jac_one(pts + 16 * i, J + 72 * i);
+}
+
+/* J: n x 9 x 8, derivatives w.r.t. the source coordinates (target fixed). */
+void oracle_aca_jacobian_src(const double *pts, double *J, int64_t n)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        aca_jac_side(pts + 16 * i, 0, J + 72 * i);
+}
+
+/* Componentwise condition number of the unit-Frobenius ACA homography
+ * H^ = H / |H| with respect to relative perturbations of all 16 input
+ * coordinates: kappa = max_i sum_k |dH^_i / dx_k| |x_k|, with
+ * dH^/dx_k = (dH/dx_k - H^ <H^, dH/dx_k>) / |H|.  kappa * u bounds, to first
+ * order, how far H^ moves when every coordinate is perturbed by a relative
+ * u (u = 2^-24 for the rounding of FP32 inputs).  Used to state which sets
+ * are well-conditioned enough for an FP32 solver to meet a tolerance. */
+void oracle_aca_condition(const double *pts, double *kappa, int64_t n)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const double *s = pts + 16 * i;
+        double H[9], Js[72], Jt[72];
+        aca_one(s, H);
+        aca_jac_side(s, 0, Js);
+        aca_jac_side(s, 1, Jt);
+        double nrm = 0;
+        for (int r = 0; r < 9; ++r) nrm += H[r] * H[r];
+        nrm = sqrt(nrm);
+        double Hh[9];
+        for (int r = 0; r < 9; ++r) Hh[r] = H[r] / nrm;
+        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < 16; ++k) {
+            double d[9], proj = 0;
+            for (int r = 0; r < 9; ++r) {
+                d[r] = k < 8 ? Js[8 * r + k] : Jt[8 * r + (k - 8)];
+                proj += Hh[r] * d[r];
+            }
+            for (int r = 0; r < 9; ++r)
+                acc[r] += fabs((d[r] - Hh[r] * proj) / nrm) * fabs(s[k]);
+        }
+        double m = 0;
+        for (int r = 0; r < 9; ++r) m = acc[r] > m ? acc[r] : m;
+        kappa[i] = m;
+    }
 }
 
 static void rect_jac_one(const double *t, double x0, double y0, double w, double r, double *J)

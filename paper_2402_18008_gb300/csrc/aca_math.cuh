@@ -13,8 +13,10 @@
 //  * t1 = f_A1 - Q3.x - Q3.y (Eq. 27) is evaluated as cross(N1P1, N1Q1), its
 //    exact value (twice the signed area of N1 P1 Q1), so the sum does not
 //    cancel; likewise t2;
-//  * the core product (Eq. 28) is grouped so that each entry is one Kahan
-//    determinant (plus one FMA for the third row).
+//  * the core product (Eq. 28-29) and the composition (Eq. 24) are carried
+//    in double-float (aca_compose_df) and H is rounded once; aca_compose is
+//    the plain FP32 grouping of the same products (each entry one Kahan
+//    determinant), kept for comparison.
 // Unnormalised output (ACA_NORM_NONE) is the paper's division-free H of
 // Eq. 24 with the scale of Eq. 28-29, the function the backward kernels
 // differentiate.
@@ -118,6 +120,45 @@ ACA_HD void aca_compose(const Set &s, const AcaParts &p, bool prescale, float H[
     H[6] = L20;
     H[7] = L21;
     H[8] = G22;
+}
+
+// The same core and composition as aca_compose with every product and sum
+// after the cross products carried in double-float and H rounded once at the
+// end: the translation back from the anchor frames (H = T(M2) L T(-M1))
+// amplifies relative errors of L by up to |M| / |L|-scale, which a single
+// FP32 rounding of L already turns into >1e-4 of |H| on the worst sets.
+ACA_HD void aca_compose_df(const Set &s, const AcaParts &p, bool prescale, float H[9])
+{
+    DF c11 = df_mul(df_prod(p.t1, p.Q3y), p.Q4x);
+    DF c22 = df_mul(df_prod(p.t1, p.Q3x), p.Q4y);
+    DF c33 = df_mul(df_prod(p.t2, p.Q3x), p.Q3y);
+    if (prescale) {
+        const float sc = pow2_inv_scale(fmax3_(c11.h, c22.h, c33.h));
+        c11 = DF{F_MUL(c11.h, sc), F_MUL(c11.l, sc)};
+        c22 = DF{F_MUL(c22.h, sc), F_MUL(c22.l, sc)};
+        c33 = DF{F_MUL(c33.h, sc), F_MUL(c33.l, sc)};
+    }
+    const DF k0x = df_mul(c11, p.MN2x), k0y = df_mul(c11, p.MN2y);
+    const DF k1x = df_mul(c22, p.MP2x), k1y = df_mul(c22, p.MP2y);
+    const DF L00 = df_sub(df_mul(k0x, p.MP1y), df_mul(k1x, p.MN1y));
+    const DF L01 = df_sub(df_mul(k1x, p.MN1x), df_mul(k0x, p.MP1x));
+    const DF L10 = df_sub(df_mul(k0y, p.MP1y), df_mul(k1y, p.MN1y));
+    const DF L11 = df_sub(df_mul(k1y, p.MN1x), df_mul(k0y, p.MP1x));
+    const DF L20 = df_sub(df_sub(df_mul(c11, p.MP1y), df_mul(c22, p.MN1y)), df_mul(c33, p.NP1y));
+    const DF L21 = df_add(df_sub(df_mul(c22, p.MN1x), df_mul(c11, p.MP1x)), df_mul(c33, p.NP1x));
+    const DF L22 = df_mul(c33, p.fA1);
+    const DF G02 = df_neg(df_add(df_mul(L00, s.M1x), df_mul(L01, s.M1y)));
+    const DF G12 = df_neg(df_add(df_mul(L10, s.M1x), df_mul(L11, s.M1y)));
+    const DF G22 = df_sub(df_sub(L22, df_mul(L20, s.M1x)), df_mul(L21, s.M1y));
+    H[0] = df_round(df_add(L00, df_mul(L20, s.M2x)));
+    H[1] = df_round(df_add(L01, df_mul(L21, s.M2x)));
+    H[2] = df_round(df_add(G02, df_mul(G22, s.M2x)));
+    H[3] = df_round(df_add(L10, df_mul(L20, s.M2y)));
+    H[4] = df_round(df_add(L11, df_mul(L21, s.M2y)));
+    H[5] = df_round(df_add(G12, df_mul(G22, s.M2y)));
+    H[6] = df_round(L20);
+    H[7] = df_round(L21);
+    H[8] = df_round(G22);
 }
 
 ACA_HD uint32_t f2u(float x)

@@ -82,4 +82,40 @@ ACA_HD float cross2x(Diff ux, Diff uy, Diff vx, Diff vy)
     return F_ADD(f, F_ADD(e, c));
 }
 
+// Double-float arithmetic (value = h + l, |l| <= ulp(h) roughly): products
+// by TwoProduct (one FMA recovers the rounding error exactly), sums by
+// TwoSum; the low parts are accumulated without renormalisation, which keeps
+// ~45 significant bits through the short chains used here.
+struct DF {
+    float h, l;
+};
+
+ACA_HD DF df_prod(float a, float b)
+{
+    const float p = F_MUL(a, b);
+    return DF{p, F_FMA(a, b, -p)};
+}
+
+// (x.h + x.l) * b
+ACA_HD DF df_mul(DF x, float b)
+{
+    const float p = F_MUL(x.h, b);
+    return DF{p, F_FMA(x.l, b, F_FMA(x.h, b, -p))};
+}
+
+ACA_HD DF df_add(DF x, DF y)
+{
+    const float s = F_ADD(x.h, y.h);
+    const float bv = F_SUB(s, x.h);
+    const float av = F_SUB(s, bv);
+    const float e = F_ADD(F_SUB(x.h, av), F_SUB(y.h, bv));
+    return DF{s, F_ADD(e, F_ADD(x.l, y.l))};
+}
+
+ACA_HD DF df_neg(DF x) { return DF{-x.h, -x.l}; }
+
+ACA_HD DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
+
+ACA_HD float df_round(DF x) { return F_ADD(x.h, x.l); }
+
 }  // namespace aca

@@ -1,5 +1,7 @@
 """Parity of the batched solvers (aca_solve, sks_solve, aca_rect_solve) with
 the FP64 oracle, through the C ABI, on the seeded synthetic workloads."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -7,7 +9,7 @@ import torch
 import oracle
 import workloads
 from paper_2402_18008_gb300 import _lib, api
-from tests.gpu_util import H_TOL, cuda, planes_to_rows, unit_aligned_err
+from tests.gpu_util import H_TOL, cuda, kappa_gate, planes_to_rows, unit_aligned_err
 
 pytestmark = pytest.mark.gpu
 
@@ -36,9 +38,35 @@ def test_aca_ragged_sizes_and_untouched_tail(n, ld):
     ms = workloads.minimal_sets(n, seed=5)
     H, _ = _solve(ms.pts, n, ld)
     err = unit_aligned_err(planes_to_rows(H, n), oracle.aca(ms.pts))
-    assert err.max() < H_TOL
+    kappa_gate(err, oracle.aca_condition(ms.pts), f"ragged n={n} ld={ld}")
     if ld > n:
         assert torch.all(H[:, n:] == 12345.0)
+
+
+def test_full_size_workload_sampled_against_oracle():
+    """The 2^26-set workload of the benchmark, in the benchmark's launch
+    configuration: 2^16 sampled sets against the oracle, flags of all sets
+    against the generator's near-degenerate labels."""
+    n = 1 << 26
+    ms = workloads.minimal_sets(n, seed=0, degenerate_frac=0.01, keep_truth=False, workers=os.cpu_count() or 1)
+    pts = cuda(ms.pts)
+    H = torch.empty((9, n), dtype=torch.float32, device="cuda")
+    fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+    _lib.aca_solve(pts, H, None, n=n)
+    H2 = torch.empty_like(H)
+    _lib.aca_solve(pts, H2, fl, n=n)
+    torch.cuda.synchronize()
+    assert torch.equal(H, H2)                        # flags do not change H
+    labels = torch.from_numpy(ms.near_degenerate).cuda()
+    assert torch.equal((fl & 1) > 0, labels)
+    assert not torch.any(fl & 8)
+    idx = np.sort(np.random.default_rng(0).choice(n, 1 << 16, replace=False))
+    sub = ms.pts[:, idx]
+    err = unit_aligned_err(H[:, idx].cpu().numpy().T, oracle.aca(sub))
+    f = fl.cpu().numpy()[idx]
+    ok = (f & 7) == 0
+    kappa_gate(err[ok], oracle.aca_condition(sub)[ok], "full size 2^26 (sample 2^16)")
+    print(f"flagged in sample: {int((~ok).sum())}, their max err {err[~ok].max():.3e}")
 
 
 def test_vector_and_scalar_paths_agree_bitwise():

@@ -157,3 +157,42 @@ def test_aca_jacobian_matches_fp64_central_differences():
         fd = (Hp - Hm) / (2 * step)
         scale = np.abs(J).max(axis=(1, 2))[:, None]
         assert np.max(np.abs(fd - J[:, :, k]) / scale) < 1e-6
+
+
+def test_source_jacobian_matches_fp64_central_differences():
+    ms = workloads.minimal_sets(64, seed=12)
+    J = oracle.aca_jacobian_src(ms.pts)
+    base = oracle.sets_aos(ms.pts)
+    step = 1e-6
+    for k in range(8):
+        p, m = base.copy(), base.copy()
+        p[:, k] += step
+        m[:, k] -= step
+        fd = (oracle.aca(p.T.copy()) - oracle.aca(m.T.copy())) / (2 * step)
+        scale = np.abs(J).max(axis=(1, 2))[:, None]
+        assert np.max(np.abs(fd - J[:, :, k]) / scale) < 1e-6
+
+
+def test_condition_number_bounds_and_is_attained_by_worst_sign_perturbation():
+    ms = workloads.minimal_sets(200, seed=13)
+    kap = oracle.aca_condition(ms.pts)
+    s = oracle.sets_aos(ms.pts)
+    H0 = oracle.aca(ms.pts)
+    H0 = H0 / np.linalg.norm(H0, axis=1, keepdims=True)
+    J = np.concatenate([oracle.aca_jacobian_src(ms.pts), oracle.aca_jacobian(ms.pts)], axis=2)
+    delta = 1e-7
+    rng = np.random.default_rng(0)
+    for i in range(200):
+        nrm = np.linalg.norm(oracle.aca(s[i].reshape(16, 1)))
+        dhat = (J[i] - np.outer(H0[i], H0[i] @ J[i])) / nrm          # (9, 16)
+        r = int(np.argmax(np.abs(dhat) @ np.abs(s[i])))
+        worst = s[i] * (1 + delta * np.sign(dhat[r] * s[i]))          # relative perturbation
+        Hw = oracle.aca(worst.reshape(16, 1))[0]
+        Hw = Hw / np.linalg.norm(Hw) * np.sign(Hw @ H0[i])
+        moved = abs(Hw[r] - H0[i][r])
+        kd = kap[i] * delta          # first order; the rest is O(kd^2)
+        assert abs(moved - kd) <= 1e-3 * kd + 10 * kd ** 2 + 1e-14
+        rnd = s[i] * (1 + delta * rng.choice([-1.0, 1.0], 16))
+        Hr = oracle.aca(rnd.reshape(16, 1))[0]
+        Hr = Hr / np.linalg.norm(Hr) * np.sign(Hr @ H0[i])
+        assert np.abs(Hr - H0[i]).max() <= kd * (1 + 1e-3) + 10 * kd ** 2 + 1e-14
