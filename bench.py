@@ -361,16 +361,20 @@ def row_sks(torch, _lib, pts, H, flags, n, reps, stream):
 def row_ransac1(torch, api, rp, stream, dev):
     out = {}
     # fused RANSAC, one pair (config 2), graph-replayed
+    from paper_2402_18008_gb300 import autotune
     corr = torch.from_numpy(rp.corr).to(dev)
-    plan2 = api.RansacPlan(corr, torch.tensor([0, 2000], dtype=torch.int64, device=dev),
-                           torch.tensor([4096], dtype=torch.int32, device=dev), RANSAC_THR, SEED, 4096,
-                           tile_points=256, hyps_per_thread=1, block_warps=4).capture()
+    off2 = torch.tensor([0, 2000], dtype=torch.int64, device=dev)
+    k2 = torch.tensor([4096], dtype=torch.int32, device=dev)
+    make2 = lambda **kw: api.RansacPlan(corr, off2, k2, RANSAC_THR, SEED, 4096, **kw)
+    best2, _ = autotune.tune(make2, 1, 2000, 4096, device=dev)
+    plan2 = make2(**best2).capture()
     for _ in range(5):
         plan2.replay()
     t = time_region(torch, plan2.replay, 200, stream)
     tests = 4096 * 2000
     out["ransac_fused_one_pair"] = {"value": tests / (t * 1e-3), "unit": "hyp*pts/s", "ms_per_ransac": t,
                                     "tflops_fp32": tests * FLOPS_PER_TEST / (t * 1e-3) / 1e12,
+                                    "tuning": best2,
                                     "config": "N=2000, 60% inliers, 4096 hypotheses, thr 3 px, graph replay"}
     return out
 
@@ -384,7 +388,10 @@ def row_ransac512(torch, api, rb, stream, dev):
     corr3 = torch.from_numpy(rb.corr).to(dev)
     off3 = torch.from_numpy(rb.offsets).to(dev)
     k3 = torch.from_numpy(rb.n_hyp).to(dev)
-    plan3 = api.RansacPlan(corr3, off3, k3, RANSAC_THR, SEED, tot).capture()
+    from paper_2402_18008_gb300 import autotune
+    make3 = lambda **kw: api.RansacPlan(corr3, off3, k3, RANSAC_THR, SEED, tot, **kw)
+    best3, _ = autotune.tune(make3, len(rb.n_hyp), int(rb.offsets[-1]), tot, device=dev)
+    plan3 = make3(**best3).capture()
     for _ in range(3):
         plan3.replay()
     t3 = time_region(torch, plan3.replay, 20, stream)
@@ -405,7 +412,7 @@ def row_ransac512(torch, api, rb, stream, dev):
                                  "ms_512_plain_launches": tp, "speedup_vs_plain": tp / t3,
                                  "tflops_fp32": tests3 * FLOPS_PER_TEST / (t3 * 1e-3) / 1e12,
                                  "tests": tests3, "hypotheses": tot, "points": int(rb.offsets[-1]),
-                                 "batched_equals_plain": same,
+                                 "batched_equals_plain": same, "tuning": best3,
                                  "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9], "
                                            "adaptive hypotheses (99%, cap 16384), one graph replay"}
     return out

@@ -72,9 +72,11 @@ def lib():
             L.oracle_sample_degenerate.restype = ctypes.c_int
             L.oracle_normalize_frob.argtypes = [_d]
             L.oracle_score_problem.argtypes = [_f, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
-                                               ctypes.c_uint64, ctypes.c_uint32, _i32, _i32, ctypes.c_double]
+                                               ctypes.c_uint64, ctypes.c_uint32, _i32, _i32, ctypes.c_double,
+                                               ctypes.c_double]
             L.oracle_ransac.argtypes = [_f, _i64, _i32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
-                                        ctypes.c_uint32, _d, _i32, _i32, _i32, _i32, ctypes.c_double, _u8]
+                                        ctypes.c_uint32, _d, _i32, _i32, _i32, _i32, ctypes.c_double,
+                                        ctypes.c_double, _u8]
             _lib = L
     return _lib
 
@@ -201,18 +203,22 @@ def normalize_frob(H) -> np.ndarray:
     return H
 
 
-def score_problem(corr, n_hyp: int, thr: float, seed: int, prob: int = 0, band_px: float = 1e-4):
-    """Per-hypothesis counts (-1 = degenerate sample) and band counts."""
+def score_problem(corr, n_hyp: int, thr: float, seed: int, prob: int = 0, band_px: float = 1e-4,
+                  herr: float = 0.0):
+    """Per-hypothesis counts (-1 = degenerate sample) and band counts (see
+    oracle_score_problem: band_px plus, when herr > 0, the first-order
+    effect of an FP32-solver error of herr * kappa_h * 2^-24 + 2^-23 on H)."""
     c = np.ascontiguousarray(corr, dtype=np.float32)
     N = c.shape[0]
     cnt = np.empty(n_hyp, dtype=np.int32)
     band = np.empty(n_hyp, dtype=np.int32)
-    lib().oracle_score_problem(_ptr(c, _f), N, n_hyp, thr, seed, prob, _ptr(cnt, _i32), _ptr(band, _i32), band_px)
+    lib().oracle_score_problem(_ptr(c, _f), N, n_hyp, thr, seed, prob, _ptr(cnt, _i32), _ptr(band, _i32), band_px,
+                               herr)
     return cnt, band
 
 
 def ransac(corr, offsets, n_hyp, thr: float, seed: int, problem_base: int = 0, band_px: float = 1e-4,
-           want_counts: bool = True, want_mask: bool = False) -> dict:
+           want_counts: bool = True, want_mask: bool = False, herr: float = 0.0) -> dict:
     """Brute-force RANSAC over CSR problems; see oracle_ransac in oracle.c."""
     c = np.ascontiguousarray(corr, dtype=np.float32)
     off = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -227,6 +233,6 @@ def ransac(corr, offsets, n_hyp, thr: float, seed: int, problem_base: int = 0, b
     mask = np.empty(c.shape[0], dtype=np.uint8) if want_mask else None
     lib().oracle_ransac(_ptr(c, _f), _ptr(off, _i64), _ptr(k, _i32), P, thr, seed, problem_base,
                         _ptr(best_H, _d), _ptr(best_count, _i32), _ptr(best_hyp, _i32),
-                        _ptr(counts, _i32), _ptr(band, _i32), band_px, _ptr(mask, _u8))
+                        _ptr(counts, _i32), _ptr(band, _i32), band_px, herr, _ptr(mask, _u8))
     return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, hyp_counts=counts,
                 band_counts=band, inlier_mask=mask)

@@ -466,11 +466,18 @@ void oracle_aca_jacobian_src(const double *pts, double *J, int64_t n)
  * order, how far H^ moves when every coordinate is perturbed by a relative
  * u (u = 2^-24 for the rounding of FP32 inputs).  Used to state which sets
  * are well-conditioned enough for an FP32 solver to meet a tolerance. */
+static double aca_condition_one(const double *s);
+
 void oracle_aca_condition(const double *pts, double *kappa, int64_t n)
 {
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) {
-        const double *s = pts + 16 * i;
+    for (int64_t i = 0; i < n; ++i)
+        kappa[i] = aca_condition_one(pts + 16 * i);
+}
+
+static double aca_condition_one(const double *s)
+{
+    {
         double H[9], Js[72], Jt[72];
         aca_one(s, H);
         aca_jac_side(s, 0, Js);
@@ -492,7 +499,7 @@ void oracle_aca_condition(const double *pts, double *kappa, int64_t n)
         }
         double m = 0;
         for (int r = 0; r < 9; ++r) m = acc[r] > m ? acc[r] : m;
-        kappa[i] = m;
+        return m;
     }
 }
 
@@ -654,11 +661,40 @@ static int score_point(const double *H, const float *c, double thr, double *marg
     return r <= thr;
 }
 
+/* Ambiguity band of the RANSAC count parity.  An FP32 solver returns, at
+ * best, the exact H of inputs perturbed by about one FP32 rounding (the
+ * backward-stability reading of the solver gate, herr * 2^-24 relative per
+ * coordinate).  The band of point i under hypothesis h is therefore
+ * band_px + 2 * max_t |r_i(H_t) - r_i(H)| over BAND_TRIALS re-solves H_t of
+ * the minimal set with every coordinate scaled by (1 +- herr 2^-24), signs
+ * from a fixed hash of (h, t, coordinate).  A point whose exact residual is
+ * closer to the threshold than its band may legitimately be counted either
+ * way by an FP32 implementation. */
+#define BAND_TRIALS 6
+
+static double residual_of(const double *H, const float *c)
+{
+    const double x = c[0], y = c[1];
+    const double u = H[0] * x + H[1] * y + H[2];
+    const double v = H[3] * x + H[4] * y + H[5];
+    const double w = H[6] * x + H[7] * y + H[8];
+    if (w == 0) return INFINITY;
+    return hypot(c[2] - u / w, c[3] - v / w);
+}
+
+static uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+    return x;
+}
+
 /* Per-hypothesis inlier counts for one problem (N correspondences).
  * counts[h] = -1 for degenerate samples; band[h] (nullable) = number of
- * points with | ||r|| - thr | < band_px under that hypothesis. */
+ * points whose exact residual lies within the ambiguity band of the
+ * threshold (band_px alone when herr = 0, see the comment above
+ * BAND_TRIALS). */
 void oracle_score_problem(const float *corr, int64_t N, int32_t n_hyp, double thr, uint64_t seed,
-                          uint32_t prob, int32_t *counts, int32_t *band, double band_px)
+                          uint32_t prob, int32_t *counts, int32_t *band, double band_px, double herr)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int32_t h = 0; h < n_hyp; ++h) {
@@ -684,11 +720,29 @@ void oracle_score_problem(const float *corr, int64_t N, int32_t n_hyp, double th
         }
         double H[9];
         aca_one(s, H);
+        double Ht[BAND_TRIALS][9];
+        const int trials = (band && herr > 0) ? BAND_TRIALS : 0;
+        for (int t = 0; t < trials; ++t) {
+            double sp[16];
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t bit = mix32((uint32_t)h * 2654435761u ^ (uint32_t)(t * 16 + k) * 0x9E3779B9u ^ prob) & 1u;
+                sp[k] = s[k] * (1.0 + (bit ? 1.0 : -1.0) * herr * ldexp(1.0, -24));
+            }
+            aca_one(sp, Ht[t]);
+        }
         int32_t cnt = 0, nb = 0;
         for (int64_t i = 0; i < N; ++i) {
             double m;
             cnt += score_point(H, corr + 4 * i, thr, &m);
-            if (band && fabs(m) < band_px) ++nb;
+            if (band) {
+                double move = 0;
+                const double r0 = residual_of(H, corr + 4 * i);
+                for (int t = 0; t < trials; ++t) {
+                    const double d = fabs(residual_of(Ht[t], corr + 4 * i) - r0);
+                    move = d > move ? d : move;
+                }
+                if (!(fabs(m) >= band_px + 2.0 * move)) ++nb;   /* NaN (w = 0 or inf - inf) counts as ambiguous */
+            }
         }
         counts[h] = cnt;
         if (band) band[h] = nb;
@@ -704,7 +758,7 @@ void oracle_score_problem(const float *corr, int64_t N, int32_t n_hyp, double th
 void oracle_ransac(const float *corr, const int64_t *offsets, const int32_t *n_hyp, int32_t P, double thr,
                    uint64_t seed, uint32_t problem_base, double *best_H, int32_t *best_count,
                    int32_t *best_hyp, int32_t *hyp_counts, int32_t *band_counts, double band_px,
-                   uint8_t *inlier_mask)
+                   double herr, uint8_t *inlier_mask)
 {
     int64_t hoff = 0;
     for (int32_t p = 0; p < P; ++p) {
@@ -713,7 +767,7 @@ void oracle_ransac(const float *corr, const int64_t *offsets, const int32_t *n_h
         const int32_t k = n_hyp[p];
         int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * (k > 0 ? k : 1));
         int32_t *bnd = band_counts ? band_counts + hoff : NULL;
-        oracle_score_problem(c, N, k, thr, seed, problem_base + (uint32_t)p, cnt, bnd, band_px);
+        oracle_score_problem(c, N, k, thr, seed, problem_base + (uint32_t)p, cnt, bnd, band_px, herr);
         int32_t bh = -1, bc = -1;
         for (int32_t h = 0; h < k; ++h)
             if (cnt[h] > bc) {

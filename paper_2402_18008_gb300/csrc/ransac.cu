@@ -76,18 +76,70 @@ __device__ __forceinline__ bool make_hypothesis(const float4 *__restrict__ c, ui
 }
 
 // Forward transfer error test without division: with (u, v, w) = H (x, y, 1),
-// inlier iff w != 0 and (u - X w)^2 + (v - Y w)^2 <= (thr w)^2.
-__device__ __forceinline__ int inlier(const float H[9], float4 c, float thr)
+// inlier iff w != 0 and (X w - u)^2 + (Y w - v)^2 - thr^2 w^2 <= 0.
+// The hypothesis is kept as G = (-h11, -h12, -h13, -h21, -h22, -h23, h31,
+// h32, h33) and nthr2 = -thr^2 so that the test needs no negation:
+//   w = g6 x + g7 y + g8, -u = g0 x + g1 y + g2, -v = g3 x + g4 y + g5,
+//   du = X w - u, dv = Y w - v, e = du^2 + (dv^2 + (nthr2 w) w).
+// The same operations, in the same order, run lane-wise on f32x2 pairs in
+// the scoring loop (inlier2) and on scalars in the epilogue (inlier): packed
+// FP32 instructions round each lane exactly like the scalar ones, so counts
+// and masks agree bit for bit.
+__device__ __forceinline__ void to_test_form(float G[9], const float H[9])
 {
-    const float w = F_FMA(H[6], c.x, F_FMA(H[7], c.y, H[8]));
-    const float u = F_FMA(H[0], c.x, F_FMA(H[1], c.y, H[2]));
-    const float v = F_FMA(H[3], c.x, F_FMA(H[4], c.y, H[5]));
-    const float du = F_FMA(-c.z, w, u);
-    const float dv = F_FMA(-c.w, w, v);
-    const float r2 = F_FMA(du, du, F_MUL(dv, dv));
-    const float tw = F_MUL(thr, w);
-    const float d = F_FMA(tw, tw, -r2);
-    return (d >= 0.0f) & (w != 0.0f);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) G[i] = -H[i];
+    G[6] = H[6];
+    G[7] = H[7];
+    G[8] = H[8];
+}
+
+__device__ __forceinline__ int inlier(const float G[9], float4 c, float nthr2)
+{
+    const float w = F_FMA(G[6], c.x, F_FMA(G[7], c.y, G[8]));
+    const float nu = F_FMA(G[0], c.x, F_FMA(G[1], c.y, G[2]));
+    const float nv = F_FMA(G[3], c.x, F_FMA(G[4], c.y, G[5]));
+    const float du = F_FMA(c.z, w, nu);
+    const float dv = F_FMA(c.w, w, nv);
+    const float e = F_FMA(du, du, F_FMA(dv, dv, F_MUL(F_MUL(nthr2, w), w)));
+    return (e <= 0.0f) & (w != 0.0f);
+}
+
+// Packed FP32 pair operations (sm_100+ f32x2 instructions; one instruction
+// per pair, each lane rounded to nearest like the scalar operation).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// Two points (lane a, lane b) against one hypothesis given as broadcast pairs
+// g[i] = (G[i], G[i]); p = (x_a, x_b, y_a, y_b), q = (X_a, X_b, Y_a, Y_b).
+__device__ __forceinline__ int inlier2(const float2 g[9], float4 p, float4 q, float2 nthr2)
+{
+    const float2 x = make_float2(p.x, p.y), y = make_float2(p.z, p.w);
+    const float2 X = make_float2(q.x, q.y), Y = make_float2(q.z, q.w);
+    const float2 w = fma2(g[6], x, fma2(g[7], y, g[8]));
+    const float2 nu = fma2(g[0], x, fma2(g[1], y, g[2]));
+    const float2 nv = fma2(g[3], x, fma2(g[4], y, g[5]));
+    const float2 du = fma2(X, w, nu);
+    const float2 dv = fma2(Y, w, nv);
+    const float2 e = fma2(du, du, fma2(dv, dv, mul2(mul2(nthr2, w), w)));
+    return ((e.x <= 0.0f) & (w.x != 0.0f)) + ((e.y <= 0.0f) & (w.y != 0.0f));
 }
 
 struct Workspace {
@@ -230,18 +282,21 @@ __device__ int32_t find_problem(const int64_t *__restrict__ item_off, int32_t P,
 
 template <int HPT>
 __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restrict__ corr,
-                                                            const int64_t *__restrict__ offsets,
-                                                            const int32_t *__restrict__ n_hyp, int32_t P, float thr,
-                                                            uint64_t seed, uint32_t prob_base, int T, Workspace ws)
+                                                           const int64_t *__restrict__ offsets,
+                                                           const int32_t *__restrict__ n_hyp, int32_t P, float thr,
+                                                           uint64_t seed, uint32_t prob_base, int T, Workspace ws)
 {
     constexpr int HB = 32 * HPT;
     extern __shared__ float4 smem4[];
     const int W = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4 *tile = smem4;                                                   // [T]
+    float4 *tile = smem4;                                                   // [T/2][2]: point pairs
     float *Hs = reinterpret_cast<float *>(smem4 + T);                       // [HB][12]
     int32_t *red = reinterpret_cast<int32_t *>(Hs + HB * 12);               // [W][HB]
     __shared__ ItemInfo info;
+    const float nthr2s = -F_MUL(thr, thr);
+    const float2 nthr2 = make_float2(nthr2s, nthr2s);
+    const float nanv = __int_as_float(0x7fc00000);
 
     const int64_t total = ws.item_off[P];
     for (;;) {
@@ -284,9 +339,9 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
         const int64_t hbase = info.hbase;
         const float4 *cp = corr + info.base;
 
-        // hypotheses of this item -> shared memory
+        // hypotheses of this item -> shared memory (test form, see inlier)
         if ((int)threadIdx.x < HB) {
-            float H[9];
+            float H[9], G[9];
             const int t = threadIdx.x;
             bool valid = false;
             if (t < nh) {
@@ -298,35 +353,45 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
 #pragma unroll
                 for (int i = 0; i < 9; ++i) H[i] = 0.0f;   // scores nothing (w == 0)
             }
+            to_test_form(G, H);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Hs[t * 12 + i] = H[i];
+            for (int i = 0; i < 9; ++i) Hs[t * 12 + i] = G[i];
             Hs[t * 12 + 9] = valid ? 1.0f : 0.0f;
         }
-        // correspondence slice -> shared memory
-        for (int i = threadIdx.x; i < ni; i += blockDim.x)
-            tile[i] = cp[i0 + i];
+        // correspondence slice -> shared memory as interleaved pairs; an odd
+        // tail is padded with a NaN point (never an inlier)
+        const int npairs = (ni + 1) >> 1;
+        for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+            const float4 a = cp[i0 + 2 * q];
+            const float4 b = (2 * q + 1 < ni) ? cp[i0 + 2 * q + 1] : make_float4(nanv, nanv, nanv, nanv);
+            tile[2 * q] = make_float4(a.x, b.x, a.y, b.y);
+            tile[2 * q + 1] = make_float4(a.z, b.z, a.w, b.w);
+        }
         __syncthreads();
 
-        float h[HPT][9];
+        float2 g[HPT][9];
         int cnt[HPT];
 #pragma unroll
         for (int j = 0; j < HPT; ++j) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) h[j][i] = Hs[(lane + 32 * j) * 12 + i];
+            for (int i = 0; i < 9; ++i) {
+                const float v = Hs[(lane + 32 * j) * 12 + i];
+                g[j][i] = make_float2(v, v);
+            }
             cnt[j] = 0;
         }
-        int i = wid;
-        for (; i + 3 * W < ni; i += 4 * W) {
-            const float4 c0 = tile[i], c1 = tile[i + W], c2 = tile[i + 2 * W], c3 = tile[i + 3 * W];
+        int q = wid;
+        for (; q + W < npairs; q += 2 * W) {
+            const float4 p0 = tile[2 * q], q0 = tile[2 * q + 1];
+            const float4 p1 = tile[2 * (q + W)], q1 = tile[2 * (q + W) + 1];
 #pragma unroll
             for (int j = 0; j < HPT; ++j)
-                cnt[j] += inlier(h[j], c0, thr) + inlier(h[j], c1, thr) + inlier(h[j], c2, thr) +
-                          inlier(h[j], c3, thr);
+                cnt[j] += inlier2(g[j], p0, q0, nthr2) + inlier2(g[j], p1, q1, nthr2);
         }
-        for (; i < ni; i += W) {
-            const float4 c0 = tile[i];
+        for (; q < npairs; q += W) {
+            const float4 p0 = tile[2 * q], q0 = tile[2 * q + 1];
 #pragma unroll
-            for (int j = 0; j < HPT; ++j) cnt[j] += inlier(h[j], c0, thr);
+            for (int j = 0; j < HPT; ++j) cnt[j] += inlier2(g[j], p0, q0, nthr2);
         }
 #pragma unroll
         for (int j = 0; j < HPT; ++j) red[wid * HB + lane + 32 * j] = cnt[j];
@@ -396,12 +461,14 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
     }
     __syncthreads();
     if (mask) {
-        float H[9];
+        float H[9], G[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) H[i] = sH[i];
+        to_test_form(G, H);
+        const float nthr2 = -F_MUL(thr, thr);
         const bool any = s_best >= 0;
         for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
-            mask[base + i] = any ? (uint8_t)inlier(H, corr[base + i], thr) : (uint8_t)0;
+            mask[base + i] = any ? (uint8_t)inlier(G, corr[base + i], nthr2) : (uint8_t)0;
     }
 }
 
@@ -469,7 +536,7 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
         return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: block_warps must be in 1..16");
     if (HPT != 1 && HPT != 2 && HPT != 4)
         return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: hyps_per_thread must be 1, 2 or 4");
-    if (T < 32 || T > 8192 || T % 32 != 0)
+    if (T < 32 || T > 8192 || T % 32 != 0)   // even: the tile holds point pairs
         return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: tile_points must be a multiple of 32 in 32..8192");
     if (32 * HPT > 32 * W)
         return set_error(ACA_ERR_INVALID_ARG, "ransac_aca: need hyps_per_thread <= block_warps");

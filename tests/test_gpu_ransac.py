@@ -11,7 +11,8 @@ import workloads
 from paper_2402_18008_gb300 import _lib, api
 from tests.gpu_util import H_TOL, KAPPA_C, U32, cuda, unit_aligned_err
 
-BAND_PX = 1e-2
+BAND_PX = 1e-3
+HERR = KAPPA_C       # FP32 H within 16 kappa u of exact (the solver's gate)
 
 
 def _sample_kappa_u(corr, offsets, n_hyp, seed):
@@ -33,19 +34,17 @@ def _sample_kappa_u(corr, offsets, n_hyp, seed):
 
 
 def _count_gate(gc, oc, band, ku, label):
-    """Counts agree except for points within BAND_PX of the threshold; a
-    hypothesis whose minimal set is ill-conditioned for FP32 (KAPPA_C * kappa
-    * u > 1e-4: its H moves by more than 1e-4 under FP32 input rounding) may
-    differ further and is reported."""
+    """Counts agree except for points inside the oracle's ambiguity band:
+    |r - thr| < BAND_PX + e_h S_i, e_h = HERR kappa_h u + 2^-23 the FP32
+    error allowed on this hypothesis's H and S_i the first-order
+    sensitivity of point i's residual to H (oracle_score_problem)."""
     assert np.array_equal(gc < 0, oc < 0)
     d = np.abs(gc - oc)
     bad = d > band
-    ill = KAPPA_C * ku > 1e-4
     print(f"{label}: hyps {gc.size}, count mismatches {int(np.sum(d > 0))}, mismatched tests {int(d.sum())}, "
-          f"beyond the {BAND_PX} px band {int(bad.sum())} (ill-conditioned samples among them "
-          f"{int(np.sum(bad & ill))}, their kappa*u {ku[bad].tolist()[:8]})")
-    assert not np.any(bad & ~ill)
-    assert np.sum(bad) <= max(2, 0.01 * gc.size)
+          f"beyond the band {int(bad.sum())} (kappa*u there {ku[bad].tolist()[:8]}); "
+          f"ambiguous tests {int(band.sum())}")
+    assert not np.any(bad)
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +75,7 @@ def test_config2_counts_argmax_and_mask():
     rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=0)
     thr, seed, k = 3.0, 2024, 4096
     g = _np(_run(rp.corr, [0, 2000], [k], thr, seed))
-    o = oracle.ransac(rp.corr, [0, 2000], [k], thr, seed, band_px=BAND_PX)
+    o = oracle.ransac(rp.corr, [0, 2000], [k], thr, seed, band_px=BAND_PX, herr=HERR)
     gc, oc, band = g["hyp_counts"], o["hyp_counts"], o["band_counts"]
     _count_gate(gc, oc, band, _sample_kappa_u(rp.corr, [0, 2000], [k], seed), "config2")
     d = np.abs(gc - oc)
@@ -108,7 +107,7 @@ def test_edge_cases_small_and_degenerate_problems():
     offsets = [0, 3, 53, 353, 353, 357]      # 3 points, collinear, normal, empty, exactly 4 points
     n_hyp = [5, 64, 512, 3, 0]
     g = _np(_run(corr, offsets, n_hyp, 2.0, 5))
-    o = oracle.ransac(corr, offsets, n_hyp, 2.0, 5, band_px=BAND_PX)
+    o = oracle.ransac(corr, offsets, n_hyp, 2.0, 5, band_px=BAND_PX, herr=HERR)
     assert list(g["best_hyp"][[0, 1, 3, 4]]) == [-1, -1, -1, -1]
     assert list(g["best_count"][[0, 1, 3, 4]]) == [0, 0, 0, 0]
     assert np.all(g["best_H"][[0, 1, 3, 4]] == 0)
@@ -160,7 +159,7 @@ def test_graph_capture_replay_matches_eager():
 def test_batched_uneven_against_oracle_sample():
     rb = workloads.ransac_batch(P=16, seed=6, n_max=3000, cap=512)
     g = _np(_run(rb.corr, rb.offsets, rb.n_hyp, 3.0, 99))
-    o = oracle.ransac(rb.corr, rb.offsets, rb.n_hyp, 3.0, 99, band_px=BAND_PX)
+    o = oracle.ransac(rb.corr, rb.offsets, rb.n_hyp, 3.0, 99, band_px=BAND_PX, herr=HERR)
     _count_gate(g["hyp_counts"], o["hyp_counts"], o["band_counts"],
                 _sample_kappa_u(rb.corr, rb.offsets, rb.n_hyp, 99), "batched 16 pairs")
 

@@ -170,3 +170,18 @@ def test_scoring_matches_direct_residuals_of_oracle_hypotheses():
         r = np.hypot(c64[:, 2] - U[0] / U[2], c64[:, 3] - U[1] / U[2])
         assert cnt[h] == int(np.sum(ok & (r <= 3.0)))
         assert band[h] == int(np.sum(ok & (np.abs(r - 3.0) < 1e-3)))
+
+
+def test_ambiguity_band_contains_the_fixed_band_and_grows_with_the_error_model():
+    rp = workloads.ransac_problem(400, 0.6, 1.0, seed=8)
+    c0, b0 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-3)
+    c1, b1 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-3, herr=16)
+    c2, b2 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-3, herr=4096)
+    assert np.array_equal(c0, c1) and np.array_equal(c1, c2)
+    assert np.all(b0 <= b1) and np.all(b1 <= b2)
+    assert b2.sum() > b0.sum()
+    # a noise-free problem: residuals of all-inlier hypotheses are ~0, far from
+    # the threshold, except under an ill-conditioned minimal set
+    rq = workloads.ransac_problem(300, 1.0, 0.0, seed=9)
+    c, b = oracle.score_problem(rq.corr, 64, 3.0, seed=1, band_px=1e-3, herr=16)
+    assert np.mean(b[c == 300] == 0) > 0.9
