@@ -125,6 +125,23 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0) for r in rows)}
 
 
+def solve_traffic_per_launch(n):
+    """DRAM bytes per launch of the headline kernel from the committed ncu
+    capture (profiles/aca_solve_traffic.json), scaled to n sets; None when
+    the kernel's sources changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "aca_solve_traffic.json")))
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["dram_bytes_per_set"] * n
+    except Exception:
+        return None
+
+
 def sync_all(torch, dist_on):
     if dist_on:
         import torch.distributed as dist
@@ -304,7 +321,7 @@ def main():
                    "sets_per_gpu": n, "bytes_per_set": BYTES_PER_SET, "norm": "none",
                    "l2": "inputs (4 GiB) larger than L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": solve_traffic_per_launch(n),
                      "peak_source": peaks["source"], "kernel": "solve_vec4_kernel<ACA, NONE, no flags>",
                      "algorithmic_bytes_per_launch": BYTES_PER_SET * n},
         "cpu_baseline": cpu,
