@@ -186,6 +186,34 @@ aca_status ransac_aca(const float *corr, const int64_t *offsets, const int32_t *
                       void *stream);
 
 /*
+ * ransac_aca_noalloc - ransac_aca without a caller workspace and without any
+ * device allocation, for callers that may not allocate device memory: for
+ * example a plugin whose host framework owns all device memory through its
+ * own allocator, a latency-critical loop in which an allocation (which can
+ * synchronise the device) is not allowed, or a service whose device-memory
+ * budget is fixed at start-up.  The paper has no counterpart; this is a
+ * deployment variant of the RANSAC call above.
+ *
+ * The scratch is a fixed array of ACA_NOALLOC_SCRATCH_BYTES inside the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current) and caches it; make
+ * that first call before any stream capture.  All calls share the array and
+ * each call re-initialises it, so calls whose kernels may overlap on the GPU
+ * race and must be serialised by the caller.
+ *
+ *   total_hyps must equal sum(n_hyp); a request that needs more than
+ *   ACA_NOALLOC_SCRATCH_BYTES (ransac_aca_workspace_size(P, total_hyps))
+ *   is rejected with ACA_ERR_WORKSPACE before anything is launched.  Other
+ *   arguments, outputs and results are those of ransac_aca.
+ */
+#define ACA_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+aca_status ransac_aca_noalloc(const float *corr, const int64_t *offsets, const int32_t *n_hyp, int32_t P,
+                              int64_t total_hyps, const aca_ransac_params *params, float *best_H,
+                              int32_t *best_count, int32_t *best_hyp, int32_t *hyp_counts, uint8_t *inlier_mask,
+                              void *stream);
+
+/*
  * aca_sample_indices - the minimal-set indices ransac_aca draws: for
  * h = 0..n_hyp-1, idx[h][0..3] = the distinct indices (M, N, P, Q) in [0, N)
  * of hypothesis h of problem `problem` (the Philox counter's second word,

@@ -23,7 +23,9 @@ ACA_FLAG_SRC_ANCHORS, ACA_FLAG_TGT_ANCHORS, ACA_FLAG_OTHER_TRIPLE, ACA_FLAG_NON_
 _STATUS = {0: "ACA_OK", -1: "ACA_ERR_INVALID_ARG", -2: "ACA_ERR_CUDA", -3: "ACA_ERR_WORKSPACE", -4: "ACA_ERR_TIMEOUT"}
 
 EXPORTED = ("aca_solve", "sks_solve", "aca_rect_solve", "aca_backward", "aca_rect_backward",
-            "ransac_aca_workspace_size", "ransac_aca", "aca_sample_indices", "aca_last_error", "aca_version")
+            "ransac_aca_workspace_size", "ransac_aca", "ransac_aca_noalloc", "aca_sample_indices", "aca_last_error",
+            "aca_version")
+ACA_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 
 
 class AcaError(RuntimeError):
@@ -65,6 +67,7 @@ def load(build_if_missing: bool = True):
         L.ransac_aca.argtypes = [vp, vp, vp, i32, ctypes.POINTER(RansacParams), vp, vp, vp, vp, vp, vp,
                                  ctypes.c_size_t, vp]
         L.aca_sample_indices.argtypes = [i64, i32, ctypes.c_uint64, ctypes.c_uint32, vp, vp]
+        L.ransac_aca_noalloc.argtypes = [vp, vp, vp, i32, i64, ctypes.POINTER(RansacParams), vp, vp, vp, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("ransac_aca_workspace_size", "aca_last_error", "aca_version"):
                 getattr(L, name).restype = ctypes.c_int
@@ -208,3 +211,27 @@ def aca_sample_indices(N: int, n_hyp: int, seed: int, problem: int, idx, stream=
         raise ValueError("idx must be a contiguous (n_hyp, 4) int32 tensor")
     _check(load().aca_sample_indices(int(N), int(n_hyp), int(seed), int(problem), _ptr(idx),
                                      ctypes.c_void_p(_stream(stream))))
+
+
+def ransac_aca_noalloc(corr, offsets, n_hyp, total_hyps: int, params: RansacParams, best_H, best_count, best_hyp,
+                       hyp_counts=None, inlier_mask=None, stream=None):
+    """C ABI ransac_aca_noalloc: ransac_aca with the library's built-in scratch
+    (no workspace argument, no device allocation); total_hyps = sum(n_hyp)."""
+    _need(corr, "corr", torch.float32)
+    _need(offsets, "offsets", torch.int64)
+    _need(n_hyp, "n_hyp", torch.int32)
+    _need(best_H, "best_H", torch.float32)
+    _need(best_count, "best_count", torch.int32)
+    _need(best_hyp, "best_hyp", torch.int32)
+    if corr.dim() != 2 or corr.shape[1] != 4 or not corr.is_contiguous():
+        raise ValueError("corr must be a contiguous (total, 4) tensor")
+    P = n_hyp.numel()
+    if offsets.numel() != P + 1:
+        raise ValueError("offsets must have P+1 entries")
+    if hyp_counts is not None:
+        _need(hyp_counts, "hyp_counts", torch.int32)
+    if inlier_mask is not None:
+        _need(inlier_mask, "inlier_mask", torch.uint8)
+    _check(load().ransac_aca_noalloc(_ptr(corr), _ptr(offsets), _ptr(n_hyp), P, int(total_hyps), ctypes.byref(params),
+                                     _ptr(best_H), _ptr(best_count), _ptr(best_hyp), _ptr(hyp_counts),
+                                     _ptr(inlier_mask), ctypes.c_void_p(_stream(stream))))
