@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--rows", default="sks,ransac1,ransac512,diff",
                     help="comma list of extra rows: sks, ransac1, ransac512, diff")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ransac-tuning", default="",
+                    help="block_warps,hyps_per_thread,tile_points for the RANSAC rows (skips the autotuner)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the 512 per-problem RANSAC launches")
     return ap.parse_args()
 
 
@@ -348,10 +351,14 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
     reps = max(20, args.steps // 4)
     if "sks" in args.row_set:
         out.update(row_sks(torch, _lib, pts, H, flags, n, reps, stream))
+    fixed = None
+    if args.ransac_tuning:
+        w, h, t = (int(x) for x in args.ransac_tuning.split(","))
+        fixed = dict(block_warps=w, hyps_per_thread=h, tile_points=t)
     if rp is not None:
-        out.update(row_ransac1(torch, api, rp, stream, dev))
+        out.update(row_ransac1(torch, api, rp, stream, dev, fixed))
     if rb is not None:
-        out.update(row_ransac512(torch, api, rb, stream, dev))
+        out.update(row_ransac512(torch, api, rb, stream, dev, fixed, not args.no_plain))
     if rect is not None:
         out.update(row_diff(torch, _lib, rect, stream, dev))
     return out
@@ -375,7 +382,7 @@ def row_sks(torch, _lib, pts, H, flags, n, reps, stream):
     return out
 
 
-def row_ransac1(torch, api, rp, stream, dev):
+def row_ransac1(torch, api, rp, stream, dev, fixed=None):
     out = {}
     # fused RANSAC, one pair (config 2), graph-replayed
     from paper_2402_18008_gb300 import autotune
@@ -383,7 +390,7 @@ def row_ransac1(torch, api, rp, stream, dev):
     off2 = torch.tensor([0, 2000], dtype=torch.int64, device=dev)
     k2 = torch.tensor([4096], dtype=torch.int32, device=dev)
     make2 = lambda **kw: api.RansacPlan(corr, off2, k2, RANSAC_THR, SEED, 4096, **kw)
-    best2, _ = autotune.tune(make2, 1, 2000, 4096, device=dev)
+    best2 = fixed or autotune.tune(make2, 1, 2000, 4096, device=dev)[0]
     plan2 = make2(**best2).capture()
     for _ in range(5):
         plan2.replay()
@@ -396,7 +403,7 @@ def row_ransac1(torch, api, rp, stream, dev):
     return out
 
 
-def row_ransac512(torch, api, rb, stream, dev):
+def row_ransac512(torch, api, rb, stream, dev, fixed=None, plain=True):
     out = {}
     # batched uneven RANSAC (config 3) vs 512 separate per-problem launches
     tot = int(rb.n_hyp.sum())
@@ -407,11 +414,19 @@ def row_ransac512(torch, api, rb, stream, dev):
     k3 = torch.from_numpy(rb.n_hyp).to(dev)
     from paper_2402_18008_gb300 import autotune
     make3 = lambda **kw: api.RansacPlan(corr3, off3, k3, RANSAC_THR, SEED, tot, **kw)
-    best3, _ = autotune.tune(make3, len(rb.n_hyp), int(rb.offsets[-1]), tot, device=dev)
+    best3 = fixed or autotune.tune(make3, len(rb.n_hyp), int(rb.offsets[-1]), tot, device=dev)[0]
     plan3 = make3(**best3).capture()
     for _ in range(3):
         plan3.replay()
     t3 = time_region(torch, plan3.replay, 20, stream)
+    res = {"value": tests3 / (t3 * 1e-3), "unit": "hyp*pts/s", "ms_batched": t3,
+           "tflops_fp32": tests3 * FLOPS_PER_TEST / (t3 * 1e-3) / 1e12, "tests": tests3, "hypotheses": tot,
+           "points": int(rb.offsets[-1]), "tuning": best3,
+           "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9], adaptive hypotheses (99%, cap 16384), "
+                     "one graph replay"}
+    if not plain:
+        out["ransac_batched_512"] = res
+        return out
     plains = []
     for p in range(len(rb.n_hyp)):
         a, b = int(rb.offsets[p]), int(rb.offsets[p + 1])
@@ -425,13 +440,8 @@ def row_ransac512(torch, api, rb, stream, dev):
     tp = time_region(torch, run_plain, 3, stream)
     # check: batched == plain (best hypothesis per problem)
     same = all(int(pl.best_hyp.item()) == int(plan3.best_hyp[p].item()) for p, pl in enumerate(plains))
-    out["ransac_batched_512"] = {"value": tests3 / (t3 * 1e-3), "unit": "hyp*pts/s", "ms_batched": t3,
-                                 "ms_512_plain_launches": tp, "speedup_vs_plain": tp / t3,
-                                 "tflops_fp32": tests3 * FLOPS_PER_TEST / (t3 * 1e-3) / 1e12,
-                                 "tests": tests3, "hypotheses": tot, "points": int(rb.offsets[-1]),
-                                 "batched_equals_plain": same, "tuning": best3,
-                                 "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9], "
-                                           "adaptive hypotheses (99%, cap 16384), one graph replay"}
+    res.update(ms_512_plain_launches=tp, speedup_vs_plain=tp / t3, batched_equals_plain=same)
+    out["ransac_batched_512"] = res
     return out
 
 

@@ -279,67 +279,105 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 }
 
 // ---------------------------------------------------------------------------
-// SKS (Sec. 3, Eq. 4-14), in the frames of the midpoints O1, O2.
+// SKS (Sec. 3, Eq. 4-14).
+//
+// The steps of the paper, rewritten with identities that remove the
+// cancellations an FP32 evaluation would suffer (all exact in real
+// arithmetic; O = midpoint of MN, ON = MN / 2):
+//   P3 = H_S1 P1 = (ON.(P1 - O1), ON x (P1 - O1), f_S1) with
+//     ON x (P1 - O1) = ON x M1P1 and ON.(P1 - O1) = ON.M1P1 - f_S1 (Eq. 6-7);
+//   P5 = (P3.x, f_S1) / P3.y, Q7 = (Q3.x, f_S1) / Q3.y - P5 (Eq. 10-11) with
+//     Q7.x = (Q3.x P3.y - P3.x Q3.y) / (Q3.y P3.y),
+//     Q7.y = f_S1 (P3.y - Q3.y) / (Q3.y P3.y), P3.y - Q3.y = ON x Q1P1;
+//   a_K, b_K of Eq. 11 with the common denominators cancelled:
+//     a_K = d7 (n8x n7x - n8y n7y) / (d8 (n7x^2 - n7y^2)),
+//     b_K = d7 (n8y n7x - n8x n7y) / (d8 (n7x^2 - n7y^2)),
+//     where Q7 = (n7x, n7y) / d7 and Q8 = (n8x, n8y) / d8;
+//   u_K, v_K of Eq. 13; H = H_S2^-1 H_K H_S1 (Eq. 14) composed in the M
+//   frames in double-float and rounded once.
+// Differences are exact (TwoSum) and dot / cross products of them carry
+// their remainders.
 // ---------------------------------------------------------------------------
+struct SksSide {
+    Diff onx, ony;           // ON = M N / 2
+    float fS;                // |ON|^2
+    float P3x, P3y, Q3x, Q3y;
+    float cQP;               // ON x Q P (= P3.y - Q3.y)
+};
+
+ACA_HD void sks_side(float Mx, float My, float Nx, float Ny, float Px, float Py, float Qx, float Qy, SksSide &o)
+{
+    o.onx = half(diff(Nx, Mx));
+    o.ony = half(diff(Ny, My));
+    const Diff mpx = diff(Px, Mx), mpy = diff(Py, My);
+    const Diff mqx = diff(Qx, Mx), mqy = diff(Qy, My);
+    const Diff qpx = diff(Px, Qx), qpy = diff(Py, Qy);
+    const DF fS = dot2x_df(o.onx, o.ony, o.onx, o.ony);
+    o.fS = df_round(fS);
+    o.P3y = cross2x(o.onx, o.ony, mpx, mpy);
+    o.Q3y = cross2x(o.onx, o.ony, mqx, mqy);
+    o.P3x = df_round(df_sub(dot2x_df(o.onx, o.ony, mpx, mpy), fS));
+    o.Q3x = df_round(df_sub(dot2x_df(o.onx, o.ony, mqx, mqy), fS));
+    o.cQP = cross2x(o.onx, o.ony, qpx, qpy);
+}
+
 ACA_HD void sks_solve(const Set &s, float H[9])
 {
-    // Eq. 4-5: O = (M + N) / 2, ON = N - O = (N - M) / 2 (exact halving)
-    const float ON1x = F_MUL(0.5f, F_SUB(s.N1x, s.M1x)), ON1y = F_MUL(0.5f, F_SUB(s.N1y, s.M1y));
-    const float ON2x = F_MUL(0.5f, F_SUB(s.N2x, s.M2x)), ON2y = F_MUL(0.5f, F_SUB(s.N2y, s.M2y));
-    const float O1x = F_ADD(s.M1x, ON1x), O1y = F_ADD(s.M1y, ON1y);
-    const float O2x = F_ADD(s.M2x, ON2x), O2y = F_ADD(s.M2y, ON2y);
-    const float fS1 = sq2(ON1x, ON1y), fS2 = sq2(ON2x, ON2y);   // Eq. 7
-    // P3 = H_S1 P1, Q3 = H_S1 Q1 (Eq. 6), homogeneous with w = f_S1
-    const float p1x = F_SUB(s.P1x, O1x), p1y = F_SUB(s.P1y, O1y);
-    const float q1x = F_SUB(s.Q1x, O1x), q1y = F_SUB(s.Q1y, O1y);
-    const float p2x = F_SUB(s.P2x, O2x), p2y = F_SUB(s.P2y, O2y);
-    const float q2x = F_SUB(s.Q2x, O2x), q2y = F_SUB(s.Q2y, O2y);
-    const float P3x = det2(ON1x, -ON1y, p1y, p1x), P3y = cross2(ON1x, ON1y, p1x, p1y);
-    const float Q3x = det2(ON1x, -ON1y, q1y, q1x), Q3y = cross2(ON1x, ON1y, q1x, q1y);
-    const float P4x = det2(ON2x, -ON2y, p2y, p2x), P4y = cross2(ON2x, ON2y, p2x, p2y);
-    const float Q4x = det2(ON2x, -ON2y, q2y, q2x), Q4y = cross2(ON2x, ON2y, q2x, q2y);
-    // Eq. 10-11: H_E swaps y and w; dehomogenise; translate by -P5 / -P6
-    const float P5x = F_DIV(P3x, P3y), P5y = F_DIV(fS1, P3y);
-    const float P6x = F_DIV(P4x, P4y), P6y = F_DIV(fS2, P4y);
-    const float Q7x = F_SUB(F_DIV(Q3x, Q3y), P5x), Q7y = F_SUB(F_DIV(fS1, Q3y), P5y);
-    const float Q8x = F_SUB(F_DIV(Q4x, Q4y), P6x), Q8y = F_SUB(F_DIV(fS2, Q4y), P6y);
-    // Eq. 11: [Q8.x, Q8.y] = [[a, b], [b, a]] [Q7.x, Q7.y]
-    const float det = F_MUL(F_SUB(Q7x, Q7y), F_ADD(Q7x, Q7y));
-    const float aK = F_DIV(det2(Q8x, Q8y, Q7y, Q7x), det);   // Q8x Q7x - Q8y Q7y
-    const float bK = F_DIV(det2(Q8y, Q8x, Q7y, Q7x), det);   // Q8y Q7x - Q8x Q7y
-    // Eq. 13
+    SksSide a, b;
+    sks_side(s.M1x, s.M1y, s.N1x, s.N1y, s.P1x, s.P1y, s.Q1x, s.Q1y, a);
+    sks_side(s.M2x, s.M2y, s.N2x, s.N2y, s.P2x, s.P2y, s.Q2x, s.Q2y, b);
+    // Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11)
+    const float n7x = det2(a.Q3x, a.P3x, a.Q3y, a.P3y), n7y = F_MUL(a.fS, a.cQP), d7 = F_MUL(a.Q3y, a.P3y);
+    const float n8x = det2(b.Q3x, b.P3x, b.Q3y, b.P3y), n8y = F_MUL(b.fS, b.cQP), d8 = F_MUL(b.Q3y, b.P3y);
+    // Eq. 11 solved for a_K = a_G, b_K = b_G
+    const float den = F_MUL(d8, F_MUL(F_SUB(n7x, n7y), F_ADD(n7x, n7y)));
+    const float aK = F_DIV(F_MUL(d7, det2(n8x, n8y, n7y, n7x)), den);
+    const float bK = F_DIV(F_MUL(d7, det2(n8y, n8x, n7y, n7x)), den);
+    // Eq. 13 with P5 = (P3.x, f_S1) / P3.y, P6 = (P4.x, f_S2) / P4.y
+    const float P5x = F_DIV(a.P3x, a.P3y), P5y = F_DIV(a.fS, a.P3y);
+    const float P6x = F_DIV(b.P3x, b.P3y), P6y = F_DIV(b.fS, b.P3y);
     const float uK = F_SUB(P6x, F_FMA(aK, P5x, F_MUL(bK, P5y)));
     const float vK = F_SUB(P6y, F_FMA(bK, P5x, F_MUL(aK, P5y)));
-    // Eq. 14 in the midpoint frames: L = R2^-1 K R1 with
-    // R1 = [[ON1x, ON1y, 0], [-ON1y, ON1x, 0], [0, 0, fS1]],
-    // R2^-1 = [[ON2x, -ON2y, 0], [ON2y, ON2x, 0], [0, 0, 1]],
-    // K = [[aK, uK, bK], [0, 1, 0], [bK, vK, aK]].
-    // K R1:
-    const float A00 = det2(aK, uK, ON1y, ON1x);       // aK*ON1x - uK*ON1y
-    const float A01 = F_FMA(aK, ON1y, F_MUL(uK, ON1x));
-    const float A02 = F_MUL(bK, fS1);
-    const float A10 = -ON1y, A11 = ON1x;
-    const float A20 = det2(bK, vK, ON1y, ON1x);
-    const float A21 = F_FMA(bK, ON1y, F_MUL(vK, ON1x));
-    const float A22 = F_MUL(aK, fS1);
-    // R2^-1 (K R1):
-    const float L00 = det2(ON2x, ON2y, A10, A00), L01 = det2(ON2x, ON2y, A11, A01), L02 = F_MUL(ON2x, A02);
-    const float L10 = F_FMA(ON2y, A00, F_MUL(ON2x, A10)), L11 = F_FMA(ON2y, A01, F_MUL(ON2x, A11));
-    const float L12 = F_MUL(ON2y, A02);
-    const float L20 = A20, L21 = A21, L22 = A22;
-    // H = T(O2) L T(-O1)
-    const float G02 = F_FMA(-O1x, L00, F_FMA(-O1y, L01, L02));
-    const float G12 = F_FMA(-O1x, L10, F_FMA(-O1y, L11, L12));
-    const float G22 = F_FMA(-O1x, L20, F_FMA(-O1y, L21, L22));
-    H[0] = F_FMA(O2x, L20, L00);
-    H[1] = F_FMA(O2x, L21, L01);
-    H[2] = F_FMA(O2x, G22, G02);
-    H[3] = F_FMA(O2y, L20, L10);
-    H[4] = F_FMA(O2y, L21, L11);
-    H[5] = F_FMA(O2y, G22, G12);
-    H[6] = L20;
-    H[7] = L21;
-    H[8] = G22;
+    // Eq. 14 in the M frames: H = T(M2) L T(-M1) with
+    // L = T(ON2) R2^-1 K R1 T(-ON1), R1 = [[ONx, ONy, 0], [-ONy, ONx, 0], [0, 0, fS1]],
+    // R2^-1 = [[ONx, -ONy, 0], [ONy, ONx, 0], [0, 0, 1]], K = [[aK, uK, bK], [0, 1, 0], [bK, vK, aK]].
+    const float o1x = a.onx.h, o1y = a.ony.h, o2x = b.onx.h, o2y = b.ony.h;
+    // K R1 (rows), in double-float
+    const DF A00 = df_sub(df_prod(aK, o1x), df_prod(uK, o1y));
+    const DF A01 = df_add(df_prod(aK, o1y), df_prod(uK, o1x));
+    const DF A02 = df_prod(bK, a.fS);
+    const DF A20 = df_sub(df_prod(bK, o1x), df_prod(vK, o1y));
+    const DF A21 = df_add(df_prod(bK, o1y), df_prod(vK, o1x));
+    const DF A22 = df_prod(aK, a.fS);
+    // R2^-1 (K R1): row 1 of K R1 is (-o1y, o1x, 0)
+    const DF L00 = df_add(df_mul(A00, o2x), df_prod(o2y, o1y));
+    const DF L01 = df_sub(df_mul(A01, o2x), df_prod(o2y, o1x));
+    const DF L02 = df_mul(A02, o2x);
+    const DF L10 = df_sub(df_mul(A00, o2y), df_prod(o2x, o1y));
+    const DF L11 = df_add(df_mul(A01, o2y), df_prod(o2x, o1x));
+    const DF L12 = df_mul(A02, o2y);
+    // fold T(-ON1) on the right (column 3 -= ON1.x col 1 + ON1.y col 2) and
+    // T(ON2) on the left (rows 1, 2 += ON2 * row 3); ON1, ON2 as value + remainder
+    const DF G02 = df_sub(df_sub(L02, df_mul(L00, o1x)), df_mul(L01, o1y));
+    const DF G12 = df_sub(df_sub(L12, df_mul(L10, o1x)), df_mul(L11, o1y));
+    const DF G22 = df_sub(df_sub(A22, df_mul(A20, o1x)), df_mul(A21, o1y));
+    const DF J00 = df_add(L00, df_mul(A20, o2x)), J01 = df_add(L01, df_mul(A21, o2x));
+    const DF J02 = df_add(G02, df_mul(G22, o2x));
+    const DF J10 = df_add(L10, df_mul(A20, o2y)), J11 = df_add(L11, df_mul(A21, o2y));
+    const DF J12 = df_add(G12, df_mul(G22, o2y));
+    // then T(M2) J T(-M1)
+    const DF K02 = df_sub(df_sub(J02, df_mul(J00, s.M1x)), df_mul(J01, s.M1y));
+    const DF K12 = df_sub(df_sub(J12, df_mul(J10, s.M1x)), df_mul(J11, s.M1y));
+    const DF K22 = df_sub(df_sub(G22, df_mul(A20, s.M1x)), df_mul(A21, s.M1y));
+    H[0] = df_round(df_add(J00, df_mul(A20, s.M2x)));
+    H[1] = df_round(df_add(J01, df_mul(A21, s.M2x)));
+    H[2] = df_round(df_add(K02, df_mul(K22, s.M2x)));
+    H[3] = df_round(df_add(J10, df_mul(A20, s.M2y)));
+    H[4] = df_round(df_add(J11, df_mul(A21, s.M2y)));
+    H[5] = df_round(df_add(K12, df_mul(K22, s.M2y)));
+    H[6] = df_round(A20);
+    H[7] = df_round(A21);
+    H[8] = df_round(K22);
 }
 
 // ---------------------------------------------------------------------------

@@ -118,4 +118,16 @@ ACA_HD DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
 
 ACA_HD float df_round(DF x) { return F_ADD(x.h, x.l); }
 
+// u . v of two exact differences (value + remainder), as a double-float:
+// exact products of the leading parts plus first-order remainder terms.
+ACA_HD DF dot2x_df(Diff ux, Diff uy, Diff vx, Diff vy)
+{
+    const DF a = df_prod(ux.h, vx.h), b = df_prod(uy.h, vy.h);
+    const DF s = df_add(a, b);
+    const float c = F_FMA(ux.h, vx.l, F_FMA(ux.l, vx.h, F_FMA(uy.h, vy.l, F_MUL(uy.l, vy.h))));
+    return DF{s.h, F_ADD(s.l, c)};
+}
+
+ACA_HD Diff half(Diff d) { return Diff{F_MUL(0.5f, d.h), F_MUL(0.5f, d.l)}; }
+
 }  // namespace aca
