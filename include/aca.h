@@ -159,9 +159,10 @@ aca_status aca_rect_backward(const float *tgt, float x0, float y0, float w, floa
  * (M,N,P), (M,Q,P), (M,N,Q), (N,P,Q) has |cross(a, b)| <= 1e-3 |a| |b| for
  * its two edge vectors a, b.
  * Inlier test: with (u, v, w) = H (x1, y1, 1), a point is an inlier when
- * w != 0 and (u - x2 w)^2 + (v - y2 w)^2 <= thr^2 w^2, i.e. the forward
- * transfer error ||x2 - (u/w, v/w)|| <= thr, evaluated without division in
- * FP32.  Best: highest count, ties to the lowest hypothesis index.
+ * (u - x2 w)^2 + (v - y2 w)^2 - thr^2 w^2 < 0 in FP32 (H scaled by an exact
+ * power of two), i.e. the forward transfer error ||x2 - (u/w, v/w)|| < thr
+ * without a division; points exactly at the threshold are within rounding of
+ * either outcome.  Best: highest count, ties to the lowest hypothesis index.
  */
 typedef struct {
     float threshold_px;      /* inlier threshold in pixels (> 0) */

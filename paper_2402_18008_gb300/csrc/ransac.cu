@@ -76,11 +76,16 @@ __device__ __forceinline__ bool make_hypothesis(const float4 *__restrict__ c, ui
 }
 
 // Forward transfer error test without division: with (u, v, w) = H (x, y, 1),
-// inlier iff w != 0 and (X w - u)^2 + (Y w - v)^2 - thr^2 w^2 <= 0.
-// The hypothesis is kept as G = (-h11, -h12, -h13, -h21, -h22, -h23, h31,
-// h32, h33) and nthr2 = -thr^2 so that the test needs no negation:
+// e = (X w - u)^2 + (Y w - v)^2 - thr^2 w^2 and the point is an inlier when
+// e < 0, i.e. ||(X, Y) - (u/w, v/w)|| < thr (e < 0 forces w != 0).  The FP32
+// evaluation is strict; a point with e == 0 exactly lies within rounding of
+// the threshold.  The hypothesis is kept as G = (-h11, -h12, -h13, -h21,
+// -h22, -h23, h31, h32, h33) and nthr2 = -thr^2 so that no negation is
+// needed:
 //   w = g6 x + g7 y + g8, -u = g0 x + g1 y + g2, -v = g3 x + g4 y + g5,
 //   du = X w - u, dv = Y w - v, e = du^2 + (dv^2 + (nthr2 w) w).
+// e is never -0 (each step adds a non-negative square to a sum that is not
+// -0), so its sign bit is exactly (e < 0) and counting is a shift and an add.
 // The same operations, in the same order, run lane-wise on f32x2 pairs in
 // the scoring loop (inlier2) and on scalars in the epilogue (inlier): packed
 // FP32 instructions round each lane exactly like the scalar ones, so counts
@@ -102,7 +107,7 @@ __device__ __forceinline__ int inlier(const float G[9], float4 c, float nthr2)
     const float du = F_FMA(c.z, w, nu);
     const float dv = F_FMA(c.w, w, nv);
     const float e = F_FMA(du, du, F_FMA(dv, dv, F_MUL(F_MUL(nthr2, w), w)));
-    return (e <= 0.0f) & (w != 0.0f);
+    return (int)(__float_as_uint(e) >> 31);
 }
 
 // Packed FP32 pair operations (sm_100+ f32x2 instructions; one instruction
@@ -139,7 +144,7 @@ __device__ __forceinline__ int inlier2(const float2 g[9], float4 p, float4 q, fl
     const float2 du = fma2(X, w, nu);
     const float2 dv = fma2(Y, w, nv);
     const float2 e = fma2(du, du, fma2(dv, dv, mul2(mul2(nthr2, w), w)));
-    return ((e.x <= 0.0f) & (w.x != 0.0f)) + ((e.y <= 0.0f) & (w.y != 0.0f));
+    return (int)((__float_as_uint(e.x) >> 31) + (__float_as_uint(e.y) >> 31));
 }
 
 struct Workspace {
