@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-log2", type=int, default=N_LOG2)
     ap.add_argument("--no-rows", action="store_true", help="headline only")
-    ap.add_argument("--rows", default="sks,ransac1,ransac512,diff",
-                    help="comma list of extra rows: sks, ransac1, ransac512, diff")
+    ap.add_argument("--rows", default="sks,ransac1,ransac512,diff,latency",
+                    help="comma list of extra rows: sks, ransac1, ransac512, diff, latency")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ransac-tuning", default="",
                     help="block_warps,hyps_per_thread,tile_points for the RANSAC rows (skips the autotuner)")
@@ -143,6 +143,26 @@ def solve_traffic_per_launch(n):
         return rec["dram_bytes_per_set"] * n
     except Exception:
         return None
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank solves its own batch of the same size (weak scaling)."""
+    return SEED + rank
+
+
+def max_over_ranks(x: float, torch, device) -> float:
+    """Slowest rank's time: the whole job finishes when the last rank does."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(sets_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job H/s: the sets of all ranks over the slowest rank's time."""
+    return sets_per_rank * world / (max_ms * 1e-3)
 
 
 def sync_all(torch, dist_on):
@@ -249,7 +269,7 @@ def main():
         return
     n = 1 << args.n_log2
     # host-side generation first (process pool before any CUDA call)
-    ms = workloads.minimal_sets(n, seed=SEED + rank, degenerate_frac=0.01, keep_truth=False,
+    ms = workloads.minimal_sets(n, seed=rank_seed(rank), degenerate_frac=0.01, keep_truth=False,
                                 workers=max(1, os.cpu_count() or 1))
     rows_on = not args.no_rows and world == 1
     args.row_set = set(r for r in args.rows.split(",") if r) if rows_on else set()
@@ -281,10 +301,7 @@ def main():
         sync_all(torch, dist_on)
         ms_step = time_region(torch, solve, args.steps, stream)
         sync_all(torch, dist_on)
-        if dist_on:
-            t = torch.tensor([ms_step], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, torch, dev)
         # errors vs the FP64 oracle on a sample (flags from a flags-on solve)
         _lib.aca_solve(pts, H, flags, n=n)
         torch.cuda.synchronize()
@@ -313,7 +330,7 @@ def main():
     e2e_ms = time_region(torch, e2e_step, e2e_steps, stream)
 
     cpu = cpu_baseline_aca(ms.pts, args.cpu_seconds)
-    value = n * world / (ms_step * 1e-3)
+    value = job_throughput(n, world, ms_step)
     achieved = BYTES_PER_SET * n / (ms_step * 1e-3) / 1e9
     line = {
         "metric": "ACA minimal solves per second (config 1: 2^26 sets, FP32 SoA 16 in / 9 out)",
@@ -361,7 +378,44 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
         out.update(row_ransac512(torch, api, rb, stream, dev, fixed, not args.no_plain))
     if rect is not None:
         out.update(row_diff(torch, _lib, rect, stream, dev))
+    if "latency" in args.row_set:
+        out.update(row_latency(torch, _lib, pts, H, n, stream))
     return out
+
+
+# The paper's GPU sample numbers (Sec. 6.4, Table 8) and its ACA times on an
+# RTX 3090 in FP64, microseconds; context only (other hardware and precision).
+PAPER_TABLE8_ACA_US = {1: 3.11, 10: 3.16, 100: 3.19, 1000: 3.20, 10000: 5.26, 100000: 29.3, 1000000: 245.0}
+
+
+def row_latency(torch, _lib, pts, H, n_total, stream):
+    """aca_solve on the first m sets of the resident batch for the paper's
+    sample numbers.  Device time per call: 100 calls captured in one CUDA
+    graph, the graph replayed, CUDA events around the replays (host launch
+    cost excluded, as in a kernel-time measurement); plus the host-side cost
+    of one eager call through the Python binding."""
+    res = {}
+    for m in sorted(PAPER_TABLE8_ACA_US):
+        if m > n_total:
+            break
+        f = lambda: _lib.aca_solve(pts, H, None, n=m)
+        for _ in range(5):
+            f()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                for _ in range(100):
+                    _lib.aca_solve(pts, H, None, n=m, stream=s)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        t = time_region(torch, g.replay, 10, stream) / 100
+        eager = time_region(torch, f, 200, stream)
+        res[str(m)] = {"us": t * 1e3, "ns_per_set": t * 1e6 / m, "eager_call_us": eager * 1e3,
+                       "paper_rtx3090_fp64_us": PAPER_TABLE8_ACA_US[m]}
+    return {"aca_latency_sweep": res}
 
 
 def row_sks(torch, _lib, pts, H, flags, n, reps, stream):

@@ -268,7 +268,7 @@ extern "C" aca_status aca_backward(const float *pts, const float *grad_H, float 
         return set_error(ACA_ERR_INVALID_ARG, "aca_backward: null pointer");
     const cudaStream_t st = as_stream(stream);
     const int threads = 256;
-    if (ld % 4 == 0 && aligned16(pts) && aligned16(grad_H) && aligned16(grad_tgt)) {
+    if (n >= kSmallBatch && ld % 4 == 0 && aligned16(pts) && aligned16(grad_H) && aligned16(grad_tgt)) {
         const int grid = resident_grid(aca_backward_vec4_kernel, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
         aca_backward_vec4_kernel<<<grid, threads, 0, st>>>(pts, grad_H, grad_tgt, n, ld);
     } else {
@@ -292,7 +292,7 @@ extern "C" aca_status aca_rect_backward(const float *tgt, float x0, float y0, fl
     const Rect R{x0, y0, w, r};
     const cudaStream_t st = as_stream(stream);
     const int threads = 256;
-    if (ld % 4 == 0 && aligned16(tgt) && aligned16(grad_H) && aligned16(grad_tgt)) {
+    if (n >= kSmallBatch && ld % 4 == 0 && aligned16(tgt) && aligned16(grad_H) && aligned16(grad_tgt)) {
         const int grid = resident_grid(rect_backward_vec4_kernel, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
         rect_backward_vec4_kernel<<<grid, threads, 0, st>>>(tgt, R, grad_H, grad_tgt, n, ld);
     } else {

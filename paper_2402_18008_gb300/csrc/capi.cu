@@ -1,5 +1,7 @@
 // Library-wide C-ABI helpers: error message, version, device properties.
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -34,6 +36,27 @@ int sm_count()
         cache[dev] = v;
     }
     return cache[dev];
+}
+
+int blocks_per_sm(const void *kernel, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(kernel, threads, smem, dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = cache.find(key);
+        if (it != cache.end())
+            return it->second;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = per_sm;
+    return per_sm;
 }
 
 }  // namespace aca

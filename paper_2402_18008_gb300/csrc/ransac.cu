@@ -207,7 +207,7 @@ __device__ int64_t block_scan_incl(int64_t v, int64_t *warp_tot)
 
 __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__restrict__ offsets,
                                                            const int32_t *__restrict__ n_hyp, int32_t P, int HB,
-                                                           int T, Workspace ws)
+                                                           int T, Workspace ws, bool zero_here)
 {
     __shared__ int64_t wt_a[32], wt_b[32];
     __shared__ int64_t carry_a, carry_b;
@@ -245,6 +245,11 @@ __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__rest
     if (threadIdx.x == 0 && carry_a > ws.capacity) {
         *ws.flags = 1;
         ws.item_off[P] = 0;   // nothing to score
+    }
+    if (zero_here) {          // small workspaces: clear the counts here, no extra launch
+        const int64_t lim = carry_a < ws.capacity ? carry_a : ws.capacity;
+        for (int64_t i = threadIdx.x; i < lim; i += blockDim.x)
+            ws.counts[i] = 0;
     }
 }
 
@@ -549,10 +554,12 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
     const cudaStream_t st = as_stream(stream);
     const Workspace ws = carve(workspace, P, workspace_bytes);
 
-    ransac_prep_kernel<<<1, 1024, 0, st>>>(offsets, n_hyp, P, HB, T, ws);
+    // counts of small workspaces are cleared by the prep kernel itself
+    const bool zero_in_prep = ws.capacity <= 65536;
+    ransac_prep_kernel<<<1, 1024, 0, st>>>(offsets, n_hyp, P, HB, T, ws, zero_in_prep);
     aca_status s = check_launch("ransac_aca (prep)");
     if (s != ACA_OK) return s;
-    {
+    if (!zero_in_prep) {
         const int threads = 256;
         const int grid = resident_grid(zero_counts_kernel, threads, 0, (ws.capacity + threads - 1) / threads);
         zero_counts_kernel<<<grid, threads, 0, st>>>(ws, P);

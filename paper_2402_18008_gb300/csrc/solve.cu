@@ -111,7 +111,7 @@ template <int SOLVER, int NORM, bool FLAGS>
 static aca_status launch_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int64_t ld, cudaStream_t st)
 {
     const int threads = 256;
-    const bool vec = (ld % 4 == 0) && aligned16(pts) && aligned16(H) &&
+    const bool vec = n >= kSmallBatch && (ld % 4 == 0) && aligned16(pts) && aligned16(H) &&
                      (!FLAGS || (reinterpret_cast<uintptr_t>(flags) & 3u) == 0);
     if (vec) {
         auto k = solve_vec4_kernel<SOLVER, NORM, FLAGS>;
@@ -239,7 +239,7 @@ extern "C" aca_status aca_rect_solve(const float *tgt, float x0, float y0, float
     const Rect R{x0, y0, w, r};
     const cudaStream_t st = as_stream(stream);
     const int threads = 256;
-    if (ld % 4 == 0 && aligned16(tgt) && aligned16(H)) {
+    if (n >= kSmallBatch && ld % 4 == 0 && aligned16(tgt) && aligned16(H)) {
         const int grid = resident_grid(rect_vec4_kernel, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
         rect_vec4_kernel<<<grid, threads, 0, st>>>(tgt, R, H, n, ld);
     } else {

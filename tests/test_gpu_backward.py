@@ -33,7 +33,7 @@ def test_general_backward_matches_analytic_jacobian():
     assert r < GRAD_TOL
 
 
-@pytest.mark.parametrize("n,ld", [(1, 1), (5, 8), (7, 7), (1023, 1024)])
+@pytest.mark.parametrize("n,ld", [(1, 1), (5, 8), (7, 7), (1023, 1024), ((1 << 18) + 3, (1 << 18) + 4)])
 def test_backward_ragged(n, ld):
     ms = workloads.minimal_sets(n, seed=2)
     pts = torch.zeros((16, ld), device="cuda")
@@ -49,8 +49,8 @@ def test_backward_ragged(n, ld):
         assert torch.all(gt[:, n:] == 7.0)
 
 
-def test_rect_backward_matches_analytic_jacobian():
-    B = 65536
+@pytest.mark.parametrize("B", [65536, (1 << 18) + 1])
+def test_rect_backward_matches_analytic_jacobian(B):
     rb = workloads.rect_batch(B, seed=0)
     rng = np.random.default_rng(4)
     G = rng.standard_normal((9, B)).astype(np.float32)

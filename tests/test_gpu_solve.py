@@ -75,19 +75,26 @@ def test_full_size_workload_sampled_against_oracle():
     kappa_gate(err_s[ok], kap[ok], "sks full size 2^26 (sample 2^16)")
 
 
-def test_vector_and_scalar_paths_agree_bitwise():
-    n = 1000
+@pytest.mark.parametrize("solver", ["aca", "sks"])
+def test_vector_and_scalar_paths_agree_bitwise(solver):
+    # large batches (>= 2^18 sets) with ld % 4 == 0 take the float4 path,
+    # small batches, odd ld and misaligned bases the one-set-per-thread path
+    n = (1 << 18) + 5
     ms = workloads.minimal_sets(n, seed=6)
-    H4, _ = _solve(ms.pts, n, 1000)          # ld % 4 == 0 -> float4 path
-    H1, _ = _solve(ms.pts, n, 1001)          # ld odd -> scalar path
+    H4, f4 = _solve(ms.pts, n, n + 3, solver=solver, flags=True)      # float4 path, ragged tail
+    H1, f1 = _solve(ms.pts, n, n, solver=solver, flags=True)          # ld odd -> scalar path
     assert torch.equal(H4[:, :n], H1[:, :n])
-    # misaligned base pointer also takes the scalar path
-    pts = torch.zeros((16, 1025), dtype=torch.float32, device="cuda")
+    assert torch.equal(f4[:n], f1[:n])
+    assert torch.all(H4[:, n:] == 12345.0) and torch.all(f4[n:] == 0xEE)
+    pts = torch.zeros((16, n + 4), dtype=torch.float32, device="cuda")
     pts[:, 1:1 + n] = cuda(ms.pts)
-    H = torch.empty((9, 1025), dtype=torch.float32, device="cuda")
-    _lib.aca_solve(pts[:, 1:], H[:, 1:], None, n=n)
+    H = torch.empty((9, n + 4), dtype=torch.float32, device="cuda")
+    (_lib.aca_solve if solver == "aca" else _lib.sks_solve)(pts[:, 1:], H[:, 1:], None, n=n)
     torch.cuda.synchronize()
     assert torch.equal(H[:, 1:1 + n], H4[:, :n])
+    small = 1000                                                       # small batch: scalar path
+    Hs, _ = _solve(ms.pts, small, 1000, solver=solver)
+    assert torch.equal(Hs[:, :small], H4[:, :small])
 
 
 def test_norm_modes():
@@ -146,8 +153,8 @@ def test_sks_ragged_sizes_and_untouched_tail(n, ld):
         assert torch.all(H[:, n:] == 12345.0)
 
 
-def test_rect_solve_matches_eq42_and_general_aca():
-    B = 65536
+@pytest.mark.parametrize("B", [65536, (1 << 18) + 3])
+def test_rect_solve_matches_eq42_and_general_aca(B):
     rb = workloads.rect_batch(B, seed=0)
     tgt = cuda(rb.tgt)
     H = torch.empty((9, B), dtype=torch.float32, device="cuda")
