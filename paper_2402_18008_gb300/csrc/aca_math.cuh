@@ -13,10 +13,8 @@
 //  * t1 = f_A1 - Q3.x - Q3.y (Eq. 27) is evaluated as cross(N1P1, N1Q1), its
 //    exact value (twice the signed area of N1 P1 Q1), so the sum does not
 //    cancel; likewise t2;
-//  * the core product (Eq. 28-29) and the composition (Eq. 24) are carried
-//    in double-float (aca_compose_df) and H is rounded once; aca_compose is
-//    the plain FP32 grouping of the same products (each entry one Kahan
-//    determinant), kept for comparison.
+//  * the core product (Eq. 28-29) and the local-frame composition (Eq. 24)
+//    are carried in double-float and rounded once per entry (aca_compose).
 // Unnormalised output (ACA_NORM_NONE) is the paper's division-free H of
 // Eq. 24 with the scale of Eq. 28-29, the function the backward kernels
 // differentiate.
@@ -83,51 +81,23 @@ ACA_HD void aca_parts(const Set &s, AcaParts &p)
 ACA_HD float fmax3_(float a, float b, float c);
 ACA_HD float pow2_inv_scale(float x);
 
+// Core (Eq. 29) and composition (Eq. 24) from the parts, H row-major.
+// The core c11, c22, c33 and the products of the local-frame homography
+//   L = H_A2^-1(M2 frame) * H_C * H_A1(M1 frame)
+// are carried in double-float and each entry of L is rounded once; the
+// translation back, H = T(M2) L T(-M1), is plain FP32.  (Rounding c11, c22,
+// c33 and the products c * M2N2 to FP32 instead roughly doubles the error of
+// ill-conditioned sets; carrying the translation in double-float as well
+// changes nothing measurable.)
+// H_C * A1 rows with A1 = [[MP1.y, -MP1.x], [-MN1.y, MN1.x]] (Eq. 20); the
+// third row is c11*a0 + c22*a1 + c33*(-NP1.y, NP1.x, f_A1), which equals
+// (c11-c33)*a0 + (c22-c33)*a1 + c33*(0, 0, f_A1) of Eq. 28 exactly.  The
+// left factor H_A2^-1 (Eq. 22) in the M2 frame is [[MN2.x, MP2.x],
+// [MN2.y, MP2.y]].  With `prescale`, (c11, c22, c33) are first multiplied by
+// a power of two (exact) so that the largest has magnitude in [1, 2): H
+// changes by that exact factor only, and normalised outputs stay clear of
+// overflow.
 ACA_HD void aca_compose(const Set &s, const AcaParts &p, bool prescale, float H[9])
-{
-    float c11 = F_MUL(F_MUL(p.t1, p.Q3y), p.Q4x);
-    float c22 = F_MUL(F_MUL(p.t1, p.Q3x), p.Q4y);
-    float c33 = F_MUL(F_MUL(p.t2, p.Q3x), p.Q3y);
-    if (prescale) {
-        const float sc = pow2_inv_scale(fmax3_(c11, c22, c33));
-        c11 = F_MUL(c11, sc);
-        c22 = F_MUL(c22, sc);
-        c33 = F_MUL(c33, sc);
-    }
-    // H_C * A1 rows with A1 = [[MP1.y, -MP1.x], [-MN1.y, MN1.x]] (Eq. 20);
-    // third row = c11*a0 + c22*a1 + c33*(-NP1.y, NP1.x, f_A1), which equals
-    // (c11-c33)*a0 + (c22-c33)*a1 + c33*(0, 0, f_A1) of Eq. 28 exactly.
-    // Left factor H_A2^-1 (Eq. 22) in the M2 frame: [[MN2.x, MP2.x], [MN2.y, MP2.y]].
-    const float k0x = F_MUL(c11, p.MN2x), k0y = F_MUL(c11, p.MN2y);
-    const float k1x = F_MUL(c22, p.MP2x), k1y = F_MUL(c22, p.MP2y);
-    const float L00 = det2(k0x, k1x, p.MN1y, p.MP1y);     // k0x*MP1y - k1x*MN1y
-    const float L01 = det2(k1x, k0x, p.MP1x, p.MN1x);     // k1x*MN1x - k0x*MP1x
-    const float L10 = det2(k0y, k1y, p.MN1y, p.MP1y);
-    const float L11 = det2(k1y, k0y, p.MP1x, p.MN1x);
-    const float L20 = F_FMA(-c33, p.NP1y, det2(c11, c22, p.MN1y, p.MP1y));
-    const float L21 = F_FMA(c33, p.NP1x, det2(c22, c11, p.MP1x, p.MN1x));
-    const float L22 = F_MUL(c33, p.fA1);
-    // H = T(M2) * L * T(-M1)
-    const float G02 = -F_FMA(s.M1x, L00, F_MUL(s.M1y, L01));
-    const float G12 = -F_FMA(s.M1x, L10, F_MUL(s.M1y, L11));
-    const float G22 = F_FMA(-s.M1x, L20, F_FMA(-s.M1y, L21, L22));
-    H[0] = F_FMA(s.M2x, L20, L00);
-    H[1] = F_FMA(s.M2x, L21, L01);
-    H[2] = F_FMA(s.M2x, G22, G02);
-    H[3] = F_FMA(s.M2y, L20, L10);
-    H[4] = F_FMA(s.M2y, L21, L11);
-    H[5] = F_FMA(s.M2y, G22, G12);
-    H[6] = L20;
-    H[7] = L21;
-    H[8] = G22;
-}
-
-// The same core and composition as aca_compose with every product and sum
-// after the cross products carried in double-float and H rounded once at the
-// end: the translation back from the anchor frames (H = T(M2) L T(-M1))
-// amplifies relative errors of L by up to |M| / |L|-scale, which a single
-// FP32 rounding of L already turns into >1e-4 of |H| on the worst sets.
-ACA_HD void aca_compose_df(const Set &s, const AcaParts &p, bool prescale, float H[9])
 {
     DF c11 = df_mul(df_prod(p.t1, p.Q3y), p.Q4x);
     DF c22 = df_mul(df_prod(p.t1, p.Q3x), p.Q4y);
@@ -140,25 +110,25 @@ ACA_HD void aca_compose_df(const Set &s, const AcaParts &p, bool prescale, float
     }
     const DF k0x = df_mul(c11, p.MN2x), k0y = df_mul(c11, p.MN2y);
     const DF k1x = df_mul(c22, p.MP2x), k1y = df_mul(c22, p.MP2y);
-    const DF L00 = df_sub(df_mul(k0x, p.MP1y), df_mul(k1x, p.MN1y));
-    const DF L01 = df_sub(df_mul(k1x, p.MN1x), df_mul(k0x, p.MP1x));
-    const DF L10 = df_sub(df_mul(k0y, p.MP1y), df_mul(k1y, p.MN1y));
-    const DF L11 = df_sub(df_mul(k1y, p.MN1x), df_mul(k0y, p.MP1x));
-    const DF L20 = df_sub(df_sub(df_mul(c11, p.MP1y), df_mul(c22, p.MN1y)), df_mul(c33, p.NP1y));
-    const DF L21 = df_add(df_sub(df_mul(c22, p.MN1x), df_mul(c11, p.MP1x)), df_mul(c33, p.NP1x));
-    const DF L22 = df_mul(c33, p.fA1);
-    const DF G02 = df_neg(df_add(df_mul(L00, s.M1x), df_mul(L01, s.M1y)));
-    const DF G12 = df_neg(df_add(df_mul(L10, s.M1x), df_mul(L11, s.M1y)));
-    const DF G22 = df_sub(df_sub(L22, df_mul(L20, s.M1x)), df_mul(L21, s.M1y));
-    H[0] = df_round(df_add(L00, df_mul(L20, s.M2x)));
-    H[1] = df_round(df_add(L01, df_mul(L21, s.M2x)));
-    H[2] = df_round(df_add(G02, df_mul(G22, s.M2x)));
-    H[3] = df_round(df_add(L10, df_mul(L20, s.M2y)));
-    H[4] = df_round(df_add(L11, df_mul(L21, s.M2y)));
-    H[5] = df_round(df_add(G12, df_mul(G22, s.M2y)));
-    H[6] = df_round(L20);
-    H[7] = df_round(L21);
-    H[8] = df_round(G22);
+    const float L00 = df_round(df_sub(df_mul(k0x, p.MP1y), df_mul(k1x, p.MN1y)));
+    const float L01 = df_round(df_sub(df_mul(k1x, p.MN1x), df_mul(k0x, p.MP1x)));
+    const float L10 = df_round(df_sub(df_mul(k0y, p.MP1y), df_mul(k1y, p.MN1y)));
+    const float L11 = df_round(df_sub(df_mul(k1y, p.MN1x), df_mul(k0y, p.MP1x)));
+    const float L20 = df_round(df_sub(df_sub(df_mul(c11, p.MP1y), df_mul(c22, p.MN1y)), df_mul(c33, p.NP1y)));
+    const float L21 = df_round(df_add(df_sub(df_mul(c22, p.MN1x), df_mul(c11, p.MP1x)), df_mul(c33, p.NP1x)));
+    const float L22 = df_round(df_mul(c33, p.fA1));
+    const float G02 = -F_FMA(s.M1x, L00, F_MUL(s.M1y, L01));
+    const float G12 = -F_FMA(s.M1x, L10, F_MUL(s.M1y, L11));
+    const float G22 = F_FMA(-s.M1x, L20, F_FMA(-s.M1y, L21, L22));
+    H[0] = F_FMA(s.M2x, L20, L00);
+    H[1] = F_FMA(s.M2x, L21, L01);
+    H[2] = F_FMA(s.M2x, G22, G02);
+    H[3] = F_FMA(s.M2y, L20, L10);
+    H[4] = F_FMA(s.M2y, L21, L11);
+    H[5] = F_FMA(s.M2y, G22, G12);
+    H[6] = L20;
+    H[7] = L21;
+    H[8] = G22;
 }
 
 ACA_HD uint32_t f2u(float x)
@@ -294,7 +264,8 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 //     b_K = d7 (n8y n7x - n8x n7y) / (d8 (n7x^2 - n7y^2)),
 //     where Q7 = (n7x, n7y) / d7 and Q8 = (n8x, n8y) / d8;
 //   u_K, v_K of Eq. 13; H = H_S2^-1 H_K H_S1 (Eq. 14) composed in the M
-//   frames in double-float and rounded once.
+//   frames in double-float, rounded once per entry, then translated back in
+//   FP32.
 // Differences are exact (TwoSum) and dot / cross products of them carry
 // their remainders.
 // ---------------------------------------------------------------------------
@@ -365,19 +336,23 @@ ACA_HD void sks_solve(const Set &s, float H[9])
     const DF J02 = df_add(G02, df_mul(G22, o2x));
     const DF J10 = df_add(L10, df_mul(A20, o2y)), J11 = df_add(L11, df_mul(A21, o2y));
     const DF J12 = df_add(G12, df_mul(G22, o2y));
-    // then T(M2) J T(-M1)
-    const DF K02 = df_sub(df_sub(J02, df_mul(J00, s.M1x)), df_mul(J01, s.M1y));
-    const DF K12 = df_sub(df_sub(J12, df_mul(J10, s.M1x)), df_mul(J11, s.M1y));
-    const DF K22 = df_sub(df_sub(G22, df_mul(A20, s.M1x)), df_mul(A21, s.M1y));
-    H[0] = df_round(df_add(J00, df_mul(A20, s.M2x)));
-    H[1] = df_round(df_add(J01, df_mul(A21, s.M2x)));
-    H[2] = df_round(df_add(K02, df_mul(K22, s.M2x)));
-    H[3] = df_round(df_add(J10, df_mul(A20, s.M2y)));
-    H[4] = df_round(df_add(J11, df_mul(A21, s.M2y)));
-    H[5] = df_round(df_add(K12, df_mul(K22, s.M2y)));
-    H[6] = df_round(A20);
-    H[7] = df_round(A21);
-    H[8] = df_round(K22);
+    // J is the homography in the M frames, rounded once per entry; then
+    // H = T(M2) J T(-M1) in FP32, as for ACA
+    const float j00 = df_round(J00), j01 = df_round(J01), j02 = df_round(J02);
+    const float j10 = df_round(J10), j11 = df_round(J11), j12 = df_round(J12);
+    const float j20 = df_round(A20), j21 = df_round(A21), j22 = df_round(G22);
+    const float K02 = F_FMA(-s.M1x, j00, F_FMA(-s.M1y, j01, j02));
+    const float K12 = F_FMA(-s.M1x, j10, F_FMA(-s.M1y, j11, j12));
+    const float K22 = F_FMA(-s.M1x, j20, F_FMA(-s.M1y, j21, j22));
+    H[0] = F_FMA(s.M2x, j20, j00);
+    H[1] = F_FMA(s.M2x, j21, j01);
+    H[2] = F_FMA(s.M2x, K22, K02);
+    H[3] = F_FMA(s.M2y, j20, j10);
+    H[4] = F_FMA(s.M2y, j21, j11);
+    H[5] = F_FMA(s.M2y, K22, K12);
+    H[6] = j20;
+    H[7] = j21;
+    H[8] = K22;
 }
 
 // ---------------------------------------------------------------------------

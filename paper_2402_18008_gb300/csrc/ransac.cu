@@ -67,7 +67,7 @@ __device__ __forceinline__ bool make_hypothesis(const float4 *__restrict__ c, ui
     aca_parts(s, p);
     if (sample_degenerate(p))
         return false;
-    aca_compose_df(s, p, true, H);
+    aca_compose(s, p, true, H);
     const float sc = pow2_inv_scale(max_abs9(H));
 #pragma unroll
     for (int i = 0; i < 9; ++i)

@@ -21,7 +21,7 @@ __device__ __forceinline__ void solve_one(const Set &s, float H[9], uint8_t &fla
     if (SOLVER == kAca) {
         AcaParts p;
         aca_parts(s, p);
-        aca_compose_df(s, p, NORM != ACA_NORM_NONE, H);
+        aca_compose(s, p, NORM != ACA_NORM_NONE, H);
         if (NORM == ACA_NORM_H33) normalize_h33(H);
         if (NORM == ACA_NORM_FROB) normalize_frob(H);
         if (FLAGS) flag = aca_flags(s, p, H);
