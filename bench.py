@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-log2", type=int, default=N_LOG2)
     ap.add_argument("--no-rows", action="store_true", help="headline only")
-    ap.add_argument("--rows", default="sks,ransac1,ransac512,diff,latency",
-                    help="comma list of extra rows: sks, ransac1, ransac512, diff, latency")
+    ap.add_argument("--rows", default="sks,affine,ransac1,ransac512,diff,latency",
+                    help="comma list of extra rows: sks, affine, ransac1, ransac512, diff, latency")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ransac-tuning", default="",
                     help="block_warps,hyps_per_thread,tile_points for the RANSAC rows (skips the autotuner)")
@@ -372,6 +372,8 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
     if args.ransac_tuning:
         w, h, t = (int(x) for x in args.ransac_tuning.split(","))
         fixed = dict(block_warps=w, hyps_per_thread=h, tile_points=t)
+    if "affine" in args.row_set:
+        out.update(row_affine(torch, _lib, pts, n, reps, stream))
     if rp is not None:
         out.update(row_ransac1(torch, api, rp, stream, dev, fixed))
     if rb is not None:
@@ -433,6 +435,21 @@ def row_sks(torch, _lib, pts, H, flags, n, reps, stream):
     t = time_region(torch, fl, reps, stream)
     out["aca_solve_with_flags"] = {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
                                    "achieved_gbs": (BYTES_PER_SET + 1) * n / (t * 1e-3) / 1e9}
+    return out
+
+
+def row_affine(torch, _lib, pts, n, reps, stream):
+    """Three-point affine solve (Eq. 38) on the M, N, P points of the same
+    sets: 12 float planes in, 9 out (84 B per set)."""
+    p12 = torch.cat([pts[0:6], pts[8:14]], dim=0).contiguous()
+    A = torch.empty((9, n), dtype=torch.float32, device=pts.device)
+    f = lambda: _lib.aca_affine_solve(p12, A, n=n)
+    for _ in range(3):
+        f()
+    t = time_region(torch, f, reps, stream)
+    out = {"aca_affine_solve": {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
+                                "achieved_gbs": 84 * n / (t * 1e-3) / 1e9, "bytes_per_set": 84}}
+    del p12, A
     return out
 
 

@@ -98,6 +98,18 @@ aca_status aca_rect_solve(const float *tgt, float x0, float y0, float w, float r
                           int64_t ld, void *stream);
 
 /*
+ * aca_affine_solve - batched affine map from three correspondences by the
+ * affine-decomposition of Sec. 5.2 (Eq. 38): H_A = H_A2^-1 H_A1, the ACA
+ * chain with the identity core.
+ *   pts [12][ld] float: M1 N1 P1 (source) then M2 N2 P2 (target), x/y planes.
+ *   H   [9][ld] float: row-major; with ACA_NORM_NONE the division-free form
+ *       with third row (0, 0, f_A1), f_A1 = M1N1 x M1P1; ACA_NORM_H33 gives
+ *       the usual affine matrix with third row (0, 0, 1).  A collinear
+ *       anchor triple gives f_A1 = 0 (singular map, non-finite with H33).
+ */
+aca_status aca_affine_solve(const float *pts, float *H, int64_t n, int64_t ld, int32_t norm, void *stream);
+
+/*
  * aca_backward - vector-Jacobian product of the unnormalised ACA H
  * (aca_solve with ACA_NORM_NONE, Eq. 24-29) with respect to the 8 target
  * coordinates, the source points held fixed.  ACA uses only +, -, * (the

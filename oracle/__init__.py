@@ -60,6 +60,8 @@ def lib():
                          "oracle_aca_jacobian_src", "oracle_aca_condition"):
                 getattr(L, name).argtypes = [_d, _d, ctypes.c_int64]
                 getattr(L, name).restype = None
+            L.oracle_aca_affine.argtypes = [_d, _d, ctypes.c_int64]
+            L.oracle_aca_affine.restype = None
             L.oracle_dlt.argtypes = [_d, _d, ctypes.c_int64]
             L.oracle_dlt.restype = ctypes.c_int64
             for name in ("oracle_aca_rect", "oracle_aca_rect_alg1", "oracle_aca_rect_jacobian"):
@@ -110,6 +112,16 @@ def aca(pts16, n=None):
 def aca_divform(pts16, n=None):
     """ACA with the division-form core (Eq. 23, 26)."""
     return _solve("oracle_aca_divform", pts16, n)
+
+
+def aca_affine(pts12, n=None):
+    """Affine map from three correspondences, Eq. 38: H_A2^-1 H_A1, (n, 9),
+    third row (0, 0, f_A1).  pts12: SoA (12, ld) = M1 N1 P1 M2 N2 P2."""
+    n = pts12.shape[1] if n is None else n
+    a = np.ascontiguousarray(np.asarray(pts12[:, :n], dtype=np.float64).T)
+    H = np.empty((n, 9))
+    lib().oracle_aca_affine(_ptr(a, _d), _ptr(H, _d), n)
+    return H
 
 
 def sks(pts16, n=None):

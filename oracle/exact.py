@@ -165,3 +165,24 @@ def proportional(A, B) -> bool:
         return False
     lam = F(A[k]) / F(B[k])
     return all(F(A[i]) == lam * F(B[i]) for i in range(9))
+
+
+def affine(s12):
+    """Eq. 38, first form: H_A2^-1 H_A1 (s12 = M1 N1 P1 M2 N2 P2)."""
+    s12 = [F(v) for v in s12]
+    M1x, M1y, N1x, N1y, P1x, P1y, M2x, M2y, N2x, N2y, P2x, P2y = s12
+    MN1x, MN1y, MP1x, MP1y = N1x - M1x, N1y - M1y, P1x - M1x, P1y - M1y
+    MN2x, MN2y, MP2x, MP2y = N2x - M2x, N2y - M2y, P2x - M2x, P2y - M2y
+    fA1 = MN1x * MP1y - MN1y * MP1x
+    HA1 = _mm([MP1y, -MP1x, 0, -MN1y, MN1x, 0, 0, 0, fA1], [1, 0, -M1x, 0, 1, -M1y, 0, 0, 1])
+    return _mm([MN2x, MP2x, M2x, MN2y, MP2y, M2y, 0, 0, 1], HA1)
+
+
+def inverse3(A):
+    """Exact inverse of a 3x3 matrix (adjugate / determinant)."""
+    a, b, c, d, e, f, g, h, i = [F(x) for x in A]
+    det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g)
+    adj = [e * i - f * h, c * h - b * i, b * f - c * e,
+           f * g - d * i, a * i - c * g, c * d - a * f,
+           d * h - e * g, b * g - a * h, a * e - b * d]
+    return [x / det for x in adj]

@@ -148,6 +148,35 @@ void oracle_aca_divform(const double *pts, double *H, int64_t n)
 }
 
 /* ------------------------------------------------------------------ */
+/* Affine transformation from three correspondences: Sec. 5.2, Eq. 38   */
+/* ------------------------------------------------------------------ */
+/* H_A = H_A2^-1 H_A1 with H_A1 of Eq. 20 (anchor points M1, N1, P1) and
+ * H_A2^-1 of Eq. 22 (M2, N2, P2): the core is the identity when the map is
+ * affine.  s: 12 doubles M1 N1 P1 M2 N2 P2 (x, y); H: 9 doubles, third row
+ * (0, 0, f_A1) (division-free, like ACA). */
+static void affine_one(const double *s, double *H)
+{
+    const double M1x = s[0], M1y = s[1], N1x = s[2], N1y = s[3], P1x = s[4], P1y = s[5];
+    const double M2x = s[6], M2y = s[7], N2x = s[8], N2y = s[9], P2x = s[10], P2y = s[11];
+    const double MN1x = N1x - M1x, MN1y = N1y - M1y, MP1x = P1x - M1x, MP1y = P1y - M1y;
+    const double MN2x = N2x - M2x, MN2y = N2y - M2y, MP2x = P2x - M2x, MP2y = P2y - M2y;
+    const double fA1 = MN1x * MP1y - MN1y * MP1x;
+    const double L1[9] = {MP1y, -MP1x, 0, -MN1y, MN1x, 0, 0, 0, fA1};
+    const double T1[9] = {1, 0, -M1x, 0, 1, -M1y, 0, 0, 1};
+    double HA1[9];
+    mat3_mul(L1, T1, HA1);
+    const double HA2inv[9] = {MN2x, MP2x, M2x, MN2y, MP2y, M2y, 0, 0, 1};
+    mat3_mul(HA2inv, HA1, H);
+}
+
+void oracle_aca_affine(const double *pts, double *H, int64_t n)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        affine_one(pts + 12 * i, H + 9 * i);
+}
+
+/* ------------------------------------------------------------------ */
 /* DLT: Sec. 2.1, Eq. 1-3, inhomogeneous 8x8 form (h33 = 1) solved by   */
 /* Gaussian elimination with partial pivoting (the GPT-LU solver the    */
 /* paper compares against).  Independent of the ACA code above.         */

@@ -22,7 +22,7 @@ ACA_NORM_NONE, ACA_NORM_H33, ACA_NORM_FROB = 0, 1, 2
 ACA_FLAG_SRC_ANCHORS, ACA_FLAG_TGT_ANCHORS, ACA_FLAG_OTHER_TRIPLE, ACA_FLAG_NON_FINITE = 1, 2, 4, 8
 _STATUS = {0: "ACA_OK", -1: "ACA_ERR_INVALID_ARG", -2: "ACA_ERR_CUDA", -3: "ACA_ERR_WORKSPACE", -4: "ACA_ERR_TIMEOUT"}
 
-EXPORTED = ("aca_solve", "sks_solve", "aca_rect_solve", "aca_backward", "aca_rect_backward",
+EXPORTED = ("aca_solve", "sks_solve", "aca_rect_solve", "aca_affine_solve", "aca_backward", "aca_rect_backward",
             "ransac_aca_workspace_size", "ransac_aca", "ransac_aca_noalloc", "aca_sample_indices", "aca_last_error",
             "aca_version")
 ACA_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
@@ -60,6 +60,7 @@ def load(build_if_missing: bool = True):
         for name in ("aca_solve", "sks_solve"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, i64, i32, vp]
         L.aca_rect_solve.argtypes = [vp, f32, f32, f32, f32, vp, i64, i64, vp]
+        L.aca_affine_solve.argtypes = [vp, vp, i64, i64, i32, vp]
         L.aca_backward.argtypes = [vp, vp, vp, i64, i64, vp]
         L.aca_rect_backward.argtypes = [vp, f32, f32, f32, f32, vp, vp, i64, i64, vp]
         L.ransac_aca_workspace_size.argtypes = [i32, i64]
@@ -142,6 +143,15 @@ def aca_rect_solve(tgt, rect, H, n=None, stream=None):
     n = tgt.shape[1] if n is None else n
     x0, y0, w, r = (float(v) for v in rect)
     _check(load().aca_rect_solve(_ptr(tgt), x0, y0, w, r, _ptr(H), n, ld, ctypes.c_void_p(_stream(stream))))
+
+
+def aca_affine_solve(pts, H, n=None, norm=ACA_NORM_NONE, stream=None):
+    """C ABI aca_affine_solve: (12, ld) planes M1 N1 P1 M2 N2 P2 -> (9, ld)."""
+    _need(pts, "pts", torch.float32, 12)
+    _need(H, "H", torch.float32, 9)
+    ld = _ld(pts, H)
+    n = pts.shape[1] if n is None else n
+    _check(load().aca_affine_solve(_ptr(pts), _ptr(H), n, ld, norm, ctypes.c_void_p(_stream(stream))))
 
 
 def aca_backward(pts, grad_H, grad_tgt, n=None, stream=None):

@@ -356,6 +356,43 @@ ACA_HD void sks_solve(const Set &s, float H[9])
 }
 
 // ---------------------------------------------------------------------------
+// Affine map from three correspondences (Sec. 5.2, Eq. 38): H_A = H_A2^-1
+// H_A1, the ACA chain with the identity core.  In the anchor frames it is
+// L = [[M2N2.x, M2P2.x], [M2N2.y, M2P2.y]] [[M1P1.y, -M1P1.x], [-M1N1.y,
+// M1N1.x]] with f_A1 in the corner; each entry of L is a 2x2 determinant of
+// exact differences (compensated), and the translation column
+// M2 f_A1 - L M1 is summed in double-float.  Third row (0, 0, f_A1).
+// ---------------------------------------------------------------------------
+struct Set3 {
+    float M1x, M1y, N1x, N1y, P1x, P1y;
+    float M2x, M2y, N2x, N2y, P2x, P2y;
+};
+
+ACA_HD void affine_solve(const Set3 &s, float H[9])
+{
+    const Diff mn1x = diff(s.N1x, s.M1x), mn1y = diff(s.N1y, s.M1y);
+    const Diff mp1x = diff(s.P1x, s.M1x), mp1y = diff(s.P1y, s.M1y);
+    const Diff mn2x = diff(s.N2x, s.M2x), mn2y = diff(s.N2y, s.M2y);
+    const Diff mp2x = diff(s.P2x, s.M2x), mp2y = diff(s.P2y, s.M2y);
+    const float fA1 = cross2x(mn1x, mn1y, mp1x, mp1y);            // Eq. 21
+    const float L00 = cross2x(mn2x, mp2x, mn1y, mp1y);            // MN2x MP1y - MP2x MN1y
+    const float L01 = cross2x(mp2x, mn2x, mp1x, mn1x);            // MP2x MN1x - MN2x MP1x
+    const float L10 = cross2x(mn2y, mp2y, mn1y, mp1y);
+    const float L11 = cross2x(mp2y, mn2y, mp1x, mn1x);
+    const DF t0 = df_sub(df_sub(df_prod(s.M2x, fA1), df_prod(s.M1x, L00)), df_prod(s.M1y, L01));
+    const DF t1 = df_sub(df_sub(df_prod(s.M2y, fA1), df_prod(s.M1x, L10)), df_prod(s.M1y, L11));
+    H[0] = L00;
+    H[1] = L01;
+    H[2] = df_round(t0);
+    H[3] = L10;
+    H[4] = L11;
+    H[5] = df_round(t1);
+    H[6] = 0.0f;
+    H[7] = 0.0f;
+    H[8] = fA1;
+}
+
+// ---------------------------------------------------------------------------
 // Rectangle source (Sec. 5.3, Eq. 39-42): M1 = (x0, y0) upper-left corner,
 // width w, aspect ratio r = width / height; target corners M2 N2 P2 Q2.
 // ---------------------------------------------------------------------------

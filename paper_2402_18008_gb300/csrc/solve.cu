@@ -209,9 +209,110 @@ __global__ void __launch_bounds__(256) rect_scalar_kernel(const float *__restric
     }
 }
 
+// --------------------------------------------------------------------------
+// Affine map from three correspondences (Eq. 38): 12 planes in, 9 out.
+// --------------------------------------------------------------------------
+template <int NORM>
+__device__ __forceinline__ void affine_one(const Set3 &s, float H[9])
+{
+    affine_solve(s, H);
+    if (NORM == ACA_NORM_H33) normalize_h33(H);
+    if (NORM == ACA_NORM_FROB) normalize_frob(H);
+}
+
+template <int NORM>
+__global__ void __launch_bounds__(256) affine_vec4_kernel(const float *__restrict__ pts, float *__restrict__ Hout,
+                                                           int64_t n, int64_t ld)
+{
+    const int64_t nq = (n + 3) >> 2, ldq = ld >> 2;
+    const float4 *in = reinterpret_cast<const float4 *>(pts);
+    float4 *out = reinterpret_cast<float4 *>(Hout);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        float4 v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            v[k] = ld_stream(in + k * ldq + q);
+        float4 h[9];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Set3 s;
+            float *sv = &s.M1x;
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                sv[k] = (&v[k].x)[j];
+            float H[9];
+            affine_one<NORM>(s, H);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                (&h[k].x)[j] = H[k];
+        }
+        const int64_t i0 = q << 2;
+        if (i0 + 3 < n) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                st_stream(out + k * ldq + q, h[k]);
+        } else {
+            for (int j = 0; j < 4 && i0 + j < n; ++j)
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    Hout[k * ld + i0 + j] = (&h[k].x)[j];
+        }
+    }
+}
+
+template <int NORM>
+__global__ void __launch_bounds__(256) affine_scalar_kernel(const float *__restrict__ pts, float *__restrict__ Hout,
+                                                             int64_t n, int64_t ld)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Set3 s;
+        float *sv = &s.M1x;
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            sv[k] = ld_stream(pts + k * ld + i);
+        float H[9];
+        affine_one<NORM>(s, H);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            st_stream(Hout + k * ld + i, H[k]);
+    }
+}
+
+template <int NORM>
+static aca_status launch_affine(const float *pts, float *H, int64_t n, int64_t ld, cudaStream_t st)
+{
+    const int threads = 256;
+    if (n >= kSmallBatch && ld % 4 == 0 && aligned16(pts) && aligned16(H)) {
+        auto k = affine_vec4_kernel<NORM>;
+        const int grid = resident_grid(k, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
+        k<<<grid, threads, 0, st>>>(pts, H, n, ld);
+    } else {
+        auto k = affine_scalar_kernel<NORM>;
+        const int grid = resident_grid(k, threads, 0, (n + threads - 1) / threads);
+        k<<<grid, threads, 0, st>>>(pts, H, n, ld);
+    }
+    return check_launch("aca_affine_solve");
+}
+
 }  // namespace aca
 
 using namespace aca;
+
+extern "C" aca_status aca_affine_solve(const float *pts, float *H, int64_t n, int64_t ld, int32_t norm, void *stream)
+{
+    if (n < 0 || ld < n)
+        return set_error(ACA_ERR_INVALID_ARG, "aca_affine_solve: need 0 <= n <= ld");
+    if (norm < ACA_NORM_NONE || norm > ACA_NORM_FROB)
+        return set_error(ACA_ERR_INVALID_ARG, "aca_affine_solve: unknown norm %d", norm);
+    if (n == 0)
+        return ACA_OK;
+    if (!pts || !H)
+        return set_error(ACA_ERR_INVALID_ARG, "aca_affine_solve: null pts or H");
+    const cudaStream_t st = as_stream(stream);
+    if (norm == ACA_NORM_NONE) return launch_affine<ACA_NORM_NONE>(pts, H, n, ld, st);
+    if (norm == ACA_NORM_H33) return launch_affine<ACA_NORM_H33>(pts, H, n, ld, st);
+    return launch_affine<ACA_NORM_FROB>(pts, H, n, ld, st);
+}
 
 extern "C" aca_status aca_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int64_t ld, int32_t norm,
                                 void *stream)

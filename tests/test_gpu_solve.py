@@ -181,3 +181,36 @@ def test_api_solve_and_layout_helpers():
     H, fl = api.solve(pts, norm=_lib.ACA_NORM_FROB, with_flags=True)
     M = api.planes_to_mats(H, 64).cpu().numpy().reshape(64, 9)
     assert np.abs(M - oracle.normalize_frob(oracle.aca(ms.pts))).max() < H_TOL
+
+
+def _affine_planes(ms):
+    return np.ascontiguousarray(np.concatenate([ms.pts[0:6], ms.pts[8:14]], axis=0))
+
+
+@pytest.mark.parametrize("n,ld", [(1, 1), (5, 8), (4096, 4096), (1023, 1023), ((1 << 18) + 3, (1 << 18) + 4)])
+def test_affine_three_point_solver_parity(n, ld):
+    ms = workloads.minimal_sets(n, seed=10)
+    p12 = _affine_planes(ms)
+    pts = torch.zeros((12, ld), dtype=torch.float32, device="cuda")
+    pts[:, :n] = cuda(p12)
+    H = torch.full((9, ld), 12345.0, dtype=torch.float32, device="cuda")
+    _lib.aca_affine_solve(pts, H, n=n)
+    torch.cuda.synchronize()
+    h = planes_to_rows(H, n)
+    err = unit_aligned_err(h, oracle.aca_affine(p12))
+    print(f"affine n={n}: max {err.max():.3e}")
+    assert err.max() < H_TOL
+    assert np.all(h[:, 6] == 0) and np.all(h[:, 7] == 0)
+    if ld > n:
+        assert torch.all(H[:, n:] == 12345.0)
+    H33 = torch.empty((9, ld), dtype=torch.float32, device="cuda")
+    _lib.aca_affine_solve(pts, H33, n=n, norm=_lib.ACA_NORM_H33)
+    torch.cuda.synchronize()
+    a = planes_to_rows(H33, n)
+    assert np.all(a[:, 8] == 1.0) and np.all(a[:, 6:8] == 0)
+    # the affine map sends M1, N1, P1 to M2, N2, P2 (to FP32 accuracy)
+    s = p12.astype(np.float64)
+    for k in range(3):
+        X = a[:, 0] * s[2 * k] + a[:, 1] * s[2 * k + 1] + a[:, 2]
+        Y = a[:, 3] * s[2 * k] + a[:, 4] * s[2 * k + 1] + a[:, 5]
+        assert np.max(np.hypot(X - s[6 + 2 * k], Y - s[7 + 2 * k])) < 1e-2

@@ -219,3 +219,47 @@ def test_fp64_oracle_reprojects_the_four_points():
         y = np.einsum("nij,nj->ni", H, x)
         err = np.hypot(y[:, 0] / y[:, 2] - s[:, 8 + 2 * k], y[:, 1] / y[:, 2] - s[:, 9 + 2 * k])
         assert err.max() < 1e-8
+
+
+def _affine_sets(k, seed):
+    rnd = random.Random(seed)
+    out = []
+    while len(out) < k:
+        s = [rnd.randint(0, 640) for _ in range(12)]
+        a = ((s[2] - s[0]) * (s[5] - s[1]) - (s[3] - s[1]) * (s[4] - s[0]))
+        b = ((s[8] - s[6]) * (s[11] - s[7]) - (s[9] - s[7]) * (s[10] - s[6]))
+        if a != 0 and b != 0:
+            out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("s", _affine_sets(20, 41))
+def test_exact_affine_maps_the_three_points_and_equals_eq38_second_form(s):
+    H = exact.affine(s)
+    assert H[6] == 0 and H[7] == 0 and H[8] != 0
+    for k in range(3):
+        u, v, w = exact.apply(H, F(s[2 * k]), F(s[2 * k + 1]))
+        assert (u / w, v / w) == (s[6 + 2 * k], s[7 + 2 * k])
+    # Eq. 38 second form: [N2 P2 M2; 1 1 1] [N1 P1 M1; 1 1 1]^-1
+    A2 = [s[8], s[10], s[6], s[9], s[11], s[7], 1, 1, 1]
+    A1 = [s[2], s[4], s[0], s[3], s[5], s[1], 1, 1, 1]
+    assert exact.proportional(H, exact._mm(A2, exact.inverse3(A1)))
+
+
+def test_affine_equals_aca_for_an_affine_fourth_point():
+    for s in _affine_sets(10, 42):
+        H = exact.affine(s)
+        # fourth correspondence Q consistent with the affine map
+        q = (F(s[0] + s[2]) / 3 + 7, F(s[1] + s[5]) / 5 - 3)
+        u, v, w = exact.apply(H, q[0], q[1])
+        s16 = s[0:6] + [q[0], q[1]] + s[6:12] + [u / w, v / w]
+        assert exact.proportional(exact.aca(s16), H)
+
+
+def test_fp64_affine_oracle_matches_exact():
+    sets = _affine_sets(50, 43)
+    pts = np.array(sets, dtype=np.float64).T.copy()
+    Ho = oracle.aca_affine(pts)
+    for k, s in enumerate(sets):
+        He = np.array([float(x) for x in exact.affine(s)])
+        assert np.max(np.abs(Ho[k] - He)) <= 1e-12 * np.abs(He).max()
