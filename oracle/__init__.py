@@ -248,3 +248,7 @@ def ransac(corr, offsets, n_hyp, thr: float, seed: int, problem_base: int = 0, b
                         _ptr(counts, _i32), _ptr(band, _i32), band_px, herr, _ptr(mask, _u8))
     return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, hyp_counts=counts,
                 band_counts=band, inlier_mask=mask)
+
+
+
+from .refit import hartley_normalization, refit, refit_dlt, refit_lm, reprojection_cost  # noqa: E402,F401
