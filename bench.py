@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-log2", type=int, default=N_LOG2)
     ap.add_argument("--no-rows", action="store_true", help="headline only")
-    ap.add_argument("--rows", default="sks,affine,ransac1,ransac512,diff,latency",
-                    help="comma list of extra rows: sks, affine, ransac1, ransac512, diff, latency")
+    ap.add_argument("--rows", default="sks,affine,ransac1,ransac512,refit,diff,latency",
+                    help="comma list of extra rows: sks, affine, ransac1, ransac512, refit, diff, latency")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ransac-tuning", default="",
                     help="block_warps,hyps_per_thread,tile_points for the RANSAC rows (skips the autotuner)")
@@ -274,7 +274,7 @@ def main():
     rows_on = not args.no_rows and world == 1
     args.row_set = set(r for r in args.rows.split(",") if r) if rows_on else set()
     rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=SEED) if "ransac1" in args.row_set else None
-    rb = workloads.ransac_batch(512, seed=SEED) if "ransac512" in args.row_set else None
+    rb = workloads.ransac_batch(512, seed=SEED) if args.row_set & {"ransac512", "refit"} else None
     rect = workloads.rect_batch(65536, seed=SEED) if "diff" in args.row_set else None
 
     import torch
@@ -376,8 +376,10 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
         out.update(row_affine(torch, _lib, pts, n, reps, stream))
     if rp is not None:
         out.update(row_ransac1(torch, api, rp, stream, dev, fixed))
-    if rb is not None:
+    if rb is not None and "ransac512" in args.row_set:
         out.update(row_ransac512(torch, api, rb, stream, dev, fixed, not args.no_plain))
+    if rb is not None and "refit" in args.row_set:
+        out.update(row_refit(torch, _lib, api, rb, stream, dev, fixed))
     if rect is not None:
         out.update(row_diff(torch, _lib, rect, stream, dev))
     if "latency" in args.row_set:
@@ -514,6 +516,42 @@ def row_ransac512(torch, api, rb, stream, dev, fixed=None, plain=True):
     res.update(ms_512_plain_launches=tp, speedup_vs_plain=tp / t3, batched_equals_plain=same)
     out["ransac_batched_512"] = res
     return out
+
+
+def row_refit(torch, _lib, api, rb, stream, dev, fixed=None):
+    """Refit on all inliers (aca_refit) over the 512 pairs of the batched
+    RANSAC workload: with the generated inlier masks alone (DLT only and DLT
+    + 10 LM steps), and appended to the batched RANSAC in one CUDA graph."""
+    P = len(rb.n_hyp)
+    corr = torch.from_numpy(rb.corr).to(dev)
+    off = torch.from_numpy(rb.offsets).to(dev)
+    mask = torch.from_numpy(rb.is_inlier.astype(np.uint8)).to(dev)
+    H = torch.empty((P, 9), dtype=torch.float32, device=dev)
+    used = int(rb.is_inlier.sum())
+    res = {"unit": "used points/s", "pairs": P, "used_points": used,
+           "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9]; masks = generated inliers"}
+    for iters in (0, 10):
+        f = lambda: _lib.aca_refit(corr, off, H, mask=mask, lm_iters=iters)
+        for _ in range(3):
+            f()
+        t = time_region(torch, f, 20, stream)
+        res[f"ms_lm{iters}"] = t
+        if iters == 10:
+            res["value"] = used / (t * 1e-3)
+    tot = int(rb.n_hyp.sum())
+    k = torch.from_numpy(rb.n_hyp).to(dev)
+    from paper_2402_18008_gb300 import autotune
+    make = lambda **kw: api.RansacPlan(corr, off, k, RANSAC_THR, SEED, tot, **kw)
+    best = fixed or autotune.tune(make, P, int(rb.offsets[-1]), tot, device=dev)[0]
+    times = {}
+    for name, kw in (("ransac_only", {"want_mask": True}), ("ransac_plus_refit", {"refit_iters": 10})):
+        plan = make(**best, **kw).capture()
+        for _ in range(3):
+            plan.replay()
+        times[name] = time_region(torch, plan.replay, 20, stream)
+    res.update(ms_ransac_with_mask=times["ransac_only"], ms_ransac_plus_refit=times["ransac_plus_refit"],
+               refit_share_of_pipeline=1.0 - times["ransac_only"] / times["ransac_plus_refit"])
+    return {"refit_512": res}
 
 
 def row_diff(torch, _lib, rect, stream, dev):

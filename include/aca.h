@@ -236,6 +236,42 @@ aca_status ransac_aca_noalloc(const float *corr, const int64_t *offsets, const i
 aca_status aca_sample_indices(int64_t N, int32_t n_hyp, uint64_t seed, uint32_t problem, int32_t *idx,
                               void *stream);
 
+/*
+ * aca_refit - re-estimate one homography per problem from ALL of its masked
+ * correspondences: the global optimisation with all inliers that follows
+ * the RANSAC loop (Sec. 6.2, stage 5, where it is a Levenberg-Marquardt
+ * minimisation).  Per problem:
+ *   1. Hartley normalisation of each image (centroid to the origin, mean
+ *      distance sqrt(2));
+ *   2. the normalised DLT: h minimises the algebraic residual of the two
+ *      Eq. 2 rows of every point under |h| = 1 (smallest eigenvector of the
+ *      9x9 normal matrix, FP64 inverse iteration);
+ *   3. lm_iters trial steps of Levenberg-Marquardt on the reprojection error
+ *      sum_i |pi(H x1_i) - x2_i|^2 (eight entries with h33 = 1 in the
+ *      normalised frames; damping of Madsen, Nielsen & Tingleff 2004,
+ *      Alg. 3.16), stopping early once a step is below FP32 resolution.
+ *      It is skipped when the normalised DLT has |h33| < 1e-3.
+ *   corr     [total][4] float (x1, y1, x2, y2), the points of problem p at rows
+ *            offsets[p] .. offsets[p+1]-1; 16-byte aligned (device memory).
+ *   offsets  [P+1] int64, offsets[0] = 0, non-decreasing (device memory).
+ *   mask     [total] uint8 or NULL: nonzero = use the point (e.g. the
+ *            inlier_mask of ransac_aca); NULL uses every point.
+ *   lm_iters 0..10000 trial steps (0: the normalised DLT only).
+ *   H        [P][9] float out: row-major, unit Frobenius norm, h33 > 0 (or the
+ *            largest entry > 0 when |h33| < 1e-6); all zeros for a problem
+ *            with fewer than 4 used points.
+ *   n_used   [P] int32 out or NULL: number of used points.
+ *   rms      [P] float out or NULL: RMS reprojection error in pixels of the
+ *            returned H over the used points (-1 when step 3 was skipped).
+ * One block per problem, all buffers caller-owned, nothing allocated.
+ * Points in general position are assumed: with all used points collinear
+ * the minimiser is not unique and H is one of them.  Returns
+ * ACA_ERR_INVALID_ARG for P < 0, lm_iters outside its range, a null or
+ * misaligned buffer; ACA_ERR_CUDA if the launch fails.
+ */
+aca_status aca_refit(const float *corr, const int64_t *offsets, const uint8_t *mask, int32_t P, int32_t lm_iters,
+                     float *H, int32_t *n_used, float *rms, void *stream);
+
 /* Message describing the last non-OK status returned on this thread. */
 const char *aca_last_error(void);
 

@@ -9,7 +9,9 @@ generators, none of the method's arithmetic) serves both.
 ``oracle.c`` holds the FP64 implementations (ACA Eq. 20-29, the independent
 8x8 DLT of Eq. 2, SKS Eq. 4-14, the rectangle form Eq. 42 / Algorithm 1,
 Philox sampling, brute-force RANSAC scoring and the analytic Jacobian);
-``exact.py`` holds exact-rational versions used by the pins.
+``exact.py`` holds exact-rational versions used by the pins;
+``inlier_refit.py`` the float64 refit on all inliers (normalised DLT, then
+Levenberg-Marquardt: the global optimisation of Sec. 6.2, stage 5).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (exact agreement with an independent DLT, invariants, special cases, cuRAND's
@@ -251,4 +253,4 @@ def ransac(corr, offsets, n_hyp, thr: float, seed: int, problem_base: int = 0, b
 
 
 
-from .refit import hartley_normalization, refit, refit_dlt, refit_lm, reprojection_cost  # noqa: E402,F401
+from .inlier_refit import hartley_normalization, refit, refit_dlt, refit_lm, refit_tolerance, reprojection_cost  # noqa: E402,F401

@@ -53,13 +53,13 @@ def _homog(xy):
 
 def _dlt_normalized(x, X) -> np.ndarray:
     """Smallest right singular vector of the Eq. 2 rows of normalised points."""
-    A = np.zeros((2 * len(x), 9))
+    A = np.zeros((max(2 * len(x), 9), 9))     # a zero row keeps 9 singular vectors for n = 4
     xh = _homog(x)
-    A[0::2, 0:3] = xh
-    A[0::2, 6:9] = -X[:, 0:1] * xh
-    A[1::2, 3:6] = -xh
-    A[1::2, 6:9] = X[:, 1:2] * xh
-    return np.linalg.svd(A)[2][-1].reshape(3, 3)
+    A[0:2 * len(x):2, 0:3] = xh
+    A[0:2 * len(x):2, 6:9] = -X[:, 0:1] * xh
+    A[1:2 * len(x):2, 3:6] = -xh
+    A[1:2 * len(x):2, 6:9] = X[:, 1:2] * xh
+    return np.linalg.svd(A, full_matrices=False)[2][-1].reshape(3, 3)
 
 
 def _frame(sel):
@@ -173,4 +173,24 @@ def reprojection_cost(H, corr, offsets, mask) -> np.ndarray:
         with np.errstate(divide="ignore", invalid="ignore"):
             e = (q[0] / q[2] - sel[:, 2]) ** 2 + (q[1] / q[2] - sel[:, 3]) ** 2
         out[p] = np.sum(e) if np.all(np.isfinite(e)) else np.inf
+    return out
+
+
+def refit_tolerance(corr, offsets, mask, lm_iters: int = 200, draws: int = 4, rel: float = 16 * 2.0 ** -24,
+                    seed: int = 0) -> np.ndarray:
+    """Per-problem conditioning of the refit: the largest entry-wise movement
+    of the unit-Frobenius H when every input coordinate is moved by `rel`
+    relative (random signs, `draws` draws, rounded back to float32).  An FP32
+    evaluation is backward stable with errors of a few units of 2^-24 in the
+    normalised coordinates, so its distance from the float64 result is of
+    the order of this movement."""
+    c = np.asarray(corr, dtype=np.float32)
+    H0, _ = refit(c, offsets, mask, lm_iters)
+    rng = np.random.default_rng(seed)
+    out = np.zeros(H0.shape[0])
+    for _ in range(draws):
+        s = rng.choice([-1.0, 1.0], size=c.shape)
+        cp = (c.astype(np.float64) * (1.0 + rel * s)).astype(np.float32)
+        H1, _ = refit(cp, offsets, mask, lm_iters)
+        out = np.maximum(out, np.max(np.abs(H1 - H0), axis=1))
     return out

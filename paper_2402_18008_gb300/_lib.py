@@ -23,8 +23,8 @@ ACA_FLAG_SRC_ANCHORS, ACA_FLAG_TGT_ANCHORS, ACA_FLAG_OTHER_TRIPLE, ACA_FLAG_NON_
 _STATUS = {0: "ACA_OK", -1: "ACA_ERR_INVALID_ARG", -2: "ACA_ERR_CUDA", -3: "ACA_ERR_WORKSPACE", -4: "ACA_ERR_TIMEOUT"}
 
 EXPORTED = ("aca_solve", "sks_solve", "aca_rect_solve", "aca_affine_solve", "aca_backward", "aca_rect_backward",
-            "ransac_aca_workspace_size", "ransac_aca", "ransac_aca_noalloc", "aca_sample_indices", "aca_last_error",
-            "aca_version")
+            "ransac_aca_workspace_size", "ransac_aca", "ransac_aca_noalloc", "aca_sample_indices", "aca_refit",
+            "aca_last_error", "aca_version")
 ACA_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 
 
@@ -69,6 +69,7 @@ def load(build_if_missing: bool = True):
                                  ctypes.c_size_t, vp]
         L.aca_sample_indices.argtypes = [i64, i32, ctypes.c_uint64, ctypes.c_uint32, vp, vp]
         L.ransac_aca_noalloc.argtypes = [vp, vp, vp, i32, i64, ctypes.POINTER(RansacParams), vp, vp, vp, vp, vp, vp]
+        L.aca_refit.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("ransac_aca_workspace_size", "aca_last_error", "aca_version"):
                 getattr(L, name).restype = ctypes.c_int
@@ -245,3 +246,28 @@ def ransac_aca_noalloc(corr, offsets, n_hyp, total_hyps: int, params: RansacPara
     _check(load().ransac_aca_noalloc(_ptr(corr), _ptr(offsets), _ptr(n_hyp), P, int(total_hyps), ctypes.byref(params),
                                      _ptr(best_H), _ptr(best_count), _ptr(best_hyp), _ptr(hyp_counts),
                                      _ptr(inlier_mask), ctypes.c_void_p(_stream(stream))))
+
+
+def aca_refit(corr, offsets, H, mask=None, lm_iters=10, n_used=None, rms=None, stream=None):
+    """C ABI aca_refit.  corr (total, 4) float32; offsets (P+1,) int64;
+    mask (total,) uint8 or None (every point); outputs H (P, 9) float32,
+    n_used (P,) int32 and rms (P,) float32, the last two optional."""
+    _need(corr, "corr", torch.float32)
+    _need(offsets, "offsets", torch.int64)
+    _need(H, "H", torch.float32)
+    if corr.dim() != 2 or corr.shape[1] != 4 or not corr.is_contiguous():
+        raise ValueError("corr must be a contiguous (total, 4) tensor")
+    P = offsets.numel() - 1
+    if P < 0 or not offsets.is_contiguous() or not H.is_contiguous() or H.numel() < 9 * P:
+        raise ValueError("offsets must be (P+1,) and H a contiguous (P, 9) tensor")
+    if mask is not None:
+        _need(mask, "mask", torch.uint8)
+        if mask.numel() < corr.shape[0] or not mask.is_contiguous():
+            raise ValueError("mask must be a contiguous (total,) tensor")
+    for t, nm, dt in ((n_used, "n_used", torch.int32), (rms, "rms", torch.float32)):
+        if t is not None:
+            _need(t, nm, dt)
+            if t.numel() < P or not t.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous (P,) tensor")
+    _check(load().aca_refit(_ptr(corr), _ptr(offsets), _ptr(mask), P, int(lm_iters), _ptr(H), _ptr(n_used),
+                            _ptr(rms), ctypes.c_void_p(_stream(stream))))

@@ -63,6 +63,8 @@ class RansacResult:
     best_hyp: torch.Tensor    # (P,) int32
     hyp_counts: torch.Tensor | None
     inlier_mask: torch.Tensor | None
+    refit_H: torch.Tensor | None = None     # (P, 9) after the refit on all inliers
+    refit_rms: torch.Tensor | None = None   # (P,) RMS reprojection error (px) of refit_H
 
 
 class RansacPlan:
@@ -70,15 +72,18 @@ class RansacPlan:
     batch layout (P problems, total_hyps hypotheses, total points).
 
     ``run()`` enqueues one full RANSAC (prep, scoring, argmax) on the current
-    stream; ``capture()`` records it into a CUDA graph and ``replay()``
-    launches that graph.
+    stream, followed, when ``refit_iters`` is not None, by the refit of each
+    best H on all of its inliers (aca_refit with that many LM steps);
+    ``capture()`` records it into a CUDA graph and ``replay()`` launches that
+    graph.
     """
 
     def __init__(self, corr: torch.Tensor, offsets: torch.Tensor, n_hyp: torch.Tensor, threshold_px: float,
                  seed: int, total_hyps: int, problem_base: int = 0, block_warps: int = 0,
                  hyps_per_thread: int = 0, tile_points: int = 0, grid_blocks: int = 0,
-                 want_counts: bool = False, want_mask: bool = False):
+                 want_counts: bool = False, want_mask: bool = False, refit_iters: int | None = None):
         _require_cuda(corr, "corr")
+        want_mask = want_mask or refit_iters is not None
         dev = corr.device
         self.corr, self.offsets, self.n_hyp = corr, offsets, n_hyp
         self.P = n_hyp.numel()
@@ -93,11 +98,17 @@ class RansacPlan:
         self.best_hyp = torch.empty(self.P, dtype=torch.int32, device=dev)
         self.hyp_counts = torch.empty(max(int(total_hyps), 1), dtype=torch.int32, device=dev) if want_counts else None
         self.inlier_mask = torch.empty(max(corr.shape[0], 1), dtype=torch.uint8, device=dev) if want_mask else None
+        self.refit_iters = refit_iters
+        self.refit_H = torch.empty((self.P, 9), dtype=torch.float32, device=dev) if refit_iters is not None else None
+        self.refit_rms = torch.empty(self.P, dtype=torch.float32, device=dev) if refit_iters is not None else None
         self.graph = None
 
     def run(self) -> RansacResult:
         _lib.ransac_aca(self.corr, self.offsets, self.n_hyp, self.params, self.best_H, self.best_count,
                         self.best_hyp, self.workspace, hyp_counts=self.hyp_counts, inlier_mask=self.inlier_mask)
+        if self.refit_iters is not None:
+            _lib.aca_refit(self.corr, self.offsets, self.refit_H, mask=self.inlier_mask, lm_iters=self.refit_iters,
+                           rms=self.refit_rms)
         return self.result()
 
     def capture(self, warmup: int = 1) -> "RansacPlan":
@@ -118,15 +129,30 @@ class RansacPlan:
         return self.result()
 
     def result(self) -> RansacResult:
-        return RansacResult(self.best_H, self.best_count, self.best_hyp, self.hyp_counts, self.inlier_mask)
+        return RansacResult(self.best_H, self.best_count, self.best_hyp, self.hyp_counts, self.inlier_mask,
+                            self.refit_H, self.refit_rms)
 
 
 def ransac(corr: torch.Tensor, offsets: torch.Tensor, n_hyp: torch.Tensor, threshold_px: float, seed: int,
            total_hyps: int | None = None, want_counts: bool = False, want_mask: bool = False,
-           **tuning) -> RansacResult:
-    """One-shot RANSAC over CSR problems (see include/aca.h, ransac_aca)."""
+           refit_iters: int | None = None, **tuning) -> RansacResult:
+    """One-shot RANSAC over CSR problems (see include/aca.h, ransac_aca),
+    optionally followed by the refit on all inliers (refit_iters LM steps)."""
     if total_hyps is None:
         total_hyps = int(n_hyp.sum().item())
     plan = RansacPlan(corr, offsets, n_hyp, threshold_px, seed, total_hyps, want_counts=want_counts,
-                      want_mask=want_mask, **tuning)
+                      want_mask=want_mask, refit_iters=refit_iters, **tuning)
     return plan.run()
+
+
+def refit(corr: torch.Tensor, offsets: torch.Tensor, mask: torch.Tensor | None = None, lm_iters: int = 10):
+    """Homography per problem from all masked points: normalised DLT, then
+    lm_iters Levenberg-Marquardt steps (include/aca.h, aca_refit).  Returns
+    (H (P, 9), n_used (P,), rms (P,))."""
+    _require_cuda(corr, "corr")
+    P = offsets.numel() - 1
+    H = torch.empty((P, 9), dtype=torch.float32, device=corr.device)
+    n_used = torch.empty(P, dtype=torch.int32, device=corr.device)
+    rms = torch.empty(P, dtype=torch.float32, device=corr.device)
+    _lib.aca_refit(corr, offsets, H, mask=mask, lm_iters=lm_iters, n_used=n_used, rms=rms)
+    return H, n_used, rms

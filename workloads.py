@@ -241,6 +241,7 @@ class RansacBatch:
     n_hyp: np.ndarray      # int32 (P,)
     inlier_ratio: np.ndarray
     sigma: np.ndarray
+    is_inlier: np.ndarray  # bool (total,): the point was generated from the true H
 
 
 def ransac_batch(P: int = 512, seed: int = 0, n_min: int = 200, n_max: int = 8000,
@@ -253,12 +254,14 @@ def ransac_batch(P: int = 512, seed: int = 0, n_min: int = 200, n_max: int = 800
     Ns = np.exp(rng.uniform(math.log(n_min), math.log(n_max), P)).round().astype(np.int64)
     eps = rng.uniform(eps_lo, eps_hi, P)
     sig = rng.uniform(sigma_lo, sigma_hi, P)
-    parts = [ransac_problem(int(Ns[p]), float(eps[p]), float(sig[p]), seed, stream=p + 1).corr for p in range(P)]
+    probs = [ransac_problem(int(Ns[p]), float(eps[p]), float(sig[p]), seed, stream=p + 1) for p in range(P)]
+    parts = [pr.corr for pr in probs]
     offsets = np.zeros(P + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(Ns)
     n_hyp = np.array([adaptive_hypotheses(float(e), cap=cap) for e in eps], dtype=np.int32)
     return RansacBatch(corr=np.ascontiguousarray(np.concatenate(parts, axis=0)), offsets=offsets,
-                       n_hyp=n_hyp, inlier_ratio=eps, sigma=sig)
+                       n_hyp=n_hyp, inlier_ratio=eps, sigma=sig,
+                       is_inlier=np.concatenate([pr.is_inlier for pr in probs]))
 
 
 # --------------------------------------------------------------------------
