@@ -8,7 +8,8 @@ generators, none of the method's arithmetic) serves both.
 
 ``oracle.c`` holds the FP64 implementations (ACA Eq. 20-29, the independent
 8x8 DLT of Eq. 2, SKS Eq. 4-14, the rectangle form Eq. 42 / Algorithm 1,
-Philox sampling, brute-force RANSAC scoring and the analytic Jacobian);
+Philox sampling, brute-force RANSAC scoring, the online adaptive stop of
+Sec. 6.2 and the analytic Jacobian);
 ``exact.py`` holds exact-rational versions used by the pins;
 ``inlier_refit.py`` the float64 refit on all inliers (normalised DLT, then
 Levenberg-Marquardt: the global optimisation of Sec. 6.2, stage 5).
@@ -81,6 +82,13 @@ def lib():
             L.oracle_ransac.argtypes = [_f, _i64, _i32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
                                         ctypes.c_uint32, _d, _i32, _i32, _i32, _i32, ctypes.c_double,
                                         ctypes.c_double, _u8]
+            L.oracle_adaptive_k.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_double]
+            L.oracle_adaptive_k.restype = ctypes.c_int32
+            L.oracle_adaptive_stop.argtypes = [_i32, ctypes.c_int32, ctypes.c_int64, ctypes.c_double]
+            L.oracle_adaptive_stop.restype = ctypes.c_int32
+            L.oracle_ransac_adaptive.argtypes = [_f, _i64, _i32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
+                                                 ctypes.c_uint32, ctypes.c_double, _d, _i32, _i32, _i32, _i32,
+                                                 _i32, ctypes.c_double, ctypes.c_double, _u8]
             _lib = L
     return _lib
 
@@ -251,6 +259,45 @@ def ransac(corr, offsets, n_hyp, thr: float, seed: int, problem_base: int = 0, b
     return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, hyp_counts=counts,
                 band_counts=band, inlier_mask=mask)
 
+
+
+def adaptive_k(c: int, N: int, cap: int, confidence: float = 0.99) -> int:
+    """Hypotheses required by the online stop rule for a best count c of N
+    (see oracle_adaptive_k)."""
+    return int(lib().oracle_adaptive_k(int(c), int(N), int(cap), float(np.log(1.0 - confidence))))
+
+
+def adaptive_stop(counts, N: int, confidence: float = 0.99) -> int:
+    """Number of hypotheses the sequential loop evaluates over `counts`
+    (cap = len(counts)); see oracle_adaptive_stop."""
+    c = np.ascontiguousarray(counts, dtype=np.int32)
+    return int(lib().oracle_adaptive_stop(_ptr(c, _i32), c.size, int(N), float(np.log(1.0 - confidence))))
+
+
+def ransac_adaptive(corr, offsets, max_hyp, thr: float, seed: int, confidence: float = 0.99,
+                    problem_base: int = 0, band_px: float = 1e-4, want_mask: bool = False,
+                    herr: float = 0.0) -> dict:
+    """RANSAC with the online stop (oracle_ransac_adaptive): counts and band
+    counts of all max_hyp hypotheses, n_eval, and the best over the evaluated
+    ones."""
+    c = np.ascontiguousarray(corr, dtype=np.float32)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    k = np.ascontiguousarray(max_hyp, dtype=np.int32)
+    P = k.shape[0]
+    tot = int(k.sum())
+    best_H = np.empty((P, 9))
+    best_count = np.empty(P, dtype=np.int32)
+    best_hyp = np.empty(P, dtype=np.int32)
+    n_eval = np.empty(P, dtype=np.int32)
+    counts = np.empty(tot, dtype=np.int32)
+    band = np.empty(tot, dtype=np.int32)
+    mask = np.empty(c.shape[0], dtype=np.uint8) if want_mask else None
+    lib().oracle_ransac_adaptive(_ptr(c, _f), _ptr(off, _i64), _ptr(k, _i32), P, thr, seed, problem_base,
+                                 confidence, _ptr(best_H, _d), _ptr(best_count, _i32), _ptr(best_hyp, _i32),
+                                 _ptr(n_eval, _i32), _ptr(counts, _i32), _ptr(band, _i32), band_px, herr,
+                                 _ptr(mask, _u8))
+    return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, n_eval=n_eval, hyp_counts=counts,
+                band_counts=band, inlier_mask=mask)
 
 
 from .inlier_refit import hartley_normalization, refit, refit_dlt, refit_lm, refit_tolerance, reprojection_cost  # noqa: E402,F401

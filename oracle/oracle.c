@@ -836,3 +836,100 @@ void oracle_ransac(const float *corr, const int64_t *offsets, const int32_t *n_h
         hoff += k;
     }
 }
+
+/* ---------------------------------------------------------------------------
+ * Online adaptive termination (Sec. 6.2: the number of loops follows from the
+ * inlier ratio with 99% probability that one 4-point sample is all inliers,
+ * with a cap).  With the best count c so far among N correspondences,
+ * w = c / N and the required number of hypotheses is
+ *     K(c) = ceil(log(1 - confidence) / log(1 - w^4)),
+ * clamped to [1, cap]; c <= 0 gives cap.  log_fail = log(1 - confidence).
+ * ------------------------------------------------------------------------- */
+int32_t oracle_adaptive_k(int32_t c, int64_t N, int32_t cap, double log_fail)
+{
+    if (c <= 0 || N <= 0) return cap;
+    const double w = (double)c / (double)N;
+    const double w4 = (w * w) * (w * w);
+    if (w4 >= 1.0) return 1;
+    const double den = log1p(-w4);
+    if (!(den < 0.0)) return cap;
+    const double r = ceil(log_fail / den);
+    if (!(r < (double)cap)) return cap;
+    return r < 1.0 ? 1 : (int32_t)r;
+}
+
+/* The sequential loop: before hypothesis i, stop if i >= K(best of 0..i-1);
+ * the best improves only on a strictly larger count.  Returns the number of
+ * hypotheses evaluated (1..k; k if the cap is reached). */
+int32_t oracle_adaptive_stop(const int32_t *cnt, int32_t k, int64_t N, double log_fail)
+{
+    int32_t best = -1, kreq = k;
+    for (int32_t i = 0; i < k; ++i) {
+        if (i >= kreq) return i;
+        if (cnt[i] > best) {
+            best = cnt[i];
+            kreq = oracle_adaptive_k(best, N, k, log_fail);
+        }
+    }
+    return k;
+}
+
+/* RANSAC with the online stop: every problem scores its cap max_hyp[p]
+ * hypotheses (hyp_counts / band_counts as in oracle_ransac, all of them),
+ * n_eval[p] = the stop index, and the best is the argmax over the evaluated
+ * hypotheses only (ties to the lowest index). */
+void oracle_ransac_adaptive(const float *corr, const int64_t *offsets, const int32_t *max_hyp, int32_t P, double thr,
+                            uint64_t seed, uint32_t problem_base, double confidence, double *best_H,
+                            int32_t *best_count, int32_t *best_hyp, int32_t *n_eval, int32_t *hyp_counts,
+                            int32_t *band_counts, double band_px, double herr, uint8_t *inlier_mask)
+{
+    const double log_fail = log(1.0 - confidence);
+    int64_t hoff = 0;
+    for (int32_t p = 0; p < P; ++p) {
+        const int64_t N = offsets[p + 1] - offsets[p];
+        const float *c = corr + 4 * offsets[p];
+        const int32_t k = max_hyp[p];
+        int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * (k > 0 ? k : 1));
+        int32_t *bnd = band_counts ? band_counts + hoff : NULL;
+        oracle_score_problem(c, N, k, thr, seed, problem_base + (uint32_t)p, cnt, bnd, band_px, herr);
+        const int32_t ne = N >= 4 && k > 0 ? oracle_adaptive_stop(cnt, k, N, log_fail) : 0;
+        int32_t bh = -1, bc = -1;
+        for (int32_t h = 0; h < ne; ++h)
+            if (cnt[h] > bc) {
+                bc = cnt[h];
+                bh = h;
+            }
+        if (bc < 0) {
+            bh = -1;
+            bc = 0;
+        }
+        if (hyp_counts) memcpy(hyp_counts + hoff, cnt, sizeof(int32_t) * (k > 0 ? k : 0));
+        best_hyp[p] = bh;
+        best_count[p] = bc;
+        n_eval[p] = ne;
+        double H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (bh >= 0) {
+            int64_t idx[4];
+            oracle_sample4(seed, problem_base + (uint32_t)p, (uint32_t)bh, N, idx);
+            double s[16];
+            for (int q = 0; q < 4; ++q) {
+                s[2 * q] = c[4 * idx[q]];
+                s[2 * q + 1] = c[4 * idx[q] + 1];
+                s[8 + 2 * q] = c[4 * idx[q] + 2];
+                s[8 + 2 * q + 1] = c[4 * idx[q] + 3];
+            }
+            aca_one(s, H);
+            if (inlier_mask)
+                for (int64_t i = 0; i < N; ++i) {
+                    double m;
+                    inlier_mask[offsets[p] + i] = (uint8_t)score_point(H, c + 4 * i, thr, &m);
+                }
+            oracle_normalize_frob(H);
+        } else if (inlier_mask) {
+            memset(inlier_mask + offsets[p], 0, (size_t)N);
+        }
+        memcpy(best_H + 9 * p, H, sizeof H);
+        free(cnt);
+        hoff += k > 0 ? k : 0;
+    }
+}
