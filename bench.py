@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-log2", type=int, default=N_LOG2)
     ap.add_argument("--no-rows", action="store_true", help="headline only")
-    ap.add_argument("--rows", default="sks,affine,ransac1,ransac512,refit,diff,latency",
-                    help="comma list of extra rows: sks, affine, ransac1, ransac512, refit, diff, latency")
+    ap.add_argument("--rows", default="sks,affine,ransac1,ransac512,adaptive,refit,diff,latency",
+                    help="comma list of extra rows: sks, affine, ransac1, ransac512, adaptive, refit, diff, latency")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ransac-tuning", default="",
                     help="block_warps,hyps_per_thread,tile_points for the RANSAC rows (skips the autotuner)")
@@ -274,7 +274,7 @@ def main():
     rows_on = not args.no_rows and world == 1
     args.row_set = set(r for r in args.rows.split(",") if r) if rows_on else set()
     rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=SEED) if "ransac1" in args.row_set else None
-    rb = workloads.ransac_batch(512, seed=SEED) if args.row_set & {"ransac512", "refit"} else None
+    rb = workloads.ransac_batch(512, seed=SEED) if args.row_set & {"ransac512", "adaptive", "refit"} else None
     rect = workloads.rect_batch(65536, seed=SEED) if "diff" in args.row_set else None
 
     import torch
@@ -378,6 +378,8 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
         out.update(row_ransac1(torch, api, rp, stream, dev, fixed))
     if rb is not None and "ransac512" in args.row_set:
         out.update(row_ransac512(torch, api, rb, stream, dev, fixed, not args.no_plain))
+    if rb is not None and "adaptive" in args.row_set:
+        out.update(row_adaptive(torch, api, rb, stream, dev, fixed))
     if rb is not None and "refit" in args.row_set:
         out.update(row_refit(torch, _lib, api, rb, stream, dev, fixed))
     if rect is not None:
@@ -516,6 +518,43 @@ def row_ransac512(torch, api, rb, stream, dev, fixed=None, plain=True):
     res.update(ms_512_plain_launches=tp, speedup_vs_plain=tp / t3, batched_equals_plain=same)
     out["ransac_batched_512"] = res
     return out
+
+
+ADAPTIVE_CAP = 16384
+
+
+def row_adaptive(torch, api, rb, stream, dev, fixed=None):
+    """Batched RANSAC with the online adaptive stop (99% confidence) over the
+    512 pairs with the same cap for every pair (no knowledge of the inlier
+    ratio), against fixed counts: the cap for every pair, and counts computed
+    from the generated inlier ratios (the batched row's workload)."""
+    P = len(rb.n_hyp)
+    Ns = (rb.offsets[1:] - rb.offsets[:-1]).astype(np.float64)
+    corr = torch.from_numpy(rb.corr).to(dev)
+    off = torch.from_numpy(rb.offsets).to(dev)
+    caps_np = np.full(P, ADAPTIVE_CAP, np.int32)
+    caps = torch.from_numpy(caps_np).to(dev)
+    tot = int(caps_np.sum())
+    from paper_2402_18008_gb300 import autotune
+    k = torch.from_numpy(rb.n_hyp).to(dev)
+    make = lambda **kw: api.RansacPlan(corr, off, k, RANSAC_THR, SEED, int(rb.n_hyp.sum()), **kw)
+    best = fixed or autotune.tune(make, P, int(rb.offsets[-1]), int(rb.n_hyp.sum()), device=dev)[0]
+    res = {"unit": "ms per batch", "pairs": P, "cap": ADAPTIVE_CAP, "confidence": 0.99, "tuning": best,
+           "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9]; one graph replay each"}
+    plans = {"adaptive": api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, tot, confidence=0.99, **best),
+             "fixed_cap": api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, tot, **best),
+             "fixed_from_true_ratio": make(**best)}
+    for name, plan in plans.items():
+        plan.capture()
+        for _ in range(3):
+            plan.replay()
+        res[f"ms_{name}"] = time_region(torch, plan.replay, 10 if name == "fixed_cap" else 20, stream)
+    ne = plans["adaptive"].n_evaluated.cpu().numpy().astype(np.float64)
+    res.update(hypotheses_evaluated=int(ne.sum()), tests_evaluated=float(np.sum(ne * Ns)),
+               median_evaluated=float(np.median(ne)), max_evaluated=int(ne.max()),
+               hypotheses_fixed_from_true_ratio=int(rb.n_hyp.sum()),
+               value=res["ms_adaptive"], speedup_vs_fixed_cap=res["ms_fixed_cap"] / res["ms_adaptive"])
+    return {"ransac_adaptive_512": res}
 
 
 def row_refit(torch, _lib, api, rb, stream, dev, fixed=None):

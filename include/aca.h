@@ -237,6 +237,42 @@ aca_status aca_sample_indices(int64_t N, int32_t n_hyp, uint64_t seed, uint32_t 
                               void *stream);
 
 /*
+ * ransac_aca_adaptive - ransac_aca with the online adaptive stop of the
+ * paper's RANSAC loop (Sec. 6.2: the number of loops follows from the inlier
+ * ratio, at a confidence that one 4-point sample is all inliers, with a cap).
+ * For problem p the loop over hypotheses h = 0, 1, ... stops before h when
+ *     h >= K(best count among hypotheses 0..h-1),
+ *     K(c) = ceil(log(1 - confidence) / log(1 - (c / N)^4)), clamped to
+ *            [1, max_hyp[p]] (c <= 0: max_hyp[p]),
+ * or after max_hyp[p] hypotheses.  The result is that of this sequential loop
+ * exactly: hypotheses are sampled, solved and scored as in ransac_aca (same
+ * Philox streams, same counts), the best is the argmax over the evaluated
+ * hypotheses (ties to the lowest index).  On the GPU, work on hypotheses the
+ * loop is certain not to reach is skipped; which of them were scored does
+ * not change any output.
+ *   max_hyp    [P] int32 >= 0: the cap per problem (device memory).
+ *   total_max_hyps  sum of max_hyp (sizes the workspace).
+ *   confidence in (0, 1), e.g. 0.99.
+ *   n_evaluated[P] int32 or NULL: the number of hypotheses the loop evaluated
+ *              (0 when the problem has fewer than 4 points or max_hyp[p] = 0).
+ *   hyp_counts [total_max_hyps] int32 or NULL: counts of the evaluated
+ *              hypotheses (-1 degenerate), -2 for the ones after the stop.
+ *   workspace  at least ransac_aca_adaptive_workspace_size(P, total_max_hyps)
+ *              bytes, 256-byte aligned.
+ * Other arguments, outputs and errors as ransac_aca; confidence outside
+ * (0, 1) is ACA_ERR_INVALID_ARG.  Work order: the items of all problems are
+ * taken in rounds (round r = hypothesis block r of every problem that has
+ * one), so that a problem's earlier blocks finish while its later ones wait.
+ */
+size_t ransac_aca_adaptive_workspace_size(int32_t P, int64_t total_max_hyps);
+
+aca_status ransac_aca_adaptive(const float *corr, const int64_t *offsets, const int32_t *max_hyp, int32_t P,
+                               int64_t total_max_hyps, const aca_ransac_params *params, double confidence,
+                               float *best_H, int32_t *best_count, int32_t *best_hyp, int32_t *n_evaluated,
+                               int32_t *hyp_counts, uint8_t *inlier_mask, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
+/*
  * aca_refit - re-estimate one homography per problem from ALL of its masked
  * correspondences: the global optimisation with all inliers that follows
  * the RANSAC loop (Sec. 6.2, stage 5, where it is a Levenberg-Marquardt

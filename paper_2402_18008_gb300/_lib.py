@@ -23,8 +23,8 @@ ACA_FLAG_SRC_ANCHORS, ACA_FLAG_TGT_ANCHORS, ACA_FLAG_OTHER_TRIPLE, ACA_FLAG_NON_
 _STATUS = {0: "ACA_OK", -1: "ACA_ERR_INVALID_ARG", -2: "ACA_ERR_CUDA", -3: "ACA_ERR_WORKSPACE", -4: "ACA_ERR_TIMEOUT"}
 
 EXPORTED = ("aca_solve", "sks_solve", "aca_rect_solve", "aca_affine_solve", "aca_backward", "aca_rect_backward",
-            "ransac_aca_workspace_size", "ransac_aca", "ransac_aca_noalloc", "aca_sample_indices", "aca_refit",
-            "aca_last_error", "aca_version")
+            "ransac_aca_workspace_size", "ransac_aca", "ransac_aca_noalloc", "ransac_aca_adaptive_workspace_size",
+            "ransac_aca_adaptive", "aca_sample_indices", "aca_refit", "aca_last_error", "aca_version")
 ACA_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 
 
@@ -70,8 +70,13 @@ def load(build_if_missing: bool = True):
         L.aca_sample_indices.argtypes = [i64, i32, ctypes.c_uint64, ctypes.c_uint32, vp, vp]
         L.ransac_aca_noalloc.argtypes = [vp, vp, vp, i32, i64, ctypes.POINTER(RansacParams), vp, vp, vp, vp, vp, vp]
         L.aca_refit.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp]
+        L.ransac_aca_adaptive_workspace_size.argtypes = [i32, i64]
+        L.ransac_aca_adaptive_workspace_size.restype = ctypes.c_size_t
+        L.ransac_aca_adaptive.argtypes = [vp, vp, vp, i32, i64, ctypes.POINTER(RansacParams), ctypes.c_double, vp,
+                                          vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         for name in EXPORTED:
-            if name not in ("ransac_aca_workspace_size", "aca_last_error", "aca_version"):
+            if name not in ("ransac_aca_workspace_size", "ransac_aca_adaptive_workspace_size", "aca_last_error",
+                            "aca_version"):
                 getattr(L, name).restype = ctypes.c_int
         L.aca_last_error.restype = ctypes.c_char_p
         L.aca_version.restype = ctypes.c_char_p
@@ -271,3 +276,48 @@ def aca_refit(corr, offsets, H, mask=None, lm_iters=10, n_used=None, rms=None, s
                 raise ValueError(f"{nm} must be a contiguous (P,) tensor")
     _check(load().aca_refit(_ptr(corr), _ptr(offsets), _ptr(mask), P, int(lm_iters), _ptr(H), _ptr(n_used),
                             _ptr(rms), ctypes.c_void_p(_stream(stream))))
+
+
+def ransac_aca_adaptive_workspace_size(P: int, total_max_hyps: int) -> int:
+    return int(load().ransac_aca_adaptive_workspace_size(int(P), int(total_max_hyps)))
+
+
+def ransac_aca_adaptive(corr, offsets, max_hyp, total_max_hyps, params: RansacParams, confidence, best_H,
+                        best_count, best_hyp, workspace, n_evaluated=None, hyp_counts=None, inlier_mask=None,
+                        stream=None):
+    """C ABI ransac_aca_adaptive: ransac_aca with the online stop at
+    `confidence`; max_hyp (P,) int32 caps; n_evaluated (P,) int32."""
+    _need(corr, "corr", torch.float32)
+    _need(offsets, "offsets", torch.int64)
+    _need(max_hyp, "max_hyp", torch.int32)
+    _need(best_H, "best_H", torch.float32)
+    _need(best_count, "best_count", torch.int32)
+    _need(best_hyp, "best_hyp", torch.int32)
+    _need(workspace, "workspace", torch.uint8)
+    if corr.dim() != 2 or corr.shape[1] != 4 or not corr.is_contiguous():
+        raise ValueError("corr must be a contiguous (total, 4) tensor")
+    P = max_hyp.numel()
+    if offsets.numel() != P + 1:
+        raise ValueError("offsets must have P+1 entries")
+    for t, nm in ((offsets, "offsets"), (max_hyp, "max_hyp"), (best_H, "best_H"), (best_count, "best_count"),
+                  (best_hyp, "best_hyp")):
+        if not t.is_contiguous():
+            raise ValueError(f"{nm} must be contiguous")
+    if best_H.numel() < 9 * P or best_count.numel() < P or best_hyp.numel() < P:
+        raise ValueError("output tensors too small")
+    if n_evaluated is not None:
+        _need(n_evaluated, "n_evaluated", torch.int32)
+        if n_evaluated.numel() < P:
+            raise ValueError("n_evaluated too small")
+    if hyp_counts is not None:
+        _need(hyp_counts, "hyp_counts", torch.int32)
+        if hyp_counts.numel() < total_max_hyps:
+            raise ValueError("hyp_counts too small")
+    if inlier_mask is not None:
+        _need(inlier_mask, "inlier_mask", torch.uint8)
+        if inlier_mask.numel() < corr.shape[0]:
+            raise ValueError("inlier_mask too small")
+    _check(load().ransac_aca_adaptive(_ptr(corr), _ptr(offsets), _ptr(max_hyp), P, int(total_max_hyps),
+                                      ctypes.byref(params), float(confidence), _ptr(best_H), _ptr(best_count),
+                                      _ptr(best_hyp), _ptr(n_evaluated), _ptr(hyp_counts), _ptr(inlier_mask),
+                                      _ptr(workspace), workspace.numel(), ctypes.c_void_p(_stream(stream))))

@@ -63,6 +63,7 @@ class RansacResult:
     best_hyp: torch.Tensor    # (P,) int32
     hyp_counts: torch.Tensor | None
     inlier_mask: torch.Tensor | None
+    n_evaluated: torch.Tensor | None = None  # (P,) hypotheses before the online stop (adaptive plans)
     refit_H: torch.Tensor | None = None     # (P, 9) after the refit on all inliers
     refit_rms: torch.Tensor | None = None   # (P,) RMS reprojection error (px) of refit_H
 
@@ -70,6 +71,10 @@ class RansacResult:
 class RansacPlan:
     """Buffers and launch parameters for repeated ransac_aca calls on one
     batch layout (P problems, total_hyps hypotheses, total points).
+
+    With ``confidence`` set, ``n_hyp`` is the cap per problem and the loop
+    stops online (ransac_aca_adaptive): hypothesis h is evaluated only while
+    h < K(best count so far) at that confidence.
 
     ``run()`` enqueues one full RANSAC (prep, scoring, argmax) on the current
     stream, followed, when ``refit_iters`` is not None, by the refit of each
@@ -81,9 +86,12 @@ class RansacPlan:
     def __init__(self, corr: torch.Tensor, offsets: torch.Tensor, n_hyp: torch.Tensor, threshold_px: float,
                  seed: int, total_hyps: int, problem_base: int = 0, block_warps: int = 0,
                  hyps_per_thread: int = 0, tile_points: int = 0, grid_blocks: int = 0,
-                 want_counts: bool = False, want_mask: bool = False, refit_iters: int | None = None):
+                 want_counts: bool = False, want_mask: bool = False, refit_iters: int | None = None,
+                 confidence: float | None = None):
         _require_cuda(corr, "corr")
         want_mask = want_mask or refit_iters is not None
+        self.confidence = confidence
+        self.total_hyps = int(total_hyps)
         dev = corr.device
         self.corr, self.offsets, self.n_hyp = corr, offsets, n_hyp
         self.P = n_hyp.numel()
@@ -91,21 +99,29 @@ class RansacPlan:
                                    seed=int(seed), block_warps=int(block_warps),
                                    hyps_per_thread=int(hyps_per_thread), grid_blocks=int(grid_blocks),
                                    tile_points=int(tile_points))
-        ws = _lib.ransac_aca_workspace_size(self.P, int(total_hyps))
+        ws = (_lib.ransac_aca_adaptive_workspace_size(self.P, int(total_hyps)) if confidence is not None
+              else _lib.ransac_aca_workspace_size(self.P, int(total_hyps)))
         self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
         self.best_H = torch.empty((self.P, 9), dtype=torch.float32, device=dev)
         self.best_count = torch.empty(self.P, dtype=torch.int32, device=dev)
         self.best_hyp = torch.empty(self.P, dtype=torch.int32, device=dev)
         self.hyp_counts = torch.empty(max(int(total_hyps), 1), dtype=torch.int32, device=dev) if want_counts else None
         self.inlier_mask = torch.empty(max(corr.shape[0], 1), dtype=torch.uint8, device=dev) if want_mask else None
+        self.n_evaluated = torch.empty(self.P, dtype=torch.int32, device=dev) if confidence is not None else None
         self.refit_iters = refit_iters
         self.refit_H = torch.empty((self.P, 9), dtype=torch.float32, device=dev) if refit_iters is not None else None
         self.refit_rms = torch.empty(self.P, dtype=torch.float32, device=dev) if refit_iters is not None else None
         self.graph = None
 
     def run(self) -> RansacResult:
-        _lib.ransac_aca(self.corr, self.offsets, self.n_hyp, self.params, self.best_H, self.best_count,
-                        self.best_hyp, self.workspace, hyp_counts=self.hyp_counts, inlier_mask=self.inlier_mask)
+        if self.confidence is not None:
+            _lib.ransac_aca_adaptive(self.corr, self.offsets, self.n_hyp, self.total_hyps, self.params,
+                                     self.confidence, self.best_H, self.best_count, self.best_hyp, self.workspace,
+                                     n_evaluated=self.n_evaluated, hyp_counts=self.hyp_counts,
+                                     inlier_mask=self.inlier_mask)
+        else:
+            _lib.ransac_aca(self.corr, self.offsets, self.n_hyp, self.params, self.best_H, self.best_count,
+                            self.best_hyp, self.workspace, hyp_counts=self.hyp_counts, inlier_mask=self.inlier_mask)
         if self.refit_iters is not None:
             _lib.aca_refit(self.corr, self.offsets, self.refit_H, mask=self.inlier_mask, lm_iters=self.refit_iters,
                            rms=self.refit_rms)
@@ -130,18 +146,19 @@ class RansacPlan:
 
     def result(self) -> RansacResult:
         return RansacResult(self.best_H, self.best_count, self.best_hyp, self.hyp_counts, self.inlier_mask,
-                            self.refit_H, self.refit_rms)
+                            self.n_evaluated, self.refit_H, self.refit_rms)
 
 
 def ransac(corr: torch.Tensor, offsets: torch.Tensor, n_hyp: torch.Tensor, threshold_px: float, seed: int,
            total_hyps: int | None = None, want_counts: bool = False, want_mask: bool = False,
-           refit_iters: int | None = None, **tuning) -> RansacResult:
-    """One-shot RANSAC over CSR problems (see include/aca.h, ransac_aca),
-    optionally followed by the refit on all inliers (refit_iters LM steps)."""
+           refit_iters: int | None = None, confidence: float | None = None, **tuning) -> RansacResult:
+    """One-shot RANSAC over CSR problems (see include/aca.h, ransac_aca; with
+    `confidence`, ransac_aca_adaptive and n_hyp as the caps), optionally
+    followed by the refit on all inliers (refit_iters LM steps)."""
     if total_hyps is None:
         total_hyps = int(n_hyp.sum().item())
     plan = RansacPlan(corr, offsets, n_hyp, threshold_px, seed, total_hyps, want_counts=want_counts,
-                      want_mask=want_mask, refit_iters=refit_iters, **tuning)
+                      want_mask=want_mask, refit_iters=refit_iters, confidence=confidence, **tuning)
     return plan.run()
 
 

@@ -24,6 +24,24 @@
 //                           index), re-solve of the winner with the same
 //                           device code (bit-identical H), inlier mask, outputs.
 // There are no inter-block waits: progress only needs the atomics.
+//
+// With the online adaptive stop (ransac_aca_adaptive, Sec. 6.2: the loop
+// count follows from the best inlier ratio so far), the same scoring loop
+// runs with three changes:
+//  - items are ordered in rounds, round r holding chunk r (hypotheses
+//    r*HB .. r*HB+HB-1) of every problem that has one, so that a problem's
+//    earlier chunks are finished while its later ones wait in the queue;
+//  - the block that finishes the last slice of a chunk takes the chunk's best
+//    count c at index j and lowers the problem's bound to max(j + 1, K(c)),
+//    K being the required number of hypotheses; a chunk starting at or after
+//    the bound is skipped: the sequential loop is certain to stop before it
+//    (the best over hypotheses 0..h0-1 is at least c, so K at h0 is at most
+//    K(c) <= h0);
+//  - the finish kernel finds the sequential stop index from the prefix
+//    maxima of the counts (the stop condition i >= K(best of 0..i-1) is
+//    monotone in i) and takes the argmax before it.
+// Every output is deterministic: counts before the stop are complete sums,
+// everything after it is reported as not evaluated.
 #include "aca_math.cuh"
 #include "common.cuh"
 #include "philox.cuh"
@@ -180,6 +198,95 @@ static size_t header_bytes(int32_t P)
     return 2 * align256(sizeof(int64_t) * (size_t)(P + 1)) + 256;
 }
 
+// Extra workspace of the adaptive variant (after the standard header).
+struct AdaptiveWs {
+    int64_t *chunk_off;    // [P+1] prefix of C_p, the chunks of HB hypotheses of problem p
+    int32_t *order;        // [P] problems by C_p, largest first
+    int64_t *spref;        // [P+1] prefix of the slice counts S_p over `order`
+    int64_t *round_off;    // [rb+1] first item of round r
+    int32_t *round_cnt;    // [rb+1] problems in round r (those with C_p > r)
+    int32_t *cursor;       // [rb+1] counting-sort cursors
+    int32_t *rounds;       // [1] number of rounds (max C_p)
+    int32_t *kbound;       // [P] the stop is certain before this hypothesis index
+    int32_t *chunk_done;   // [cb] completed slices per chunk
+    int32_t *prefix;       // [capacity] inclusive prefix maxima of the counts (finish)
+    int64_t rb, cb;        // capacities (bounds for HB = 32)
+    double log_fail;       // log(1 - confidence)
+};
+
+// Layout: standard header, adaptive arrays, counts (total_hyps), prefix.
+static size_t adaptive_bytes(int32_t P, int64_t total, int64_t *rb, int64_t *cb, size_t *counts_at)
+{
+    const int64_t r = total / 32 + 2, c = total / 32 + (int64_t)P + 1;
+    size_t o = header_bytes(P);
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));    // chunk_off
+    o += align256(sizeof(int32_t) * (size_t)P);          // order
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));    // spref
+    o += align256(sizeof(int64_t) * (size_t)(r + 1));    // round_off
+    o += 2 * align256(sizeof(int32_t) * (size_t)(r + 1));// round_cnt, cursor
+    o += 256;                                            // rounds
+    o += align256(sizeof(int32_t) * (size_t)P);          // kbound
+    o += align256(sizeof(int32_t) * (size_t)c);          // chunk_done
+    if (counts_at) *counts_at = o;
+    o += 2 * align256(sizeof(int32_t) * (size_t)total);  // counts, prefix
+    if (rb) *rb = r;
+    if (cb) *cb = c;
+    return o;
+}
+
+static void carve_adaptive(void *base, int32_t P, int64_t total, Workspace &w, AdaptiveWs &a)
+{
+    char *b = static_cast<char *>(base);
+    size_t counts_at = 0;
+    adaptive_bytes(P, total, &a.rb, &a.cb, &counts_at);
+    size_t o = 0;
+    w.hyp_off = reinterpret_cast<int64_t *>(b + o);
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));
+    w.item_off = reinterpret_cast<int64_t *>(b + o);
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));
+    w.counter = reinterpret_cast<unsigned long long *>(b + o);
+    w.flags = reinterpret_cast<int32_t *>(b + o + 8);
+    o += 256;
+    a.chunk_off = reinterpret_cast<int64_t *>(b + o);
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));
+    a.order = reinterpret_cast<int32_t *>(b + o);
+    o += align256(sizeof(int32_t) * (size_t)P);
+    a.spref = reinterpret_cast<int64_t *>(b + o);
+    o += align256(sizeof(int64_t) * (size_t)(P + 1));
+    a.round_off = reinterpret_cast<int64_t *>(b + o);
+    o += align256(sizeof(int64_t) * (size_t)(a.rb + 1));
+    a.round_cnt = reinterpret_cast<int32_t *>(b + o);
+    o += align256(sizeof(int32_t) * (size_t)(a.rb + 1));
+    a.cursor = reinterpret_cast<int32_t *>(b + o);
+    o += align256(sizeof(int32_t) * (size_t)(a.rb + 1));
+    a.rounds = reinterpret_cast<int32_t *>(b + o);
+    o += 256;
+    a.kbound = reinterpret_cast<int32_t *>(b + o);
+    o += align256(sizeof(int32_t) * (size_t)P);
+    a.chunk_done = reinterpret_cast<int32_t *>(b + o);
+    o += align256(sizeof(int32_t) * (size_t)a.cb);
+    w.counts = reinterpret_cast<int32_t *>(b + counts_at);
+    w.capacity = total;
+    a.prefix = reinterpret_cast<int32_t *>(b + counts_at + align256(sizeof(int32_t) * (size_t)total));
+}
+
+// Required number of hypotheses for the best count c of N at confidence p
+// (log_fail = log(1 - p)): K = ceil(log(1 - p) / log(1 - w^4)), w = c / N,
+// clamped to [1, cap]; c <= 0 gives cap (Sec. 6.2).
+__device__ int32_t adaptive_k(int32_t c, int64_t N, int32_t cap, double log_fail)
+{
+    if (c <= 0 || N <= 0) return cap;
+    const double w = __ddiv_rn((double)c, (double)N);
+    const double w2 = __dmul_rn(w, w);
+    const double w4 = __dmul_rn(w2, w2);
+    if (w4 >= 1.0) return 1;
+    const double den = log1p(-w4);
+    if (!(den < 0.0)) return cap;
+    const double r = ceil(__ddiv_rn(log_fail, den));
+    if (!(r < (double)cap)) return cap;
+    return r < 1.0 ? 1 : (int32_t)r;
+}
+
 // Inclusive block scan of int64 (blockDim.x == 1024).
 __device__ int64_t block_scan_incl(int64_t v, int64_t *warp_tot)
 {
@@ -253,6 +360,139 @@ __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__rest
     }
 }
 
+// Set-up of the adaptive variant (one block of 1024 threads): the standard
+// offsets, the chunk offsets, the bounds (initially the cap), and the round
+// order: problems sorted by C_p, largest first (counting sort; the order
+// among equal C_p follows the atomics and only affects speed), so that round
+// r, which holds the problems with C_p > r, is a prefix of that order.
+__global__ void __launch_bounds__(1024) ransac_prep_adaptive_kernel(const int64_t *__restrict__ offsets,
+                                                                    const int32_t *__restrict__ max_hyp, int32_t P,
+                                                                    int HB, int T, Workspace ws, AdaptiveWs aw)
+{
+    __shared__ int64_t wt_a[32], wt_b[32], wt_c[32];
+    __shared__ int64_t carry_a, carry_b, carry_c;
+    __shared__ int32_t s_rounds;
+    if (threadIdx.x == 0) {
+        carry_a = carry_b = carry_c = 0;
+        s_rounds = 0;
+        ws.hyp_off[0] = 0;
+        ws.item_off[0] = 0;
+        aw.chunk_off[0] = 0;
+        *ws.counter = 0ull;
+        *ws.flags = 0;
+    }
+    __syncthreads();
+    for (int32_t base = 0; base < P; base += 1024) {
+        const int32_t p = base + (int32_t)threadIdx.x;
+        int64_t k = 0, items = 0, C = 0;
+        if (p < P) {
+            k = max_hyp[p] > 0 ? max_hyp[p] : 0;
+            const int64_t N = offsets[p + 1] - offsets[p];
+            if (N >= 4 && k > 0) {
+                C = (k + HB - 1) / HB;
+                items = C * ((N + T - 1) / T);
+            }
+            aw.kbound[p] = (int32_t)k;
+            if (C > 0) atomicMax(&s_rounds, (int32_t)(C < 0x7fffffff ? C : 0x7fffffff));
+        }
+        const int64_t ia = block_scan_incl(k, wt_a);
+        const int64_t ib = block_scan_incl(items, wt_b);
+        const int64_t ic = block_scan_incl(C, wt_c);
+        if (p < P) {
+            ws.hyp_off[p + 1] = carry_a + ia;
+            ws.item_off[p + 1] = carry_b + ib;
+            aw.chunk_off[p + 1] = carry_c + ic;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            carry_a += ia;
+            carry_b += ib;
+            carry_c += ic;
+        }
+        __syncthreads();
+    }
+    const int32_t R = s_rounds;
+    if (carry_a > ws.capacity || (int64_t)R > aw.rb || carry_c > aw.cb) {
+        if (threadIdx.x == 0) {
+            *ws.flags = 1;
+            ws.item_off[P] = 0;   // nothing to score
+            *aw.rounds = 0;
+        }
+        return;
+    }
+    if (threadIdx.x == 0) *aw.rounds = R;
+    // histogram of C_p over 0..R
+    for (int32_t c = threadIdx.x; c <= R; c += 1024) aw.round_cnt[c] = 0;
+    __syncthreads();
+    for (int32_t p = threadIdx.x; p < P; p += 1024)
+        atomicAdd(&aw.round_cnt[aw.chunk_off[p + 1] - aw.chunk_off[p]], 1);
+    __syncthreads();
+    // descending exclusive prefix: #{p : C_p > c}; it is both the size of
+    // round c and the first position of bin c in the order
+    if (threadIdx.x == 0) carry_a = 0;
+    __syncthreads();
+    for (int32_t base = 0; base <= R; base += 1024) {
+        const int32_t c = R - (base + (int32_t)threadIdx.x);
+        const int64_t v = c >= 0 ? aw.round_cnt[c] : 0;
+        const int64_t incl = block_scan_incl(v, wt_a);
+        __syncthreads();                        // every thread has read its bin
+        if (c >= 0) {
+            const int32_t above = (int32_t)(carry_a + incl - v);
+            aw.round_cnt[c] = above;
+            aw.cursor[c] = above;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry_a += incl;
+        __syncthreads();
+    }
+    for (int32_t p = threadIdx.x; p < P; p += 1024) {
+        const int32_t C = (int32_t)(aw.chunk_off[p + 1] - aw.chunk_off[p]);
+        if (C > 0) aw.order[atomicAdd(&aw.cursor[C], 1)] = p;
+    }
+    __syncthreads();
+    // slice prefix over the order, then the round offsets
+    const int32_t n1 = R > 0 ? aw.round_cnt[0] : 0;
+    if (threadIdx.x == 0) {
+        carry_b = 0;
+        carry_c = 0;
+        aw.spref[0] = 0;
+        aw.round_off[0] = 0;
+    }
+    __syncthreads();
+    for (int32_t base = 0; base < n1; base += 1024) {
+        const int32_t j = base + (int32_t)threadIdx.x;
+        int64_t v = 0;
+        if (j < n1) {
+            const int32_t p = aw.order[j];
+            v = (offsets[p + 1] - offsets[p] + T - 1) / T;
+        }
+        const int64_t incl = block_scan_incl(v, wt_b);
+        if (j < n1) aw.spref[j + 1] = carry_b + incl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry_b += incl;
+        __syncthreads();
+    }
+    for (int32_t base = 0; base < R; base += 1024) {
+        const int32_t r = base + (int32_t)threadIdx.x;
+        const int64_t v = r < R ? aw.spref[aw.round_cnt[r]] : 0;
+        const int64_t incl = block_scan_incl(v, wt_c);
+        if (r < R) aw.round_off[r + 1] = carry_c + incl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry_c += incl;
+        __syncthreads();
+    }
+}
+
+// Clears the counts and the chunk completion counters of the adaptive variant.
+__global__ void zero_adaptive_kernel(Workspace ws, AdaptiveWs aw, int32_t P)
+{
+    if (*ws.flags) return;
+    const int64_t nc = ws.hyp_off[P], nk = aw.chunk_off[P];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) ws.counts[i] = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += stride) aw.chunk_done[i] = 0;
+}
+
 __global__ void zero_counts_kernel(Workspace ws, int32_t P)
 {
     const int64_t total = ws.hyp_off[P];
@@ -270,6 +510,11 @@ struct ItemInfo {
     int32_t h0, nh; // hypotheses of this item
     int32_t i0, ni; // points of this item
     int32_t slice;
+    // adaptive variant only
+    int32_t skip;   // the stop is certain before h0: nothing to score
+    int32_t S;      // slices of problem p
+    int32_t k;      // hypothesis cap of problem p
+    int64_t cid;    // chunk id (completion counter)
 };
 
 // Largest p with item_off[p] <= item (item_off non-decreasing, p < P):
@@ -290,11 +535,12 @@ __device__ int32_t find_problem(const int64_t *__restrict__ item_off, int32_t P,
     return lo;
 }
 
-template <int HPT>
+template <int HPT, bool ADAPTIVE>
 __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restrict__ corr,
                                                            const int64_t *__restrict__ offsets,
                                                            const int32_t *__restrict__ n_hyp, int32_t P, float thr,
-                                                           uint64_t seed, uint32_t prob_base, int T, Workspace ws)
+                                                           uint64_t seed, uint32_t prob_base, int T, Workspace ws,
+                                                           AdaptiveWs aw)
 {
     constexpr int HB = 32 * HPT;
     extern __shared__ float4 smem4[];
@@ -304,11 +550,13 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
     float *Hs = reinterpret_cast<float *>(smem4 + T);                       // [HB][12]
     int32_t *red = reinterpret_cast<int32_t *>(Hs + HB * 12);               // [W][HB]
     __shared__ ItemInfo info;
+    __shared__ int32_t s_last;
     const float nthr2s = -F_MUL(thr, thr);
     const float2 nthr2 = make_float2(nthr2s, nthr2s);
     const float nanv = __int_as_float(0x7fc00000);
 
     const int64_t total = ws.item_off[P];
+    const int32_t R = ADAPTIVE ? *aw.rounds : 0;
     for (;;) {
         if (wid == 0) {
             int64_t item = 0;
@@ -316,14 +564,28 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
                 item = (int64_t)atomicAdd(ws.counter, 1ull);
             item = __shfl_sync(0xffffffffu, item, 0);
             if (item < total) {
-                const int32_t p = find_problem(ws.item_off, P, item);
+                int32_t p = 0, chunk = 0, slice = 0;
+                if constexpr (ADAPTIVE) {
+                    // round r = chunk r of every problem with more than r chunks
+                    const int32_t r = find_problem(aw.round_off, R, item);
+                    const int64_t rem = item - aw.round_off[r];
+                    const int32_t j = find_problem(aw.spref, aw.round_cnt[r], rem);
+                    p = aw.order[j];
+                    chunk = r;
+                    slice = (int32_t)(rem - aw.spref[j]);
+                } else {
+                    p = find_problem(ws.item_off, P, item);
+                }
                 if (lane == 0) {
                     const int64_t base = offsets[p];
                     const uint32_t N = (uint32_t)(offsets[p + 1] - base);
                     const int32_t k = n_hyp[p];
-                    const int64_t r = item - ws.item_off[p];
                     const int32_t S = (int32_t)((N + T - 1) / T);
-                    const int32_t chunk = (int32_t)(r / S), slice = (int32_t)(r % S);
+                    if constexpr (!ADAPTIVE) {
+                        const int64_t r = item - ws.item_off[p];
+                        chunk = (int32_t)(r / S);
+                        slice = (int32_t)(r % S);
+                    }
                     info.item = item;
                     info.p = p;
                     info.N = N;
@@ -334,6 +596,13 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
                     info.i0 = slice * T;
                     info.ni = (int32_t)min((int64_t)T, (int64_t)N - (int64_t)slice * T);
                     info.slice = slice;
+                    info.skip = 0;
+                    if constexpr (ADAPTIVE) {
+                        info.S = S;
+                        info.k = k;
+                        info.cid = aw.chunk_off[p] + chunk;
+                        info.skip = chunk > 0 && chunk * HB >= __ldcg(&aw.kbound[p]);
+                    }
                 }
             } else if (lane == 0) {
                 info.item = item;
@@ -348,6 +617,12 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
         const uint32_t N = info.N;
         const int64_t hbase = info.hbase;
         const float4 *cp = corr + info.base;
+        if constexpr (ADAPTIVE) {
+            if (info.skip) {
+                __syncthreads();        // all have read `info`
+                continue;
+            }
+        }
 
         // hypotheses of this item -> shared memory (test form, see inlier)
         if ((int)threadIdx.x < HB) {
@@ -411,6 +686,32 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
             for (int w = 0; w < W; ++w) s += red[w * HB + threadIdx.x];
             if (s)
                 atomicAdd(&ws.counts[hbase + h0 + threadIdx.x], s);
+        }
+        if constexpr (ADAPTIVE) {
+            // the last slice of a chunk publishes the chunk's bound
+            const int64_t cid = info.cid;
+            const int32_t S = info.S, kcap = info.k;
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&aw.chunk_done[cid], 1) == S - 1;
+            __syncthreads();
+            if (s_last && wid == 0) {
+                __threadfence();
+                int32_t bc = -2, bj = 0x7fffffff;
+                for (int t = lane; t < nh; t += 32) {
+                    const int32_t c = __ldcg(&ws.counts[hbase + h0 + t]);
+                    if (c > bc) { bc = c; bj = t; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int32_t c2 = __shfl_xor_sync(0xffffffffu, bc, o), j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+                    if (c2 > bc || (c2 == bc && j2 < bj)) { bc = c2; bj = j2; }
+                }
+                if (lane == 0 && bc > 0) {
+                    const int32_t K = adaptive_k(bc, (int64_t)N, kcap, aw.log_fail);
+                    atomicMin(&aw.kbound[p], max(h0 + bj + 1, K));
+                }
+            }
         }
     }
 }
@@ -477,6 +778,142 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
         to_test_form(G, H);
         const float nthr2 = -F_MUL(thr, thr);
         const bool any = s_best >= 0;
+        for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+            mask[base + i] = any ? (uint8_t)inlier(G, corr[base + i], nthr2) : (uint8_t)0;
+    }
+}
+
+// Adaptive finish, one block of 512 threads per problem: inclusive prefix
+// maxima I of the counts, tile by tile (2048 hypotheses), until the stop is
+// certain within the scanned part; the stop index is the first i in 1..k with
+// i >= K(I[i-1]) (monotone in i: I does not decrease and K does not increase
+// with the count), found by a 32-way search; the best is I at the stop and
+// its first index.  Hypotheses at or after the stop are reported as -2.
+__global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
+    const float4 *__restrict__ corr, const int64_t *__restrict__ offsets, const int32_t *__restrict__ max_hyp,
+    float thr, uint64_t seed, uint32_t prob_base, Workspace ws, AdaptiveWs aw, float *__restrict__ best_H,
+    int32_t *__restrict__ best_count, int32_t *__restrict__ best_hyp, int32_t *__restrict__ n_eval,
+    int32_t *__restrict__ hyp_counts, uint8_t *__restrict__ mask)
+{
+    constexpr int kTile = 2048, kPer = 4;
+    const int32_t p = blockIdx.x;
+    const int64_t base = offsets[p];
+    const int64_t N = offsets[p + 1] - base;
+    const int32_t k = max_hyp[p] > 0 ? max_hyp[p] : 0;
+    const bool overflow = *ws.flags != 0;
+    const int64_t hb = overflow ? 0 : ws.hyp_off[p];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ int32_t s_wmax[16], s_carry, s_stop, s_end, s_istar, s_bi;
+    __shared__ float sH[9];
+    const int32_t *cnt = ws.counts + hb;
+    int32_t *pre = aw.prefix + hb;
+
+    if (threadIdx.x == 0) {
+        s_carry = -2;
+        s_end = 0;
+        s_istar = 0;
+        s_bi = 0x7fffffff;
+    }
+    __syncthreads();
+    const bool active = !overflow && N >= 4 && k > 0;
+    if (active) {
+        for (int32_t t0 = 0; t0 < k; t0 += kTile) {
+            const int32_t b = t0 + kPer * (int32_t)threadIdx.x;
+            int32_t m[kPer], run = -2;
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int32_t c = b + q < k ? cnt[b + q] : -2;
+                run = max(run, c);
+                m[q] = run;
+            }
+            // exclusive max-scan of the thread maxima
+            int32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl = max(incl, t);
+            }
+            if (lane == 31) s_wmax[wid] = incl;
+            __syncthreads();
+            int32_t before = s_carry;
+            for (int w = 0; w < wid; ++w) before = max(before, s_wmax[w]);
+            const int32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane > 0) before = max(before, excl);
+#pragma unroll
+            for (int q = 0; q < kPer; ++q)
+                if (b + q < k) pre[b + q] = max(before, m[q]);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int32_t tile_max = s_carry;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tile_max = max(tile_max, s_wmax[w]);
+                s_carry = tile_max;
+                const int32_t e = min(t0 + kTile, k);
+                s_end = e;
+                s_stop = e == k || e >= adaptive_k(pre[e - 1], N, k, aw.log_fail);
+            }
+            __syncthreads();
+            if (s_stop) break;
+        }
+        // first i in [1, end] with the stop condition (it holds at end)
+        if (wid == 0) {
+            int32_t lo = 1, hi = s_end;
+            while (lo < hi) {
+                const int32_t st = (hi - lo + 30) / 31;    // lane 31 reaches hi: some lane holds
+                const int32_t q = lo + lane * st;
+                bool ok = true;
+                if (q < hi) ok = q == k || q >= adaptive_k(pre[q - 1], N, k, aw.log_fail);
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                const int f = __ffs(bal) - 1;
+                const int32_t nhi = min(hi, lo + f * st);
+                lo = f > 0 ? lo + (f - 1) * st + 1 : lo;
+                hi = nhi;
+            }
+            if (lane == 0) s_istar = lo;
+        }
+        __syncthreads();
+        // first index of the best count before the stop
+        const int32_t istar = s_istar, best = pre[istar - 1];
+        int32_t bi = 0x7fffffff;
+        for (int32_t h = threadIdx.x; h < istar; h += blockDim.x)
+            if (cnt[h] == best) { bi = h; break; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bi = min(bi, __shfl_xor_sync(0xffffffffu, bi, o));
+        if (lane == 0) atomicMin(&s_bi, bi);
+    }
+    __syncthreads();
+    const int32_t istar = s_istar;
+    if (hyp_counts && !overflow)
+        for (int32_t h = threadIdx.x; h < k; h += blockDim.x)
+            hyp_counts[hb + h] = !active ? -1 : (h < istar ? cnt[h] : -2);
+    if (threadIdx.x == 0) {
+        int32_t bi = -1, bc = 0;
+        if (overflow) {
+            bi = -2;
+        } else if (active && s_bi != 0x7fffffff && pre[istar - 1] >= 0) {
+            bi = s_bi;
+            bc = pre[istar - 1];
+        }
+        s_bi = bi;
+        float H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (bi >= 0)
+            make_hypothesis(corr + base, (uint32_t)N, seed, prob_base + (uint32_t)p, (uint32_t)bi, H);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sH[i] = H[i];
+        best_hyp[p] = bi;
+        best_count[p] = bc;
+        if (n_eval) n_eval[p] = overflow ? 0 : istar;
+        normalize_frob(H);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) best_H[9 * p + i] = H[i];
+    }
+    __syncthreads();
+    if (mask) {
+        float H[9], G[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) H[i] = sH[i];
+        to_test_form(G, H);
+        const float nthr2 = -F_MUL(thr, thr);
+        const bool any = s_bi >= 0;
         for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
             mask[base + i] = any ? (uint8_t)inlier(G, corr[base + i], nthr2) : (uint8_t)0;
     }
@@ -570,13 +1007,13 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
     const float4 *c4 = reinterpret_cast<const float4 *>(corr);
 #define ACA_SCORE(HPTV)                                                                                       \
     {                                                                                                          \
-        auto k = ransac_score_kernel<HPTV>;                                                                    \
+        auto k = ransac_score_kernel<HPTV, false>;                                                             \
         if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                                      (int)smem) != cudaSuccess)                                \
             return set_error(ACA_ERR_CUDA, "ransac_aca: cannot reserve %zu bytes of shared memory", smem);    \
         const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
         k<<<grid, threads, smem, st>>>(c4, offsets, n_hyp, P, params->threshold_px, params->seed,              \
-                                       params->problem_base, T, ws);                                           \
+                                       params->problem_base, T, ws, AdaptiveWs{});                             \
     }
     if (HPT == 1) ACA_SCORE(1)
     else if (HPT == 2) ACA_SCORE(2)
@@ -587,4 +1024,87 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
                                             params->problem_base, ws, best_H, best_count, best_hyp, hyp_counts,
                                             inlier_mask);
     return check_launch("ransac_aca (finish)");
+}
+
+extern "C" size_t ransac_aca_adaptive_workspace_size(int32_t P, int64_t total_max_hyps)
+{
+    if (P < 0 || total_max_hyps < 0)
+        return 0;
+    return adaptive_bytes(P, total_max_hyps, nullptr, nullptr, nullptr);
+}
+
+extern "C" aca_status ransac_aca_adaptive(const float *corr, const int64_t *offsets, const int32_t *max_hyp,
+                                          int32_t P, int64_t total_max_hyps, const aca_ransac_params *params,
+                                          double confidence, float *best_H, int32_t *best_count, int32_t *best_hyp,
+                                          int32_t *n_evaluated, int32_t *hyp_counts, uint8_t *inlier_mask,
+                                          void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (P < 0 || total_max_hyps < 0)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: P < 0 or total_max_hyps < 0");
+    if (P == 0)
+        return ACA_OK;
+    if (!corr || !offsets || !max_hyp || !params || !best_H || !best_count || !best_hyp || !workspace)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: null pointer");
+    if (!aligned16(corr))
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: corr must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: workspace must be 256-byte aligned");
+    const size_t need = adaptive_bytes(P, total_max_hyps, nullptr, nullptr, nullptr);
+    if (workspace_bytes < need)
+        return set_error(ACA_ERR_WORKSPACE, "ransac_aca_adaptive: workspace smaller than %zu bytes", need);
+    if (!(params->threshold_px > 0.0f))
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: threshold_px must be > 0");
+    if (!(confidence > 0.0 && confidence < 1.0))
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: confidence must be in (0, 1)");
+    const int W = params->block_warps ? params->block_warps : 8;
+    const int HPT = params->hyps_per_thread ? params->hyps_per_thread : 2;
+    const int T = params->tile_points ? params->tile_points : 1024;
+    if (W < 1 || W > 16)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: block_warps must be in 1..16");
+    if (HPT != 1 && HPT != 2 && HPT != 4)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: hyps_per_thread must be 1, 2 or 4");
+    if (T < 32 || T > 8192 || T % 32 != 0)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: tile_points must be a multiple of 32 in 32..8192");
+    if (HPT > W)
+        return set_error(ACA_ERR_INVALID_ARG, "ransac_aca_adaptive: need hyps_per_thread <= block_warps");
+    const int HB = 32 * HPT;
+    const cudaStream_t st = as_stream(stream);
+    Workspace ws;
+    AdaptiveWs aw;
+    carve_adaptive(workspace, P, total_max_hyps, ws, aw);
+    aw.log_fail = log(1.0 - confidence);
+
+    ransac_prep_adaptive_kernel<<<1, 1024, 0, st>>>(offsets, max_hyp, P, HB, T, ws, aw);
+    aca_status s = check_launch("ransac_aca_adaptive (prep)");
+    if (s != ACA_OK) return s;
+    {
+        const int threads = 256;
+        const int64_t work = total_max_hyps > aw.cb ? total_max_hyps : aw.cb;
+        const int grid = resident_grid(zero_adaptive_kernel, threads, 0, (work + threads - 1) / threads);
+        zero_adaptive_kernel<<<grid, threads, 0, st>>>(ws, aw, P);
+        if ((s = check_launch("ransac_aca_adaptive (zero)")) != ACA_OK) return s;
+    }
+    const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
+    const int threads = 32 * W;
+    const float4 *c4 = reinterpret_cast<const float4 *>(corr);
+#define ACA_SCORE_ADAPTIVE(HPTV)                                                                               \
+    {                                                                                                          \
+        auto k = ransac_score_kernel<HPTV, true>;                                                              \
+        if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                                     (int)smem) != cudaSuccess)                                \
+            return set_error(ACA_ERR_CUDA, "ransac_aca_adaptive: cannot reserve %zu bytes of shared memory",  \
+                             smem);                                                                            \
+        const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
+        k<<<grid, threads, smem, st>>>(c4, offsets, max_hyp, P, params->threshold_px, params->seed,            \
+                                       params->problem_base, T, ws, aw);                                       \
+    }
+    if (HPT == 1) ACA_SCORE_ADAPTIVE(1)
+    else if (HPT == 2) ACA_SCORE_ADAPTIVE(2)
+    else ACA_SCORE_ADAPTIVE(4)
+#undef ACA_SCORE_ADAPTIVE
+    if ((s = check_launch("ransac_aca_adaptive (score)")) != ACA_OK) return s;
+    ransac_finish_adaptive_kernel<<<P, 512, 0, st>>>(c4, offsets, max_hyp, params->threshold_px, params->seed,
+                                                     params->problem_base, ws, aw, best_H, best_count, best_hyp,
+                                                     n_evaluated, hyp_counts, inlier_mask);
+    return check_launch("ransac_aca_adaptive (finish)");
 }
