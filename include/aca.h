@@ -69,6 +69,11 @@ typedef enum {
  *   H     [9][ld] float, output homographies.
  *   flags [ld] uint8 or NULL: per-set ACA_FLAG_* bits.  Degenerate sets are
  *         not errors: ACA has no division, so H stays finite (rank-deficient).
+ *   pts, H and flags may each be device memory or host memory the device can
+ *   address (page-locked, e.g. cudaHostAlloc or cudaHostRegister): the
+ *   kernel then reads the sets from and writes H to host memory itself, over
+ *   the host link, with no staging copy (zero-copy; on GB300 the link, not
+ *   HBM, then bounds the call).
  *   n     number of sets, 0 <= n <= ld (n = 0 launches nothing).
  *   norm  ACA_NORM_*; ACA_NORM_NONE returns the paper's unnormalised H (the
  *         function aca_backward differentiates).

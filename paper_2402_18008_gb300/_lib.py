@@ -98,9 +98,11 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def _need(t, name, dtype, rows=None):
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+def _need(t, name, dtype, rows=None, host_ok=False):
+    # host_ok: page-locked host tensors are accepted too (the kernel reads and
+    # writes them over the host link itself; nothing runs on the CPU)
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise ValueError(f"{name} must be a CUDA tensor" + (" or a pinned host tensor" if host_ok else ""))
     if t.dtype != dtype:
         raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     if rows is not None:
@@ -120,11 +122,12 @@ def _ld(*ts):
 
 
 def aca_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
-    """C ABI aca_solve on (16, ld) float32 planes -> (9, ld) float32."""
-    _need(pts, "pts", torch.float32, 16)
-    _need(H, "H", torch.float32, 9)
+    """C ABI aca_solve on (16, ld) float32 planes -> (9, ld) float32.  Each
+    tensor may be on the GPU or in pinned host memory (zero-copy)."""
+    _need(pts, "pts", torch.float32, 16, host_ok=True)
+    _need(H, "H", torch.float32, 9, host_ok=True)
     if flags is not None:
-        _need(flags, "flags", torch.uint8)
+        _need(flags, "flags", torch.uint8, host_ok=True)
     ld = _ld(pts, H)
     n = pts.shape[1] if n is None else n
     _check(load().aca_solve(_ptr(pts), _ptr(H), _ptr(flags), n, ld, norm, ctypes.c_void_p(_stream(stream))))

@@ -5,24 +5,31 @@
 //      distance sqrt(2) (two passes over the points);
 //   2. normalised DLT: the 9x9 normal matrix M of the two Eq. 2 rows of every
 //      point (one pass), its eigenvector of the smallest eigenvalue by inverse
-//      iteration on a Cholesky factor (FP64), started from e_k with k the
-//      largest diagonal entry of M^-1 (sum_j v_j[k]^2 / lambda_j, dominated by
-//      the smallest eigenvalue's vector, so e_k has a component of at least
-//      1/3 along it);
+//      iteration on a Cholesky factor, started from e_k with k the largest
+//      diagonal entry of M^-1 (sum_j v_j[k]^2 / lambda_j, dominated by the
+//      smallest eigenvalue's vector, so e_k has a component of at least 1/3
+//      along it);
 //   3. Levenberg-Marquardt on the reprojection error in the normalised frames
 //      (the eight entries of H with h33 = 1), with the damping schedule of
 //      Madsen, Nielsen & Tingleff, "Methods for non-linear least squares
 //      problems" (2004), Alg. 3.16; each trial step is one pass.
 //
-// Precision on GB300, where FP64 runs at 1/64 of the FP32 rate:
+// Precision and speed on GB300, where FP64 runs at 1/64 of the FP32 rate and
+// a serial FP64 chain on one warp is the slowest thing in the block:
 //   - per-point arithmetic is FP32 on O(1) normalised coordinates;
 //   - sums whose cancellation matters (the DLT moments, the gradient J^T r
 //     and the cost) are double-float: FP32 partials over chunks of 8 points,
-//     accumulated by TwoSum, reduced by a fixed shuffle tree (deterministic);
-//     J^T J, which only shapes the step, is summed in FP32;
-//   - the 9x9 DLT solves run in FP64, the 8x8 LM steps in FP32 (an inexact
-//     step only slows the iteration; its fixed point is set by the gradient),
-//     both by one warp with lane i owning row i;
+//     TwoSum accumulation, then per warp a transposition through shared
+//     memory (lane k adds up value k of the 32 lanes; a shuffle tree for the
+//     24 DLT moments, summed once) and a sum over the warps, all in a fixed
+//     order (deterministic); J^T J, which only shapes the step, is summed in
+//     FP32;
+//   - the DLT eigenvector is computed in FP64 when it is the result
+//     (lm_iters = 0) and in FP32 when it only starts LM, which converges to
+//     the same minimiser from either start;
+//   - the 8x8 LM steps are FP32 (an inexact step only slows the iteration;
+//     its fixed point is set by the gradient); parameters and costs stay in
+//     FP64; the small solves run on one warp with lane i owning row i;
 //   - the cost of a trial point carries FP32 rounding noise of about 2^-16
 //     relative, so near the optimum, where the predicted decrease is below
 //     that noise, a step is accepted unless the cost rises by more than the
@@ -35,33 +42,40 @@
 namespace aca {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;         // 2 blocks (of <= 128 registers a thread) per SM
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 8;
-constexpr int kInvIters = 16;         // inverse-iteration cap
+constexpr int kPad = 33;              // transposition row stride (floats per value, padded)
+constexpr int kInvIters = 16;         // inverse-iteration cap (FP64 DLT)
 constexpr float kTau = 1e-3f;         // mu0 = tau * max diag(J^T J)
-constexpr double kEpsStep = 5.9604644775390625e-8;   // 2^-24: parameters are used in FP32
+constexpr float kEpsStep = 5.9604644775390625e-8f;   // 2^-24: parameters are used in FP32
 constexpr double kCostNoise = 1.52587890625e-05;     // 2^-16: FP32 noise of the cost, relative
 
 constexpr int kDF_DLT = 24;           // double-float sums of the DLT pass
 constexpr int kDF_LM = 9;             // gradient (8) and cost (1)
 constexpr int kF_LM = 19;             // J^T J moments
+constexpr int kTr = kDF_LM * 2 * kPad + kF_LM * kPad;   // transposition floats per warp (LM pass)
+static_assert(kDF_LM + kF_LM <= 32, "one lane per LM sum");
 
 struct Shared {
-    DF red[kWarps][kDF_DLT];          // per-warp double-float partials
-    float redf[kWarps][kF_LM];
-    double sum[kDF_DLT];              // block sums (double-float -> FP64)
+    float tr[kWarps][kTr];            // per-warp transposition scratch
+    DF wpart[kWarps][kDF_DLT];        // per-warp double-float sums
+    float wpartf[kWarps][kF_LM];
+    double sum[kDF_DLT];              // block sums (leader warp)
     float sumf[kF_LM];
-    double M[81], L9[81], r9[9];      // DLT normal matrix, Cholesky factor, 1 / diagonal
+    double M[81], L9[81], r9[9];      // DLT (FP64 variant)
+    float Mf[81], L9f[81], r9f[9];    // DLT (FP32 variant)
     double v[9];                      // DLT eigenvector
-    float S8[64], L8[64], r8[8];      // LM matrix, factor, 1 / diagonal
+    float S8[64], L8[64], r8[8];      // LM step matrix, factor, 1 / diagonal
     float par[8];                     // parameters broadcast to the pass
     float mu1x, mu1y, s1, mu2x, mu2y, s2;
     int go;                           // leader -> block decision
     // Levenberg-Marquardt state (leader warp)
     float A[64];                      // J^T J at pd
     double g[8], F;                   // J^T r and ||r||^2 / 2 at pd
-    double pd[8], d[8], mu, nu;
+    double pd[8];                     // parameters
+    float d[8], mu, nu;               // step, damping
+    int it;                           // trial steps taken
 };
 
 // Double-float accumulator: FP32 partials per chunk of kChunk points, then
@@ -95,60 +109,89 @@ __device__ __forceinline__ DF df_renorm(DF x)
     return DF{s, F_SUB(x.l, F_SUB(s, x.h))};
 }
 
-__device__ __forceinline__ DF warp_sum_df(DF x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const DF y{__shfl_xor_sync(0xffffffffu, x.h, o), __shfl_xor_sync(0xffffffffu, x.l, o)};
-        x = df_renorm(df_add(x, y));
-    }
-    return x;
-}
-
-__device__ __forceinline__ float warp_sum_f(float x)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
 
-__device__ __forceinline__ double warp_sum_d(double x)
+template <typename T>
+__device__ __forceinline__ T warp_max(T x)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
     return x;
 }
 
-// Block sums: double-float values into sh.sum[0..K) (as FP64) and FP32 values
-// into sh.sumf[0..KF); visible to all threads on return.
+// Per-warp sums of a pass: each lane writes its K double-float and KF FP32
+// values to the warp's scratch; lane k < K adds up double-float value k over
+// the 32 lanes, lane K + k value k of the FP32 ones; results to wpart.  The
+// caller then synchronises the block and the leader warp calls leader_sums.
 template <int K, int KF>
-__device__ void block_reduce(DF (&s)[K], float (&f)[KF], Shared &sh)
+__device__ void warp_partials(const DF (&s)[K], const float *f, Shared &sh)
+{
+    static_assert(K * 2 * kPad + KF * kPad <= kTr, "pass does not fit the transposition scratch");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *t = sh.tr[warp];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        t[(k * kPad + lane) * 2] = s[k].h;
+        t[(k * kPad + lane) * 2 + 1] = s[k].l;
+    }
+#pragma unroll
+    for (int k = 0; k < KF; ++k) t[K * 2 * kPad + k * kPad + lane] = f[k];
+    __syncwarp();
+    if (lane < K) {
+        const float *r = t + lane * kPad * 2;
+        DF a{r[0], r[1]};
+        for (int i = 1; i < 32; ++i) a = df_add(a, DF{r[2 * i], r[2 * i + 1]});
+        sh.wpart[warp][lane] = df_renorm(a);
+    } else if (lane < K + KF) {
+        const float *r = t + K * 2 * kPad + (lane - K) * kPad;
+        float a = r[0];
+        for (int i = 1; i < 32; ++i) a += r[i];
+        sh.wpartf[warp][lane - K] = a;
+    }
+}
+
+// Per-warp sums by a shuffle tree, for passes with more values than the
+// transposition scratch holds (the DLT moments, once per problem).
+template <int K>
+__device__ void warp_partials_shfl(const DF (&s)[K], Shared &sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const DF v = warp_sum_df(s[k]);
-        if (lane == 0) sh.red[warp][k] = v;
-    }
+        DF x = s[k];
 #pragma unroll
-    for (int k = 0; k < KF; ++k) {
-        const float v = warp_sum_f(f[k]);
-        if (lane == 0) sh.redf[warp][k] = v;
+        for (int o = 16; o > 0; o >>= 1) {
+            const DF y{__shfl_xor_sync(0xffffffffu, x.h, o), __shfl_xor_sync(0xffffffffu, x.l, o)};
+            x = df_renorm(df_add(x, y));
+        }
+        if (lane == 0) sh.wpart[warp][k] = x;
     }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        DF a = sh.red[0][threadIdx.x];
+}
+
+// Leader warp, after the block barrier: sums over the warps into sh.sum
+// (FP64) and sh.sumf; visible to the leader warp on return.
+template <int K, int KF>
+__device__ void leader_sums(Shared &sh)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < K) {
+        DF a = sh.wpart[0][lane];
 #pragma unroll
-        for (int w = 1; w < kWarps; ++w) a = df_renorm(df_add(a, sh.red[w][threadIdx.x]));
-        sh.sum[threadIdx.x] = (double)a.h + (double)a.l;
-    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + KF) {
-        const int k = threadIdx.x - 32;
-        float a = 0.0f;
+        for (int w = 1; w < kWarps; ++w) a = df_renorm(df_add(a, sh.wpart[w][lane]));
+        sh.sum[lane] = (double)a.h + (double)a.l;
+    } else if (lane < K + KF) {
+        float a = sh.wpartf[0][lane - K];
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) a += sh.redf[w][k];
-        sh.sumf[k] = a;
+        for (int w = 1; w < kWarps; ++w) a += sh.wpartf[w][lane - K];
+        sh.sumf[lane - K] = a;
     }
-    __syncthreads();
+    __syncwarp();
 }
 
 // Cholesky factor of the n x n symmetric S (row-major, shared) by one warp:
@@ -209,23 +252,27 @@ __device__ T warp_chol_solve(const T *L, const T *rd, T x)
 
 __device__ __forceinline__ bool take(const uint8_t *mask, int64_t i) { return mask == nullptr || mask[i] != 0; }
 
-// Unit Frobenius norm in FP64, sign so that h33 > 0 (or, when |h33| < 1e-6
-// |H|, so that the entry of largest magnitude is positive); written as FP32.
-__device__ void store_frob(const double h[9], float *out)
+// Calls f(q) for every used point of the block's problem, the block's threads
+// striding over them; each thread keeps kUnroll loads in flight (the passes
+// are otherwise bound by one L2 round trip per point).
+constexpr int kUnroll = 4;
+template <class Fn>
+__device__ __forceinline__ void for_points(const float4 *__restrict__ c, const uint8_t *__restrict__ m, int64_t n,
+                                           Fn &&f)
 {
-    double ss = 0.0;
-    int big = 0;
-    for (int i = 0; i < 9; ++i) {
-        ss += h[i] * h[i];
-        if (fabs(h[i]) > fabs(h[big])) big = i;
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += kUnroll * kThreads) {
+        float4 q[kUnroll];
+        bool t[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = i0 + (int64_t)u * kThreads;
+            t[u] = i < n && take(m, i);
+            q[u] = t[u] ? c[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (t[u]) f(q[u]);
     }
-    const double nrm = sqrt(ss);
-    if (!(nrm > 0.0) || !isfinite(nrm)) {
-        for (int i = 0; i < 9; ++i) out[i] = 0.0f;
-        return;
-    }
-    const double sgn = fabs(h[8]) >= 1e-6 * nrm ? (h[8] > 0 ? 1.0 : -1.0) : (h[big] > 0 ? 1.0 : -1.0);
-    for (int i = 0; i < 9; ++i) out[i] = (float)(sgn * h[i] / nrm);
 }
 
 struct Frame {
@@ -241,12 +288,76 @@ struct Frame {
     }
 };
 
-// One LM pass at the parameters in sh.par.  Sums, with xb = (x, y, 1),
-// b = (x, y), q = 1/w^2:
+// Leader warp: the normalised DLT from the 24 moments in sh.sum, in precision
+// T.  Rows of Eq. 2 per point: (xb, 0, -X xb) and (0, -xb, Y xb), so M has
+// blocks S_1 (twice), -S_X, -S_Y and S_R, S_w = sum w {xx, xy, yy, x, y, 1}.
+// Writes the unit eigenvector to sh.v; returns false if the factorisation
+// failed.
+template <typename T>
+__device__ bool dlt_leader(Shared &sh, T *M, T *L, T *rd, T floor_rel, T tol, int max_iters)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < 81; i += 32) M[i] = T(0);
+    __syncwarp();
+    if (lane < 9) {
+        const int mi[3][3] = {{0, 1, 3}, {1, 2, 4}, {3, 4, 5}};
+        const int i = lane / 3, j = lane % 3, k = mi[i][j];
+        M[i * 9 + j] = (T)sh.sum[k];
+        M[(3 + i) * 9 + 3 + j] = (T)sh.sum[k];
+        M[i * 9 + 6 + j] = -(T)sh.sum[6 + k];
+        M[(6 + j) * 9 + i] = -(T)sh.sum[6 + k];
+        M[(3 + i) * 9 + 6 + j] = -(T)sh.sum[12 + k];
+        M[(6 + j) * 9 + 3 + i] = -(T)sh.sum[12 + k];
+        M[(6 + i) * 9 + 6 + j] = (T)sh.sum[18 + k];
+    }
+    __syncwarp();
+    const T dmax = warp_max(lane < 9 ? M[lane * 10] : T(0));
+    // the pivot floor is a shift far below the eigenvalue gap
+    const bool ok = warp_cholesky<9, T>(M, L, rd, dmax * floor_rel);
+    // diag(M^-1)_k = |L^-1 e_k|^2: lane k solves L z = e_k on its own
+    T dk = T(-1);
+    if (ok && lane < 9) {
+        T z[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            T s = i == lane ? T(1) : T(0);
+#pragma unroll
+            for (int j = 0; j < i; ++j) s -= L[i * 9 + j] * z[j];
+            z[i] = s * rd[i];
+        }
+        dk = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dk += z[i] * z[i];
+    }
+    int kb = lane;
+    T best = dk;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int okb = __shfl_xor_sync(0xffffffffu, kb, o);
+        if (ob > best || (ob == best && okb < kb)) { best = ob; kb = okb; }
+    }
+    T x = lane == kb ? T(1) : T(0);
+    for (int it = 0; ok && it < max_iters; ++it) {
+        T y = warp_chol_solve<9, T>(L, rd, x);
+        const T ny = warp_sum(y * y), dot = warp_sum(y * x);
+        y *= (dot < T(0) ? T(-1) : T(1)) / sqrt(ny);
+        const T ch = warp_max(fabs(y - x));
+        x = y;
+        if (ch < tol) break;
+    }
+    if (lane < 9) sh.v[lane] = ok ? (double)x : 0.0;
+    __syncwarp();
+    return ok;
+}
+
+// One LM pass at the parameters in sh.par: per-warp sums of, with
+// xb = (x, y, 1), b = (x, y), q = 1/w^2:
 //   double-float: g = J^T r (u rows: r_u xb / w; v rows: r_v xb / w;
 //                 perspective: -(u r_u + v r_v) b / w) and ||r||^2;
 //   FP32: sum q {xx, xy, yy, x, y, 1}, sum q u {xx, xy, yy, x, y},
 //         sum q v {...}, sum q (u^2 + v^2) {xx, xy, yy}, the blocks of J^T J.
+// Ends with a block barrier; the leader warp then calls leader_sums.
 __device__ void lm_pass(const float4 *c, const uint8_t *m, int64_t n, Shared &sh)
 {
     DFAcc<kDF_LM> a;
@@ -257,10 +368,9 @@ __device__ void lm_pass(const float4 *c, const uint8_t *m, int64_t n, Shared &sh
     const Frame fr(sh);
     const float p0 = sh.par[0], p1 = sh.par[1], p2 = sh.par[2], p3 = sh.par[3];
     const float p4 = sh.par[4], p5 = sh.par[5], p6 = sh.par[6], p7 = sh.par[7];
-    for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-        if (!take(m, i)) continue;
+    for_points(c, m, n, [&](float4 pt) {
         float x, y, X, Y;
-        fr.apply(c[i], x, y, X, Y);
+        fr.apply(pt, x, y, X, Y);
         const float w = fmaf(p6, x, fmaf(p7, y, 1.0f));
         const float iw = 1.0f / w;
         const float u = fmaf(p0, x, fmaf(p1, y, p2)) * iw;
@@ -282,32 +392,143 @@ __device__ void lm_pass(const float4 *c, const uint8_t *m, int64_t n, Shared &sh
         f[11] = fmaf(qv, xx, f[11]); f[12] = fmaf(qv, xy, f[12]); f[13] = fmaf(qv, yy, f[13]);
         f[14] = fmaf(qv, x, f[14]); f[15] = fmaf(qv, y, f[15]);
         f[16] = fmaf(qr, xx, f[16]); f[17] = fmaf(qr, xy, f[17]); f[18] = fmaf(qr, yy, f[18]);
-    }
+    });
     a.flush();
-    block_reduce<kDF_LM, kF_LM>(a.s, f, sh);
+    warp_partials<kDF_LM, kF_LM>(a.s, f, sh);
+    __syncthreads();
 }
 
 // J^T J (8x8, FP32) from the FP32 sums of lm_pass: blocks
 // sum q xb xb^T (twice), -sum q u xb b^T, -sum q v xb b^T and
-// sum q (u^2 + v^2) b b^T.
+// sum q (u^2 + v^2) b b^T.  Leader warp, lane-parallel.
 __device__ void lm_assemble(const float *s, float A[64])
 {
+    const int lane = threadIdx.x & 31;
     // index of the moment {xx, xy, yy, x, y, 1} of xb_i xb_j
     const int mi[3][3] = {{0, 1, 3}, {1, 2, 4}, {3, 4, 5}};
-    for (int i = 0; i < 64; ++i) A[i] = 0.0f;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            A[i * 8 + j] = s[mi[i][j]];
-            A[(3 + i) * 8 + 3 + j] = s[mi[i][j]];
+    for (int e = lane; e < 64; e += 32) {
+        const int r = e / 8, c = e % 8;
+        float v = 0.0f;
+        if (r < 3 && c < 3) v = s[mi[r][c]];
+        else if (r >= 3 && r < 6 && c >= 3 && c < 6) v = s[mi[r - 3][c - 3]];
+        else if (r < 3 && c >= 6) v = -s[6 + mi[r][c - 6]];
+        else if (r >= 6 && c < 3) v = -s[6 + mi[c][r - 6]];
+        else if (r >= 3 && r < 6 && c >= 6) v = -s[11 + mi[r - 3][c - 6]];
+        else if (r >= 6 && c >= 3 && c < 6) v = -s[11 + mi[c - 3][r - 6]];
+        else if (r >= 6 && c >= 6) v = s[16 + mi[r - 6][c - 6]];
+        A[e] = v;
+    }
+    __syncwarp();
+}
+
+// Leader warp: the next trial step (J^T J + mu I) d = -g, counting every
+// trial (a non-positive-definite matrix is a rejected step).  Returns 1
+// (evaluate pd + d, in sh.par) or 0 (no more trials: the budget is spent, the
+// step is below the FP32 resolution of the parameters, or the damping is no
+// longer finite).
+__device__ int lm_trial(Shared &sh, int budget)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (sh.it >= budget || !(isfinite(sh.mu) && sh.mu > 0.0f)) return 0;
+        if (lane < 8) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sh.S8[lane * 8 + k] = sh.A[lane * 8 + k];
+            sh.S8[lane * 9] += sh.mu;
         }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 2; ++j) {
-            const int k = mi[i][j];   // one of xx, xy, yy, x, y
-            A[i * 8 + 6 + j] = A[(6 + j) * 8 + i] = -s[6 + k];
-            A[(3 + i) * 8 + 6 + j] = A[(6 + j) * 8 + 3 + i] = -s[11 + k];
+        __syncwarp();
+        const bool ok = warp_cholesky<8, float>(sh.S8, sh.L8, sh.r8, 0.0f);
+        __syncwarp();
+        if (lane == 0) sh.it += 1;
+        if (!ok) {
+            if (lane == 0) {
+                sh.mu *= sh.nu;
+                sh.nu *= 2.0f;
+            }
+            __syncwarp();
+            continue;
         }
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) A[(6 + i) * 8 + 6 + j] = s[16 + mi[i][j]];
+        const float dl = warp_chol_solve<8, float>(sh.L8, sh.r8, lane < 8 ? (float)-sh.g[lane] : 0.0f);
+        const float dd = lane < 8 ? dl : 0.0f;
+        const float pp = lane < 8 ? (float)sh.pd[lane] : 0.0f;
+        const float nd = warp_sum(dd * dd), np = warp_sum(pp * pp);
+        if (!(sqrtf(nd) > kEpsStep * (sqrtf(np) + kEpsStep))) return 0;
+        if (lane < 8) {
+            sh.d[lane] = dd;
+            sh.par[lane] = (float)(sh.pd[lane] + (double)dd);
+        }
+        __syncwarp();
+        return 1;
+    }
+}
+
+// Leader warp: gain ratio of the evaluated step; accept or reject it.
+__device__ void lm_update(Shared &sh)
+{
+    const int lane = threadIdx.x & 31;
+    const double Fn = 0.5 * sh.sum[8];
+    const float pl = lane < 8 ? sh.d[lane] * (sh.mu * sh.d[lane] - (float)sh.g[lane]) : 0.0f;
+    const float pred = 0.5f * warp_sum(pl);
+    const float rho = (float)(sh.F - Fn) / pred;
+    const double noise = kCostNoise * sh.F;
+    const bool accept = isfinite(Fn) && (rho > 0.0f || ((double)pred <= noise && Fn <= sh.F + noise));
+    __syncwarp();
+    if (accept) {
+        if (lane < 8) {
+            sh.pd[lane] += (double)sh.d[lane];
+            sh.g[lane] = sh.sum[lane];
+        }
+        lm_assemble(sh.sumf, sh.A);
+        if (lane == 0) {
+            sh.F = Fn;
+            const float t = rho > 0.0f && rho < 1.0f ? 2.0f * rho - 1.0f : 1.0f;
+            sh.mu *= fmaxf(1.0f / 3.0f, 1.0f - t * t * t);
+            sh.nu = 2.0f;
+        }
+    } else if (lane == 0) {
+        sh.mu *= sh.nu;
+        sh.nu *= 2.0f;
+    }
+    __syncwarp();
+}
+
+// Leader warp: H = T2^-1 Hn T1 in pixels, unit Frobenius norm with the sign
+// so that h33 > 0 (or, when |h33| < 1e-6 |H|, the first entry of largest
+// magnitude > 0); lane i writes entry i.
+__device__ void leader_store(const Shared &sh, const double *hn, float *out)
+{
+    const int lane = threadIdx.x & 31;
+    double h = 0.0;
+    if (lane < 9) {
+        const int r = lane / 3, col = lane % 3;
+        const double s1 = sh.s1, a1x = sh.mu1x, a1y = sh.mu1y;
+        // (Hn T1)[r][col]: columns 0, 1 scale by s1, column 2 picks up -s1 mu1
+        auto B = [&](int rr) {
+            return col < 2 ? hn[rr * 3 + col] * s1
+                           : hn[rr * 3 + 2] - s1 * (hn[rr * 3 + 0] * a1x + hn[rr * 3 + 1] * a1y);
+        };
+        // T2^-1 B: rows 0, 1 scaled by 1/s2 plus mu2 times row 2
+        const double b2 = B(2);
+        h = r == 2 ? b2 : B(r) / (double)sh.s2 + (r == 0 ? (double)sh.mu2x : (double)sh.mu2y) * b2;
+    }
+    const double nrm = sqrt(warp_sum(h * h));
+    double ab = lane < 9 ? fabs(h) : -1.0;
+    int big = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oa = __shfl_xor_sync(0xffffffffu, ab, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, big, o);
+        if (oa > ab || (oa == ab && ob < big)) { ab = oa; big = ob; }
+    }
+    const double h8 = __shfl_sync(0xffffffffu, h, 8), hb = __shfl_sync(0xffffffffu, h, big);
+    if (lane < 9) {
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+            out[lane] = 0.0f;
+        } else {
+            const double sgn = fabs(h8) >= 1e-6 * nrm ? (h8 > 0 ? 1.0 : -1.0) : (hb > 0 ? 1.0 : -1.0);
+            out[lane] = (float)(sgn * h / nrm);
+        }
+    }
 }
 
 __device__ void write_empty(float *H_out, float *rms, int p, float rms_value)
@@ -330,20 +551,27 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
     if (n < 0) n = 0;
     const float4 *c = corr + o0;
     const uint8_t *m = mask ? mask + o0 : nullptr;
-    float none[1] = {0.0f};
 
     // Pass 1: count and centroids.
     {
         DFAcc<5> a;
         a.zero();
-        for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-            if (!take(m, i)) continue;
-            const float4 q = c[i];
+        for_points(c, m, n, [&](float4 q) {
             a.f[0] += 1.0f; a.f[1] += q.x; a.f[2] += q.y; a.f[3] += q.z; a.f[4] += q.w;
             a.tick();
-        }
+        });
         a.flush();
-        block_reduce<5, 1>(a.s, none, sh);
+        warp_partials<5, 0>(a.s, nullptr, sh);
+        __syncthreads();
+        if (leader) {
+            leader_sums<5, 0>(sh);
+            if (lane == 0) {
+                const double cnt = sh.sum[0];
+                sh.mu1x = (float)(sh.sum[1] / cnt); sh.mu1y = (float)(sh.sum[2] / cnt);
+                sh.mu2x = (float)(sh.sum[3] / cnt); sh.mu2y = (float)(sh.sum[4] / cnt);
+            }
+        }
+        __syncthreads();
     }
     const double cnt = sh.sum[0];
     const int64_t used = (int64_t)(cnt + 0.5);
@@ -352,35 +580,31 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         write_empty(H_out, rms, p, 0.0f);
         return;
     }
-    __syncthreads();                                // all have read sh.sum
-    if (threadIdx.x == 0) {
-        sh.mu1x = (float)(sh.sum[1] / cnt); sh.mu1y = (float)(sh.sum[2] / cnt);
-        sh.mu2x = (float)(sh.sum[3] / cnt); sh.mu2y = (float)(sh.sum[4] / cnt);
-    }
-    __syncthreads();
 
     // Pass 2: mean distances to the centroids -> scales.
     {
         DFAcc<2> a;
         a.zero();
         const float m1x = sh.mu1x, m1y = sh.mu1y, m2x = sh.mu2x, m2y = sh.mu2y;
-        for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-            if (!take(m, i)) continue;
-            const float4 q = c[i];
+        for_points(c, m, n, [&](float4 q) {
             const float dx = q.x - m1x, dy = q.y - m1y, dX = q.z - m2x, dY = q.w - m2y;
             a.f[0] += sqrtf(fmaf(dx, dx, dy * dy));
             a.f[1] += sqrtf(fmaf(dX, dX, dY * dY));
             a.tick();
-        }
+        });
         a.flush();
-        block_reduce<2, 1>(a.s, none, sh);
+        warp_partials<2, 0>(a.s, nullptr, sh);
+        __syncthreads();
+        if (leader) {
+            leader_sums<2, 0>(sh);
+            if (lane == 0) {
+                const double d1 = sh.sum[0], d2 = sh.sum[1];
+                sh.s1 = d1 > 0.0 ? (float)(1.4142135623730951 * cnt / d1) : 1.0f;
+                sh.s2 = d2 > 0.0 ? (float)(1.4142135623730951 * cnt / d2) : 1.0f;
+            }
+        }
+        __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const double d1 = sh.sum[0], d2 = sh.sum[1];
-        sh.s1 = d1 > 0.0 ? (float)(1.4142135623730951 * cnt / d1) : 1.0f;
-        sh.s2 = d2 > 0.0 ? (float)(1.4142135623730951 * cnt / d2) : 1.0f;
-    }
-    __syncthreads();
 
     // Pass 3: moments of the normalised points for the Eq. 2 normal matrix:
     // S_w = sum w {xx, xy, yy, x, y, 1} for w = 1, X, Y, X^2 + Y^2.
@@ -388,10 +612,9 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         DFAcc<kDF_DLT> a;
         a.zero();
         const Frame fr(sh);
-        for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-            if (!take(m, i)) continue;
+        for_points(c, m, n, [&](float4 pt) {
             float x, y, X, Y;
-            fr.apply(c[i], x, y, X, Y);
+            fr.apply(pt, x, y, X, Y);
             const float mo[6] = {x * x, x * y, y * y, x, y, 1.0f};
             const float R = fmaf(X, X, Y * Y);
 #pragma unroll
@@ -402,69 +625,22 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
                 a.f[18 + k] = fmaf(R, mo[k], a.f[18 + k]);
             }
             a.tick();
-        }
+        });
         a.flush();
-        block_reduce<kDF_DLT, 1>(a.s, none, sh);
+        warp_partials_shfl<kDF_DLT>(a.s, sh);
+        __syncthreads();
     }
 
-    // DLT by the leader warp.  Rows of Eq. 2 per point: (xb, 0, -X xb) and
-    // (0, -xb, Y xb), so M has blocks S_1 (twice), -S_X, -S_Y and S_R.
+    // DLT, then the LM set-up and first trial, by the leader warp.
     if (leader) {
-        for (int i = lane; i < 81; i += 32) sh.M[i] = 0.0;
-        __syncwarp();
-        if (lane < 9) {
-            const int mi[3][3] = {{0, 1, 3}, {1, 2, 4}, {3, 4, 5}};
-            const int i = lane / 3, j = lane % 3, k = mi[i][j];
-            sh.M[i * 9 + j] = sh.sum[k];
-            sh.M[(3 + i) * 9 + 3 + j] = sh.sum[k];
-            sh.M[i * 9 + 6 + j] = -sh.sum[6 + k];
-            sh.M[(6 + j) * 9 + i] = -sh.sum[6 + k];
-            sh.M[(3 + i) * 9 + 6 + j] = -sh.sum[12 + k];
-            sh.M[(6 + j) * 9 + 3 + i] = -sh.sum[12 + k];
-            sh.M[(6 + i) * 9 + 6 + j] = sh.sum[18 + k];
-        }
-        __syncwarp();
-        double dmax = lane < 9 ? sh.M[lane * 10] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        // pivot floor 2^-44 max diag: a shift far below the eigenvalue gap
-        const bool ok = warp_cholesky<9, double>(sh.M, sh.L9, sh.r9, dmax * 5.684341886080802e-14);
-        // diag(M^-1)_k = |L^-1 e_k|^2: lane k solves L z = e_k on its own
-        double dk = -1.0;
-        if (ok && lane < 9) {
-            double z[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                double s = i == lane ? 1.0 : 0.0;
-#pragma unroll
-                for (int j = 0; j < i; ++j) s -= sh.L9[i * 9 + j] * z[j];
-                z[i] = s * sh.r9[i];
-            }
-            dk = 0.0;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) dk += z[i] * z[i];
-        }
-        int kb = lane;
-        double best = dk;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int okb = __shfl_xor_sync(0xffffffffu, kb, o);
-            if (ob > best || (ob == best && okb < kb)) { best = ob; kb = okb; }
-        }
-        double x = lane == kb ? 1.0 : 0.0;
-        for (int it = 0; ok && it < kInvIters; ++it) {
-            double y = warp_chol_solve<9, double>(sh.L9, sh.r9, x);
-            const double ny = warp_sum_d(y * y), dot = warp_sum_d(y * x);
-            y *= (dot < 0 ? -1.0 : 1.0) / sqrt(ny);
-            double ch = fabs(y - x);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, o));
-            x = y;
-            if (ch < 1e-11) break;      // far below the FP32 output
-        }
-        if (lane < 9) sh.v[lane] = ok ? x : 0.0;
-        __syncwarp();
+        leader_sums<kDF_DLT, 0>(sh);
+        // FP64 to convergence when the DLT is the result; FP32 and three
+        // steps (error ratio lambda1 / lambda2 per step) when it only starts
+        // LM.  Pivot floors 2^-44 and 2^-20 of the largest diagonal entry:
+        // near each precision's rounding of M, far below the eigenvalue gap.
+        const bool ok = lm_iters == 0
+                            ? dlt_leader<double>(sh, sh.M, sh.L9, sh.r9, 5.684341886080802e-14, 1e-11, kInvIters)
+                            : dlt_leader<float>(sh, sh.Mf, sh.L9f, sh.r9f, 9.5367431640625e-07f, 0.0f, 3);
         // LM gauge h33 = 1 needs the normalised h33 away from zero (v has unit norm)
         const bool gauge = ok && fabs(sh.v[8]) >= 1e-3;
         if (gauge && lane < 8) {
@@ -479,91 +655,44 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         return;
     }
 
-    // Levenberg-Marquardt: one pass at the start (it also gives the residual
-    // of the DLT when lm_iters = 0), then one pass per trial step.
+    // Levenberg-Marquardt: a pass at the start (it also gives the residual of
+    // the DLT when lm_iters = 0), then one pass per evaluated trial step.
     bool lm_ok = false;
     if (sh.go) {
         lm_pass(c, m, n, sh);
-        if (threadIdx.x == 0) {
+        if (leader) {
+            leader_sums<kDF_LM, kF_LM>(sh);
             lm_assemble(sh.sumf, sh.A);
-            for (int k = 0; k < 8; ++k) sh.g[k] = sh.sum[k];
-            sh.F = 0.5 * sh.sum[8];
-            float dmax = 0.0f;
-            for (int k = 0; k < 8; ++k) dmax = fmaxf(dmax, sh.A[k * 9]);
-            sh.mu = (double)(kTau * dmax);
-            sh.nu = 2.0;
-            sh.go = isfinite(sh.F) && isfinite(sh.mu) && sh.mu > 0.0 ? 1 : 0;
+            if (lane < 8) sh.g[lane] = sh.sum[lane];
+            float dmax = warp_max(lane < 8 ? sh.A[lane * 9] : 0.0f);
+            if (lane == 0) {
+                sh.F = 0.5 * sh.sum[8];
+                sh.mu = kTau * dmax;
+                sh.nu = 2.0f;
+                sh.it = 0;
+            }
+            __syncwarp();
+            const bool ok = isfinite(sh.F) && isfinite(sh.mu) && sh.mu > 0.0f;
+            const int go = ok ? lm_trial(sh, lm_iters) : 0;
+            if (lane == 0) sh.go = ok ? 1 + go : 0;   // 0: no LM; 1: LM, no more steps; 2: evaluate
         }
         __syncthreads();
         lm_ok = sh.go != 0;
-        __syncthreads();
-        for (int it = 0; lm_ok && it < lm_iters; ++it) {
-            // Trial step (J^T J + mu I) d = -g by the leader warp.
+        // sh.go is rewritten by the leader only after the barrier in lm_pass
+        while (sh.go == 2) {
+            lm_pass(c, m, n, sh);
             if (leader) {
-                if (lane < 8) {
-                    for (int k = 0; k < 8; ++k) sh.S8[lane * 8 + k] = sh.A[lane * 8 + k];
-                    sh.S8[lane * 9] += (float)sh.mu;
-                }
-                __syncwarp();
-                const bool ok = warp_cholesky<8, float>(sh.S8, sh.L8, sh.r8, 0.0f);
-                int go = 2;                 // not positive definite: a rejected step
-                if (ok) {
-                    const float dl = warp_chol_solve<8, float>(sh.L8, sh.r8, lane < 8 ? (float)-sh.g[lane] : 0.0f);
-                    const double dd = lane < 8 ? (double)dl : 0.0;
-                    const double pp = lane < 8 ? sh.pd[lane] : 0.0;
-                    const double nd = warp_sum_d(dd * dd), np = warp_sum_d(pp * pp);
-                    if (!(sqrt(nd) > kEpsStep * (sqrt(np) + kEpsStep))) {
-                        go = 0;             // below FP32 resolution (or not finite): converged
-                    } else {
-                        go = 1;
-                        if (lane < 8) {
-                            sh.d[lane] = dd;
-                            sh.par[lane] = (float)(pp + dd);
-                        }
-                    }
-                }
-                if (lane == 0) {
-                    if (go == 2) {
-                        sh.mu *= sh.nu;
-                        sh.nu *= 2.0;
-                        if (!isfinite(sh.mu)) go = 0;
-                    }
-                    sh.go = go;
-                }
+                leader_sums<kDF_LM, kF_LM>(sh);
+                lm_update(sh);
+                const int go = lm_trial(sh, lm_iters);
+                if (lane == 0) sh.go = 1 + go;
             }
             __syncthreads();
-            const int go = sh.go;
-            __syncthreads();                // all have read go before it changes
-            if (go == 0) break;
-            if (go == 2) continue;
-            lm_pass(c, m, n, sh);
-            if (threadIdx.x == 0) {
-                const double Fn = 0.5 * sh.sum[8];
-                double pred = 0.0;
-                for (int k = 0; k < 8; ++k) pred += sh.d[k] * (sh.mu * sh.d[k] - sh.g[k]);
-                pred *= 0.5;
-                const double rho = (sh.F - Fn) / pred;
-                const double noise = kCostNoise * sh.F;
-                const bool accept = isfinite(Fn) && (rho > 0.0 || (pred <= noise && Fn <= sh.F + noise));
-                if (accept) {
-                    for (int k = 0; k < 8; ++k) { sh.pd[k] += sh.d[k]; sh.g[k] = sh.sum[k]; }
-                    lm_assemble(sh.sumf, sh.A);
-                    sh.F = Fn;
-                    const double t = rho > 0.0 && rho < 1.0 ? 2.0 * rho - 1.0 : 1.0;
-                    sh.mu *= fmax(1.0 / 3.0, 1.0 - t * t * t);
-                    sh.nu = 2.0;
-                } else {
-                    sh.mu *= sh.nu;
-                    sh.nu *= 2.0;
-                }
-            }
-            __syncthreads();                // the update is visible to the next trial
         }
     }
-    __syncthreads();
 
-    // Back to pixels: H = T2^-1 Hn T1, unit Frobenius norm.
-    if (threadIdx.x == 0) {
+    // Back to pixels.
+    if (leader) {
         double hn[9];
         if (lm_ok) {
             for (int k = 0; k < 8; ++k) hn[k] = sh.pd[k];
@@ -571,24 +700,8 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         } else {
             for (int k = 0; k < 9; ++k) hn[k] = sh.v[k];
         }
-        const double s1 = sh.s1, s2 = sh.s2;
-        const double a1x = sh.mu1x, a1y = sh.mu1y, a2x = sh.mu2x, a2y = sh.mu2y;
-        // Hn T1: columns scale by s1, the third picks up -s1 mu1.
-        double B[9];
-        for (int r = 0; r < 3; ++r) {
-            B[r * 3 + 0] = hn[r * 3 + 0] * s1;
-            B[r * 3 + 1] = hn[r * 3 + 1] * s1;
-            B[r * 3 + 2] = hn[r * 3 + 2] - s1 * (hn[r * 3 + 0] * a1x + hn[r * 3 + 1] * a1y);
-        }
-        // T2^-1 B: rows 0, 1 scaled by 1/s2 plus mu2 times row 2.
-        double h[9];
-        for (int col = 0; col < 3; ++col) {
-            h[0 + col] = B[0 + col] / s2 + a2x * B[6 + col];
-            h[3 + col] = B[3 + col] / s2 + a2y * B[6 + col];
-            h[6 + col] = B[6 + col];
-        }
-        store_frob(h, H_out + 9 * (int64_t)p);
-        if (rms) rms[p] = lm_ok ? (float)(sqrt(2.0 * sh.F / cnt) / s2) : -1.0f;
+        leader_store(sh, hn, H_out + 9 * (int64_t)p);
+        if (lane == 0 && rms) rms[p] = lm_ok ? (float)(sqrt(2.0 * sh.F / cnt) / (double)sh.s2) : -1.0f;
     }
 }
 

@@ -214,3 +214,22 @@ def test_affine_three_point_solver_parity(n, ld):
         X = a[:, 0] * s[2 * k] + a[:, 1] * s[2 * k + 1] + a[:, 2]
         Y = a[:, 3] * s[2 * k] + a[:, 4] * s[2 * k + 1] + a[:, 5]
         assert np.max(np.hypot(X - s[6 + 2 * k], Y - s[7 + 2 * k])) < 1e-2
+
+
+@pytest.mark.parametrize("n", [1000, (1 << 18) + 5])
+def test_solve_on_pinned_host_buffers_matches_device_buffers(n):
+    # zero-copy: the kernel reads the sets from and writes H and the flags to
+    # page-locked host memory; results are bit-identical to HBM buffers
+    ms = workloads.minimal_sets(n, seed=12)
+    pts_d = cuda(ms.pts)
+    H_d = torch.empty((9, n), device="cuda")
+    f_d = torch.empty(n, dtype=torch.uint8, device="cuda")
+    _lib.aca_solve(pts_d, H_d, f_d)
+    pts_h = torch.from_numpy(ms.pts).pin_memory()
+    H_h = torch.full((9, n), 7.0).pin_memory()
+    f_h = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    _lib.aca_solve(pts_h, H_h, f_h)
+    torch.cuda.synchronize()
+    assert torch.equal(H_h, H_d.cpu()) and torch.equal(f_h, f_d.cpu())
+    with pytest.raises(ValueError):
+        _lib.aca_solve(torch.from_numpy(ms.pts), H_h)        # pageable host memory is refused
