@@ -619,13 +619,32 @@ def row_diff(torch, _lib, rect, stream, dev):
     pts4 = torch.from_numpy(np.concatenate([src, rect.tgt], axis=0)).to(dev)
     Hg = torch.empty((9, B), dtype=torch.float32, device=dev)
     plain = lambda: _lib.aca_solve(pts4, Hg, None, n=B)
-    for f in (fwd_bwd, plain):
+    # comparison: the same Eq. 42 as plain torch tensor operations with torch
+    # autograd for the backward (one kernel per operation)
+    tgt_t = tgt.clone().requires_grad_(True)
+
+    def torch_fwd_bwd():
+        x0, y0, w, r = (float(v) for v in rect.rect)
+        Mx, My, Nx, Ny, Px, Py, Qx, Qy = tgt_t
+        MPx, MPy, MQx, MQy = Px - Mx, Py - My, Qx - Mx, Qy - My
+        q4x = MQx * MPy - MQy * MPx
+        q4y = (Nx - Mx) * MQy - (Ny - My) * MQx
+        t2 = (Px - Nx) * (Qy - Ny) - (Py - Ny) * (Qx - Nx)
+        b13, b23, b33 = -q4x * x0, -r * q4y * y0, -t2 * (x0 + r * y0 + w)
+        Ht = torch.stack([Nx * q4x + Mx * t2, Px * r * q4y + Mx * r * t2, Nx * b13 + Px * b23 + Mx * b33,
+                          Ny * q4x + My * t2, Py * r * q4y + My * r * t2, Ny * b13 + Py * b23 + My * b33,
+                          q4x + t2, r * q4y + r * t2, b13 + b23 + b33])
+        tgt_t.grad = None
+        (Ht * gH).sum().backward()
+    for f in (fwd_bwd, plain, torch_fwd_bwd):
         for _ in range(5):
             f()
     tfb = time_region(torch, fwd_bwd, 200, stream)
     tpl = time_region(torch, plain, 200, stream)
+    ttt = time_region(torch, torch_fwd_bwd, 50, stream)
     out["diff_aca_rect_65536"] = {"value": B / (tfb * 1e-3), "unit": "sets/s (fwd+bwd)", "ms_fwd_bwd": tfb,
-                                  "ms_plain_aca_solve": tpl, "ratio_vs_plain": tfb / tpl}
+                                  "ms_plain_aca_solve": tpl, "ratio_vs_plain": tfb / tpl,
+                                  "ms_torch_ops_autograd_fwd_bwd": ttt, "speedup_vs_torch_ops": ttt / tfb}
     return out
 
 

@@ -97,3 +97,43 @@ def test_ransac_rejects_bad_arguments():
         for k, v in bad.items():
             setattr(q, k, v)
         assert call(1, q, aligned, 4096) == -1, bad
+
+
+def test_adaptive_ransac_rejects_bad_arguments():
+    L = _lib.load()
+    p = _lib.RansacParams(threshold_px=3.0, seed=1)
+    need = _lib.ransac_aca_adaptive_workspace_size(1, 64)
+    assert need > _lib.ransac_aca_workspace_size(1, 64)
+    assert _lib.ransac_aca_adaptive_workspace_size(512, 8388608) > _lib.ransac_aca_adaptive_workspace_size(512, 1000)
+    assert _lib.ransac_aca_adaptive_workspace_size(-1, 5) == 0
+    buf = (ctypes.c_uint8 * (need + 512))()
+    base = (ctypes.addressof(buf) + 255) & ~255
+    ws, one = ctypes.c_void_p(base), ctypes.c_void_p(base + 256)
+
+    def call(P, conf, nbytes, params=p, total=64):
+        return L.ransac_aca_adaptive(one, one, one, P, total, ctypes.byref(params), conf, one, one, one, None, None,
+                                     None, ws, nbytes, None)
+    assert call(-1, 0.99, need) == -1
+    assert call(0, 0.99, need) == 0                        # nothing to do
+    for conf in (0.0, 1.0, -0.1, float("nan")):
+        assert call(1, conf, need) == -1, conf
+    assert call(1, 0.99, need - 256) == -3                 # workspace smaller than the layout
+    assert call(1, 0.99, need, total=-1) == -1
+    q = _lib.RansacParams(threshold_px=3.0, seed=1, hyps_per_thread=3)
+    assert call(1, 0.99, need, params=q) == -1
+
+
+def test_refit_and_affine_reject_bad_arguments():
+    buf = (ctypes.c_uint8 * 1024)()
+    a = (ctypes.addressof(buf) + 255) & ~255
+    good, odd = ctypes.c_void_p(a), ctypes.c_void_p(a + 4)
+    assert _call("aca_refit", good, good, None, -1, 10, good, None, None, None)[0] == -1
+    assert _call("aca_refit", good, good, None, 0, 10, good, None, None, None)[0] == 0      # P = 0
+    assert _call("aca_refit", good, good, None, 1, -1, good, None, None, None)[0] == -1
+    assert _call("aca_refit", good, good, None, 1, 10001, good, None, None, None)[0] == -1
+    assert _call("aca_refit", None, good, None, 1, 10, good, None, None, None)[0] == -1
+    st, msg = _call("aca_refit", odd, good, None, 1, 10, good, None, None, None)
+    assert st == -1 and "aligned" in msg
+    assert _call("aca_affine_solve", None, None, 5, 4, 0, None)[0] == -1
+    assert _call("aca_affine_solve", None, None, 4, 4, 9, None)[0] == -1
+    assert _call("aca_affine_solve", None, None, 0, 0, 0, None)[0] == 0
