@@ -531,6 +531,61 @@ __device__ void leader_store(const Shared &sh, const double *hn, float *out)
     }
 }
 
+// Longest first: block b takes the problem of rank b in the order of
+// decreasing size class (size = correspondences, class = octave and quarter
+// octave: 4 log2(N) rounded down), then increasing index.  The largest
+// problems set the kernel's length; started in the first wave they finish
+// while the small ones fill the SMs.  Every block ranks all P problems
+// (two passes over the offsets), so above kOrderMaxP problems the natural
+// order is used.
+constexpr int kClasses = 128;
+constexpr int32_t kOrderMaxP = 1 << 16;
+
+__device__ __forceinline__ int size_class(int64_t N)
+{
+    if (N <= 0) return 0;
+    const uint64_t u = (uint64_t)N;
+    const int e = 63 - __clzll((long long)u);                 // floor(log2 N)
+    const int f = e >= 2 ? (int)((u >> (e - 2)) & 3u) : (int)((u << (2 - e)) & 3u);
+    const int c = 4 * e + f;
+    return c < kClasses ? c : kClasses - 1;
+}
+
+__device__ int32_t longest_first(const int64_t *__restrict__ offsets, int32_t P, int32_t b, int32_t *hist,
+                                 int32_t *scratch)
+{
+    for (int k = threadIdx.x; k < kClasses; k += kThreads) hist[k] = 0;
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q < P; q += kThreads) atomicAdd(&hist[size_class(offsets[q + 1] - offsets[q])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // class of rank b: classes in decreasing order
+        int32_t above = 0, kb = kClasses - 1;
+        for (; kb > 0 && above + hist[kb] <= b; --kb) above += hist[kb];
+        scratch[0] = kb;
+        scratch[1] = b - above;                                 // rank within the class
+        scratch[2] = -1;
+    }
+    __syncthreads();
+    const int kb = scratch[0];
+    const int32_t j = scratch[1];
+    int32_t before = 0;                                         // class members of lower index so far
+    for (int32_t base = 0; base < P && scratch[2] < 0; base += kThreads) {
+        const int32_t q = base + (int32_t)threadIdx.x;
+        const bool mine = q < P && size_class(offsets[q + 1] - offsets[q]) == kb;
+        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) scratch[4 + warp] = __popc(bal);
+        __syncthreads();
+        int32_t wbefore = before;
+        for (int w = 0; w < warp; ++w) wbefore += scratch[4 + w];
+        if (mine && wbefore + __popc(bal & ((1u << lane) - 1u)) == j) scratch[2] = q;
+        for (int w = 0; w < kWarps; ++w) before += scratch[4 + w];
+        __syncthreads();
+    }
+    return scratch[2];
+}
+
 __device__ void write_empty(float *H_out, float *rms, int p, float rms_value)
 {
     if (threadIdx.x < 9) H_out[9 * (int64_t)p + threadIdx.x] = 0.0f;
@@ -543,7 +598,9 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
              int32_t *__restrict__ n_used, float *__restrict__ rms)
 {
     __shared__ Shared sh;
-    const int p = blockIdx.x;
+    __shared__ int32_t s_hist[kClasses], s_scr[4 + kWarps];
+    const int32_t P = gridDim.x;
+    const int p = P <= kOrderMaxP ? longest_first(offsets, P, blockIdx.x, s_hist, s_scr) : (int)blockIdx.x;
     const int lane = threadIdx.x & 31;
     const bool leader = threadIdx.x < 32;          // warp 0 runs the small solves
     const int64_t o0 = offsets[p];
