@@ -716,6 +716,26 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
     }
 }
 
+// Inlier mask of one problem under the test-form hypothesis G, the block's
+// threads striding over the points with four loads in flight each.
+__device__ void write_mask(const float G[9], const float4 *__restrict__ c, int64_t N, float nthr2, bool any,
+                           uint8_t *__restrict__ out)
+{
+    for (int64_t i0 = threadIdx.x; i0 < N; i0 += 4 * (int64_t)blockDim.x) {
+        float4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * (int64_t)blockDim.x;
+            q[u] = any && i < N ? c[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * (int64_t)blockDim.x;
+            if (i < N) out[i] = any ? (uint8_t)inlier(G, q[u], nthr2) : (uint8_t)0;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__restrict__ corr,
                                                             const int64_t *__restrict__ offsets,
                                                             const int32_t *__restrict__ n_hyp, int32_t P, float thr,
@@ -737,10 +757,21 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
 
     int32_t bc = -1, bi = 0x7fffffff;
     if (!overflow && N >= 4) {
-        for (int32_t h = threadIdx.x; h < k; h += blockDim.x) {
-            const int32_t c = ws.counts[hb + h];
-            if (hyp_counts) hyp_counts[hb + h] = c;
-            if (c > bc || (c == bc && h < bi)) { bc = c; bi = h; }
+        // four counts in flight per thread (one L2 round trip per four)
+        for (int32_t h0 = threadIdx.x; h0 < k; h0 += 4 * (int32_t)blockDim.x) {
+            int32_t c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t h = h0 + u * (int32_t)blockDim.x;
+                c[u] = h < k ? ws.counts[hb + h] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t h = h0 + u * (int32_t)blockDim.x;
+                if (h >= k) break;
+                if (hyp_counts) hyp_counts[hb + h] = c[u];
+                if (c[u] > bc || (c[u] == bc && h < bi)) { bc = c[u]; bi = h; }
+            }
         }
     } else if (!overflow && hyp_counts) {
         for (int32_t h = threadIdx.x; h < k; h += blockDim.x) hyp_counts[hb + h] = -1;
@@ -777,9 +808,7 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
         for (int i = 0; i < 9; ++i) H[i] = sH[i];
         to_test_form(G, H);
         const float nthr2 = -F_MUL(thr, thr);
-        const bool any = s_best >= 0;
-        for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
-            mask[base + i] = any ? (uint8_t)inlier(G, corr[base + i], nthr2) : (uint8_t)0;
+        write_mask(G, corr + base, N, nthr2, s_best >= 0, mask + base);
     }
 }
 
@@ -913,9 +942,7 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
         for (int i = 0; i < 9; ++i) H[i] = sH[i];
         to_test_form(G, H);
         const float nthr2 = -F_MUL(thr, thr);
-        const bool any = s_bi >= 0;
-        for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
-            mask[base + i] = any ? (uint8_t)inlier(G, corr[base + i], nthr2) : (uint8_t)0;
+        write_mask(G, corr + base, N, nthr2, s_bi >= 0, mask + base);
     }
 }
 
