@@ -176,3 +176,21 @@ def test_ransac_plan_with_refit_in_a_cuda_graph():
     assert torch.equal(H2, rep.refit_H)
     # every masked point is within 3 px of the RANSAC H; the refit minimises the cost
     assert float(rep.refit_rms.max()) < 3.0
+
+
+def test_refit_many_small_problems_beyond_the_ordering_limit():
+    # more problems than the longest-first ordering ranks (natural order
+    # above 65536): per-problem results do not depend on the order, so a
+    # subset refit alone must give bit-identical outputs
+    P, k = 70000, 6
+    rp = workloads.ransac_problem(P * k, 1.0, 0.5, seed=33)
+    corr = rp.corr
+    offsets = np.arange(P + 1, dtype=np.int64) * k
+    H, n_used, rms = _gpu_refit(corr, offsets, None, 10)
+    assert np.all(n_used == k)
+    sub = 1000
+    Hs, ns, rs = _gpu_refit(corr[:sub * k], offsets[:sub + 1], None, 10)
+    assert np.array_equal(Hs, H[:sub]) and np.array_equal(rs, rms[:sub])
+    idx = np.arange(0, P, 7001)
+    sel = np.concatenate([np.arange(i * k, (i + 1) * k) for i in idx])
+    _gate(H[idx], corr[sel], np.arange(idx.size + 1) * k, np.ones(sel.size, bool), 200, "70000 problems, sampled")
