@@ -190,3 +190,25 @@ def test_full_size_512_pairs_sampled_against_the_oracle():
         assert g["best_count"][p] == gc.max() and g["best_hyp"][p] == int(np.argmax(gc == gc.max()))
         if not o["band_counts"].any():
             assert g["best_hyp"][p] == o["best_hyp"][0]
+
+
+def test_non_finite_correspondences_are_never_inliers():
+    # NaN and +-Inf coordinates (sign bits of both kinds): a hypothesis drawn
+    # from such points has a non-finite H and counts nothing; a non-finite
+    # point is never an inlier (the FP32 test yields NaN, never a negative e)
+    rp = workloads.ransac_problem(1500, 0.6, 1.0, seed=44)
+    corr = rp.corr.copy()
+    rng = np.random.default_rng(7)
+    bad = rng.choice(1500, 150, replace=False)
+    vals = np.array([np.nan, -np.nan, np.inf, -np.inf], np.float32)
+    corr[bad, rng.integers(0, 4, 150)] = vals[rng.integers(0, 4, 150)]
+    k = 1024
+    g = _np(_run(corr, [0, 1500], [k], 3.0, 17))
+    o = oracle.ransac(corr, [0, 1500], [k], 3.0, 17, band_px=BAND_PX, herr=HERR)
+    finite = np.isfinite(corr).all(axis=1)
+    assert not g["inlier_mask"][~finite].any()
+    ok = np.isfinite(o["hyp_counts"]) & (o["hyp_counts"] >= 0)
+    d = np.abs(g["hyp_counts"] - o["hyp_counts"])
+    assert np.array_equal(g["hyp_counts"] < 0, o["hyp_counts"] < 0)
+    assert np.all(d[ok] <= o["band_counts"][ok])
+    assert g["best_count"][0] == g["hyp_counts"].max() and g["best_count"][0] >= 0.5 * finite.sum()
