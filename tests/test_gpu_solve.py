@@ -233,3 +233,28 @@ def test_solve_on_pinned_host_buffers_matches_device_buffers(n):
     assert torch.equal(H_h, H_d.cpu()) and torch.equal(f_h, f_d.cpu())
     with pytest.raises(ValueError):
         _lib.aca_solve(torch.from_numpy(ms.pts), H_h)        # pageable host memory is refused
+
+
+@pytest.mark.parametrize("solver", ["aca", "sks"])
+def test_all_24_correspondence_orders_of_a_rectangle_source(solver):
+    # a rectangle source in every one of the 24 orders of its corners (the
+    # orders for which a pivot-free elimination divides by zero included):
+    # the same homography each time, within the conditioning gate
+    import itertools
+    rb = workloads.rect_batch(64, seed=21)
+    x0, y0, w, r = rb.rect
+    src = np.array([[x0, y0], [x0 + w, y0], [x0, y0 + w / r], [x0 + w, y0 + w / r]])   # M N P Q
+    tgt = rb.tgt.T.reshape(64, 4, 2).astype(np.float64)
+    sets = []
+    for perm in itertools.permutations(range(4)):
+        s = np.concatenate([src[list(perm)].reshape(1, 8).repeat(64, 0), tgt[:, list(perm)].reshape(64, 8)], axis=1)
+        sets.append(s)
+    S = np.concatenate(sets).astype(np.float32).T.copy()                # (16, 24 * 64)
+    H = torch.empty((9, S.shape[1]), device="cuda")
+    (_lib.aca_solve if solver == "aca" else _lib.sks_solve)(cuda(S), H)
+    torch.cuda.synchronize()
+    g = planes_to_rows(H, S.shape[1])
+    ref = oracle.aca(S)
+    kappa_gate(unit_aligned_err(g, ref), oracle.aca_condition(S), f"{solver} 24 orders")
+    per = unit_aligned_err(g.reshape(24, 64, 9).reshape(-1, 9), np.tile(ref[:64], (24, 1)))
+    assert per.max() < 2e-4
