@@ -651,6 +651,9 @@ static int side_degenerate(const double *p)
 
 int oracle_sample_degenerate(const double *s16)
 {
+    /* a sample with a non-finite coordinate is degenerate (it defines no map) */
+    for (int k = 0; k < 16; ++k)
+        if (!isfinite(s16[k])) return 1;
     return side_degenerate(s16) || side_degenerate(s16 + 8);
 }
 

@@ -71,7 +71,8 @@ __device__ __forceinline__ bool sample_degenerate(const AcaParts &p)
 }
 
 // Hypothesis h of a problem whose N >= 4 correspondences start at `c`:
-// sample, reject degenerate samples, solve by ACA and scale H by a power of
+// sample, reject degenerate samples (a non-finite coordinate, or a triple
+// near collinear), solve by ACA and scale H by a power of
 // two so that its largest entry lies in [1, 2) (exact; keeps the squared
 // residuals of the test far from overflow).  Returns false if degenerate.
 __device__ __forceinline__ bool make_hypothesis(const float4 *__restrict__ c, uint32_t N, uint64_t seed,
@@ -81,6 +82,14 @@ __device__ __forceinline__ bool make_hypothesis(const float4 *__restrict__ c, ui
     sample4(seed, prob, h, N, idx);
     const float4 m = c[idx[0]], n = c[idx[1]], p4 = c[idx[2]], q = c[idx[3]];
     const Set s{m.x, m.y, n.x, n.y, p4.x, p4.y, q.x, q.y, m.z, m.w, n.z, n.w, p4.z, p4.w, q.z, q.w};
+    // a sample with a non-finite coordinate is degenerate: x * 0 is 0 for
+    // every finite x and NaN otherwise
+    const float *sv = &s.M1x;
+    float z = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) z = F_FMA(sv[k], 0.0f, z);
+    if (!(z == 0.0f))
+        return false;
     AcaParts p;
     aca_parts(s, p);
     if (sample_degenerate(p))

@@ -185,3 +185,13 @@ def test_ambiguity_band_contains_the_fixed_band_and_grows_with_the_error_model()
     rq = workloads.ransac_problem(300, 1.0, 0.0, seed=9)
     c, b = oracle.score_problem(rq.corr, 64, 3.0, seed=1, band_px=1e-3, herr=16)
     assert np.mean(b[c == 300] == 0) > 0.9
+
+
+def test_a_sample_with_a_non_finite_coordinate_is_degenerate():
+    ms = workloads.minimal_sets(8, seed=3)
+    s = oracle.sets_aos(ms.pts)
+    assert not any(oracle.sample_degenerate(s[i]) for i in range(8))
+    for k, v in ((0, np.nan), (5, np.inf), (9, -np.inf), (15, -np.nan)):
+        t = s[k % 8].copy()
+        t[k] = v
+        assert oracle.sample_degenerate(t)
