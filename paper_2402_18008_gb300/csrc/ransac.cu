@@ -44,6 +44,7 @@
 // everything after it is reported as not evaluated.
 #include "aca_math.cuh"
 #include "common.cuh"
+#include "pdl.cuh"
 #include "philox.cuh"
 
 namespace aca {
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__rest
 {
     __shared__ int64_t wt_a[32], wt_b[32];
     __shared__ int64_t carry_a, carry_b;
+    grid_launch_dependents();
     if (threadIdx.x == 0) {
         carry_a = 0;
         carry_b = 0;
@@ -381,6 +383,7 @@ __global__ void __launch_bounds__(1024) ransac_prep_adaptive_kernel(const int64_
     __shared__ int64_t wt_a[32], wt_b[32], wt_c[32];
     __shared__ int64_t carry_a, carry_b, carry_c;
     __shared__ int32_t s_rounds;
+    grid_launch_dependents();
     if (threadIdx.x == 0) {
         carry_a = carry_b = carry_c = 0;
         s_rounds = 0;
@@ -495,6 +498,8 @@ __global__ void __launch_bounds__(1024) ransac_prep_adaptive_kernel(const int64_
 // Clears the counts and the chunk completion counters of the adaptive variant.
 __global__ void zero_adaptive_kernel(Workspace ws, AdaptiveWs aw, int32_t P)
 {
+    grid_launch_dependents();
+    grid_dependency_wait();
     if (*ws.flags) return;
     const int64_t nc = ws.hyp_off[P], nk = aw.chunk_off[P];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -504,6 +509,8 @@ __global__ void zero_adaptive_kernel(Workspace ws, AdaptiveWs aw, int32_t P)
 
 __global__ void zero_counts_kernel(Workspace ws, int32_t P)
 {
+    grid_launch_dependents();
+    grid_dependency_wait();
     const int64_t total = ws.hyp_off[P];
     const int64_t lim = total < ws.capacity ? total : ws.capacity;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += (int64_t)gridDim.x * blockDim.x)
@@ -564,6 +571,8 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
     const float2 nthr2 = make_float2(nthr2s, nthr2s);
     const float nanv = __int_as_float(0x7fc00000);
 
+    grid_launch_dependents();
+    grid_dependency_wait();
     const int64_t total = ws.item_off[P];
     const int32_t R = ADAPTIVE ? *aw.rounds : 0;
     for (;;) {
@@ -754,6 +763,8 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
                                                             int32_t *__restrict__ hyp_counts,
                                                             uint8_t *__restrict__ mask)
 {
+    grid_launch_dependents();
+    grid_dependency_wait();
     const int32_t p = blockIdx.x;
     const int64_t base = offsets[p];
     const int64_t N = offsets[p + 1] - base;
@@ -834,6 +845,8 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
     int32_t *__restrict__ hyp_counts, uint8_t *__restrict__ mask)
 {
     constexpr int kTile = 2048, kPer = 4;
+    grid_launch_dependents();
+    grid_dependency_wait();
     const int32_t p = blockIdx.x;
     const int64_t base = offsets[p];
     const int64_t N = offsets[p + 1] - base;
@@ -1035,7 +1048,7 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
     if (!zero_in_prep) {
         const int threads = 256;
         const int grid = resident_grid(zero_counts_kernel, threads, 0, (ws.capacity + threads - 1) / threads);
-        zero_counts_kernel<<<grid, threads, 0, st>>>(ws, P);
+        launch_after_previous(zero_counts_kernel, dim3(grid), dim3(threads), 0, st, ws, P);
         if ((s = check_launch("ransac_aca (zero)")) != ACA_OK) return s;
     }
     const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
@@ -1048,17 +1061,17 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
                                                      (int)smem) != cudaSuccess)                                \
             return set_error(ACA_ERR_CUDA, "ransac_aca: cannot reserve %zu bytes of shared memory", smem);    \
         const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
-        k<<<grid, threads, smem, st>>>(c4, offsets, n_hyp, P, params->threshold_px, params->seed,              \
-                                       params->problem_base, T, ws, AdaptiveWs{});                             \
+        launch_after_previous(k, dim3(grid), dim3(threads), smem, st, c4, offsets, n_hyp, P,                   \
+                              params->threshold_px, params->seed, params->problem_base, T, ws, AdaptiveWs{}); \
     }
     if (HPT == 1) ACA_SCORE(1)
     else if (HPT == 2) ACA_SCORE(2)
     else ACA_SCORE(4)
 #undef ACA_SCORE
     if ((s = check_launch("ransac_aca (score)")) != ACA_OK) return s;
-    ransac_finish_kernel<<<P, 256, 0, st>>>(c4, offsets, n_hyp, P, params->threshold_px, params->seed,
-                                            params->problem_base, ws, best_H, best_count, best_hyp, hyp_counts,
-                                            inlier_mask);
+    launch_after_previous(ransac_finish_kernel, dim3(P), dim3(256), 0, st, c4, offsets, n_hyp, P,
+                          params->threshold_px, params->seed, params->problem_base, ws, best_H, best_count, best_hyp,
+                          hyp_counts, inlier_mask);
     return check_launch("ransac_aca (finish)");
 }
 
@@ -1117,7 +1130,7 @@ extern "C" aca_status ransac_aca_adaptive(const float *corr, const int64_t *offs
         const int threads = 256;
         const int64_t work = total_max_hyps > aw.cb ? total_max_hyps : aw.cb;
         const int grid = resident_grid(zero_adaptive_kernel, threads, 0, (work + threads - 1) / threads);
-        zero_adaptive_kernel<<<grid, threads, 0, st>>>(ws, aw, P);
+        launch_after_previous(zero_adaptive_kernel, dim3(grid), dim3(threads), 0, st, ws, aw, P);
         if ((s = check_launch("ransac_aca_adaptive (zero)")) != ACA_OK) return s;
     }
     const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
@@ -1131,16 +1144,16 @@ extern "C" aca_status ransac_aca_adaptive(const float *corr, const int64_t *offs
             return set_error(ACA_ERR_CUDA, "ransac_aca_adaptive: cannot reserve %zu bytes of shared memory",  \
                              smem);                                                                            \
         const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
-        k<<<grid, threads, smem, st>>>(c4, offsets, max_hyp, P, params->threshold_px, params->seed,            \
-                                       params->problem_base, T, ws, aw);                                       \
+        launch_after_previous(k, dim3(grid), dim3(threads), smem, st, c4, offsets, max_hyp, P,                 \
+                              params->threshold_px, params->seed, params->problem_base, T, ws, aw);           \
     }
     if (HPT == 1) ACA_SCORE_ADAPTIVE(1)
     else if (HPT == 2) ACA_SCORE_ADAPTIVE(2)
     else ACA_SCORE_ADAPTIVE(4)
 #undef ACA_SCORE_ADAPTIVE
     if ((s = check_launch("ransac_aca_adaptive (score)")) != ACA_OK) return s;
-    ransac_finish_adaptive_kernel<<<P, 512, 0, st>>>(c4, offsets, max_hyp, params->threshold_px, params->seed,
-                                                     params->problem_base, ws, aw, best_H, best_count, best_hyp,
-                                                     n_evaluated, hyp_counts, inlier_mask);
+    launch_after_previous(ransac_finish_adaptive_kernel, dim3(P), dim3(512), 0, st, c4, offsets, max_hyp,
+                          params->threshold_px, params->seed, params->problem_base, ws, aw, best_H, best_count,
+                          best_hyp, n_evaluated, hyp_counts, inlier_mask);
     return check_launch("ransac_aca_adaptive (finish)");
 }

@@ -38,6 +38,7 @@
 
 #include "common.cuh"
 #include "fp32.cuh"
+#include "pdl.cuh"
 
 namespace aca {
 namespace {
@@ -599,6 +600,8 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
 {
     __shared__ Shared sh;
     __shared__ int32_t s_hist[kClasses], s_scr[4 + kWarps];
+    grid_launch_dependents();
+    grid_dependency_wait();                 // may follow a RANSAC finish kernel that writes the mask
     const int32_t P = gridDim.x;
     const int p = P <= kOrderMaxP ? longest_first(offsets, P, blockIdx.x, s_hist, s_scr) : (int)blockIdx.x;
     const int lane = threadIdx.x & 31;
@@ -775,7 +778,7 @@ extern "C" aca_status aca_refit(const float *corr, const int64_t *offsets, const
     if (P == 0) return ACA_OK;
     if (!corr || !offsets || !H) return set_error(ACA_ERR_INVALID_ARG, "aca_refit: null corr, offsets or H");
     if (!aligned16(corr)) return set_error(ACA_ERR_INVALID_ARG, "aca_refit: corr must be 16-byte aligned");
-    refit_kernel<<<P, kThreads, 0, as_stream(stream)>>>(reinterpret_cast<const float4 *>(corr), offsets, mask,
-                                                        lm_iters, H, n_used, rms);
+    launch_after_previous(refit_kernel, dim3(P), dim3(kThreads), 0, as_stream(stream),
+                          reinterpret_cast<const float4 *>(corr), offsets, mask, lm_iters, H, n_used, rms);
     return check_launch("aca_refit");
 }
