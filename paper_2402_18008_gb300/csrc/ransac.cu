@@ -23,7 +23,10 @@
 //  4. ransac_finish_kernel  one block per problem: argmax (ties to the lowest
 //                           index), re-solve of the winner with the same
 //                           device code (bit-identical H), inlier mask, outputs.
-// There are no inter-block waits: progress only needs the atomics.
+// There are no inter-block waits: progress only needs the atomics.  Kernels
+// 2-4 are launched as programmatic dependents of their predecessor (they are
+// scheduled while it runs and wait for it with griddepcontrol.wait before
+// touching its data), which hides the launch gaps of short problems.
 //
 // With the online adaptive stop (ransac_aca_adaptive, Sec. 6.2: the loop
 // count follows from the best inlier ratio so far), the same scoring loop
