@@ -411,7 +411,11 @@ def row_latency(torch, _lib, pts, H, n_total, stream):
     cost excluded, as in a kernel-time measurement); plus the host-side cost
     of one eager call through the Python binding."""
     res = {}
-    for m in sorted(PAPER_TABLE8_ACA_US):
+    # Table 8's sample numbers plus the 1K-20K range of the paper's Fig. 8
+    # (where its per-H time levels off, near its GPU's core count), extended
+    # to 40K for GB300's 19456 FP32 lanes
+    sizes = sorted(set(PAPER_TABLE8_ACA_US) | {2000, 5000, 15000, 20000, 30000, 40000})
+    for m in sizes:
         if m > n_total:
             break
         f = lambda: _lib.aca_solve(pts, H, None, n=m)
@@ -430,7 +434,7 @@ def row_latency(torch, _lib, pts, H, n_total, stream):
         t = time_region(torch, g.replay, 10, stream) / 100
         eager = time_region(torch, f, 200, stream)
         res[str(m)] = {"us": t * 1e3, "ns_per_set": t * 1e6 / m, "eager_call_us": eager * 1e3,
-                       "paper_rtx3090_fp64_us": PAPER_TABLE8_ACA_US[m]}
+                       "paper_rtx3090_fp64_us": PAPER_TABLE8_ACA_US.get(m)}
     return {"aca_latency_sweep": res}
 
 
