@@ -223,7 +223,6 @@ ACA_HD bool near_collinear(float cr, float la, float lb, float lc)
     return F_MUL(cr, cr) < L;
 }
 
-ACA_HD bool finite_(float x) { return x - x == 0.0f; }
 
 ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 {
@@ -240,11 +239,12 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
         near_collinear(p.t1, lNP1, lNQ1, lPQ1) || near_collinear(p.Q4x, lMQ2, lMP2, lPQ2) ||
         near_collinear(p.Q4y, lMN2, lMQ2, lNQ2) || near_collinear(p.t2, lNP2, lNQ2, lPQ2))
         f |= kFlagOtherTriple;
-    bool fin = true;
+    // x * 0 is 0 for every finite x and NaN otherwise: one FMA per value
     const float *sv = &s.M1x;
-    for (int i = 0; i < 16; ++i) fin = fin && finite_(sv[i]);
-    for (int i = 0; i < 9; ++i) fin = fin && finite_(H[i]);
-    if (!fin) f |= kFlagNonFinite;
+    float z = 0.0f;
+    for (int i = 0; i < 16; ++i) z = F_FMA(sv[i], 0.0f, z);
+    for (int i = 0; i < 9; ++i) z = F_FMA(H[i], 0.0f, z);
+    if (!(z == 0.0f)) f |= kFlagNonFinite;
     return f;
 }
 
