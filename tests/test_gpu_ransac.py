@@ -212,3 +212,29 @@ def test_non_finite_correspondences_are_never_inliers():
     assert np.array_equal(g["hyp_counts"] < 0, o["hyp_counts"] < 0)
     assert np.all(d[ok] <= o["band_counts"][ok])
     assert g["best_count"][0] == g["hyp_counts"].max() and g["best_count"][0] >= 0.5 * finite.sum()
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_many_small_problems_match_single_problem_launches(adaptive):
+    # 20000 problems (more than one pass of the set-up kernel's 1024-thread
+    # scans) of 30-60 points: sampled problems equal their own one-problem
+    # launches bit for bit (problem_base = p keeps the Philox streams)
+    rng = np.random.default_rng(11)
+    P = 20000
+    Ns = rng.integers(30, 61, P)
+    rp = workloads.ransac_problem(int(Ns.sum()), 0.7, 1.0, seed=45)
+    offsets = np.concatenate([[0], np.cumsum(Ns)]).astype(np.int64)
+    k = np.full(P, 64, np.int32)
+    kw = dict(confidence=0.99) if adaptive else {}
+    g = _np(_run(rp.corr, offsets, k, 3.0, 6, **kw))
+    for p in rng.choice(P, 6, replace=False):
+        a, b = int(offsets[p]), int(offsets[p + 1])
+        plan = api.RansacPlan(cuda(rp.corr[a:b]), cuda(np.array([0, b - a], np.int64)), cuda(k[p:p + 1]), 3.0, 6, 64,
+                              problem_base=int(p), want_counts=True, want_mask=True, **kw)
+        s = _np(plan.run())
+        assert s["best_hyp"][0] == g["best_hyp"][p] and s["best_count"][0] == g["best_count"][p]
+        assert np.array_equal(s["best_H"][0], g["best_H"][p])
+        assert np.array_equal(s["hyp_counts"], g["hyp_counts"][64 * p:64 * (p + 1)])
+        assert np.array_equal(s["inlier_mask"], g["inlier_mask"][a:b])
+        if adaptive:
+            assert s["n_evaluated"][0] == g["n_evaluated"][p]
