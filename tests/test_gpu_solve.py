@@ -258,3 +258,32 @@ def test_all_24_correspondence_orders_of_a_rectangle_source(solver):
     kappa_gate(unit_aligned_err(g, ref), oracle.aca_condition(S), f"{solver} 24 orders")
     per = unit_aligned_err(g.reshape(24, 64, 9).reshape(-1, 9), np.tile(ref[:64], (24, 1)))
     assert per.max() < 2e-4
+
+
+def test_solve_beyond_32_bit_offsets():
+    # n = 2^30 + 3 sets, ld = 2^30 + 4: plane offsets reach 2^34 floats (64 GiB
+    # in, 36 GiB out on the device).  The sets are 1024 copies of 2^20
+    # generated ones plus 3 more: every copy must give bit-identical H, a
+    # sample must pass the oracle gate, and the padding column stays untouched.
+    m, reps = 1 << 20, 1 << 10
+    n, ld = m * reps + 3, m * reps + 4
+    ms = workloads.minimal_sets(m, seed=23)
+    base = cuda(ms.pts)
+    pts = torch.empty((16, ld), device="cuda")
+    for r in range(reps):
+        pts[:, r * m:(r + 1) * m].copy_(base)
+    pts[:, m * reps:n].copy_(base[:, :3])
+    H = torch.full((9, ld), 7.0, device="cuda")
+    _lib.aca_solve(pts, H, n=n)
+    torch.cuda.synchronize()
+    first = H[:, :m]
+    for r in (1, 511, reps - 1):
+        assert torch.equal(H[:, r * m:(r + 1) * m], first), r
+    assert torch.equal(H[:, m * reps:n], first[:, :3])
+    assert torch.all(H[:, n:] == 7.0)
+    idx = np.random.default_rng(4).choice(m, 4096, replace=False)
+    g = first[:, torch.from_numpy(idx).cuda()].cpu().numpy().T.astype(np.float64)
+    sub = ms.pts[:, idx]
+    kappa_gate(unit_aligned_err(g, oracle.aca(sub)), oracle.aca_condition(sub), "2^30 + 3 sets")
+    del pts, H
+    torch.cuda.empty_cache()
