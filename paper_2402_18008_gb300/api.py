@@ -41,6 +41,16 @@ def rect_solve(tgt: torch.Tensor, rect, out: torch.Tensor | None = None):
     return H
 
 
+def affine_solve(pts: torch.Tensor, norm: int = ACA_NORM_NONE, n: int | None = None,
+                 out: torch.Tensor | None = None):
+    """3-point affine maps (Eq. 38).  pts: (12, ld) float32 planes M1 N1 P1 M2
+    N2 P2 (x, y each).  Returns H (9, ld)."""
+    _require_cuda(pts, "pts")
+    H = out if out is not None else torch.empty((9, pts.stride(0)), dtype=torch.float32, device=pts.device)
+    _lib.aca_affine_solve(pts, H, n=pts.shape[1] if n is None else n, norm=norm)
+    return H
+
+
 def to_planes(src: torch.Tensor, tgt: torch.Tensor, ld: int | None = None) -> torch.Tensor:
     """(B, 4, 2) source and target corners (M, N, P, Q order) -> (16, ld) planes."""
     B = src.shape[0]

@@ -181,6 +181,10 @@ def test_api_solve_and_layout_helpers():
     H, fl = api.solve(pts, norm=_lib.ACA_NORM_FROB, with_flags=True)
     M = api.planes_to_mats(H, 64).cpu().numpy().reshape(64, 9)
     assert np.abs(M - oracle.normalize_frob(oracle.aca(ms.pts))).max() < H_TOL
+    p12 = torch.from_numpy(np.ascontiguousarray(np.concatenate([ms.pts[0:6], ms.pts[8:14]], axis=0))).cuda()
+    Ha = api.affine_solve(p12, norm=_lib.ACA_NORM_FROB)
+    ref = oracle.normalize_frob(oracle.aca_affine(p12.cpu().numpy()))
+    assert np.abs(planes_to_rows(Ha, 64) - ref).max() < H_TOL
 
 
 def _affine_planes(ms):
