@@ -2,9 +2,11 @@
 // the global optimisation with all inliers that ends the RANSAC pipeline
 // (Sec. 6.2, stage 5).  One block per problem:
 //   1. Hartley normalisation of each side: centroid to the origin, mean
-//      distance sqrt(2) (two passes over the points);
+//      distance sqrt(2) (the centroids in a first pass over the points, the
+//      mean distances in a second);
 //   2. normalised DLT: the 9x9 normal matrix M of the two Eq. 2 rows of every
-//      point (one pass), its eigenvector of the smallest eigenvalue by inverse
+//      point (from moments of the centred points taken in the same second
+//      pass and scaled afterwards), its eigenvector of the smallest eigenvalue by inverse
 //      iteration on a Cholesky factor, started from e_k with k the largest
 //      diagonal entry of M^-1 (sum_j v_j[k]^2 / lambda_j, dominated by the
 //      smallest eigenvalue's vector, so e_k has a component of at least 1/3
@@ -52,7 +54,8 @@ constexpr float kTau = 1e-3f;         // mu0 = tau * max diag(J^T J)
 constexpr float kEpsStep = 5.9604644775390625e-8f;   // 2^-24: parameters are used in FP32
 constexpr double kCostNoise = 1.52587890625e-05;     // 2^-16: FP32 noise of the cost, relative
 
-constexpr int kDF_DLT = 24;           // double-float sums of the DLT pass
+constexpr int kDF_DLT = 24;           // moments of the normalised points (the DLT)
+constexpr int kDF_P2 = kDF_DLT + 2;   // double-float sums of pass 2 (moments + 2 distance sums)
 constexpr int kDF_LM = 9;             // gradient (8) and cost (1)
 constexpr int kF_LM = 19;             // J^T J moments
 constexpr int kTr = kDF_LM * 2 * kPad + kF_LM * kPad;   // transposition floats per warp (LM pass)
@@ -60,9 +63,9 @@ static_assert(kDF_LM + kF_LM <= 32, "one lane per LM sum");
 
 struct Shared {
     float tr[kWarps][kTr];            // per-warp transposition scratch
-    DF wpart[kWarps][kDF_DLT];        // per-warp double-float sums
+    DF wpart[kWarps][kDF_P2];         // per-warp double-float sums
     float wpartf[kWarps][kF_LM];
-    double sum[kDF_DLT];              // block sums (leader warp)
+    double sum[kDF_P2];               // block sums (leader warp)
     float sumf[kF_LM];
     double M[81], L9[81], r9[9];      // DLT (FP64 variant)
     float Mf[81], L9f[81], r9f[9];    // DLT (FP32 variant)
@@ -641,40 +644,18 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         return;
     }
 
-    // Pass 2: mean distances to the centroids -> scales.
+    // Pass 2: mean distances to the centroids (-> the scales s1, s2) and the
+    // moments of the centred points, S_w = sum w {xx, xy, yy, x, y, 1} for
+    // w = 1, X, Y, X^2 + Y^2; those of the normalised points follow by
+    // scaling each by s1^(degree in x, y) s2^(degree in X, Y).
     {
-        DFAcc<2> a;
+        DFAcc<kDF_P2> a;
         a.zero();
         const float m1x = sh.mu1x, m1y = sh.mu1y, m2x = sh.mu2x, m2y = sh.mu2y;
         for_points(c, m, n, [&](float4 q) {
-            const float dx = q.x - m1x, dy = q.y - m1y, dX = q.z - m2x, dY = q.w - m2y;
-            a.f[0] += sqrtf(fmaf(dx, dx, dy * dy));
-            a.f[1] += sqrtf(fmaf(dX, dX, dY * dY));
-            a.tick();
-        });
-        a.flush();
-        warp_partials<2, 0>(a.s, nullptr, sh);
-        __syncthreads();
-        if (leader) {
-            leader_sums<2, 0>(sh);
-            if (lane == 0) {
-                const double d1 = sh.sum[0], d2 = sh.sum[1];
-                sh.s1 = d1 > 0.0 ? (float)(1.4142135623730951 * cnt / d1) : 1.0f;
-                sh.s2 = d2 > 0.0 ? (float)(1.4142135623730951 * cnt / d2) : 1.0f;
-            }
-        }
-        __syncthreads();
-    }
-
-    // Pass 3: moments of the normalised points for the Eq. 2 normal matrix:
-    // S_w = sum w {xx, xy, yy, x, y, 1} for w = 1, X, Y, X^2 + Y^2.
-    {
-        DFAcc<kDF_DLT> a;
-        a.zero();
-        const Frame fr(sh);
-        for_points(c, m, n, [&](float4 pt) {
-            float x, y, X, Y;
-            fr.apply(pt, x, y, X, Y);
+            const float x = q.x - m1x, y = q.y - m1y, X = q.z - m2x, Y = q.w - m2y;
+            a.f[kDF_DLT] += sqrtf(fmaf(x, x, y * y));
+            a.f[kDF_DLT + 1] += sqrtf(fmaf(X, X, Y * Y));
             const float mo[6] = {x * x, x * y, y * y, x, y, 1.0f};
             const float R = fmaf(X, X, Y * Y);
 #pragma unroll
@@ -687,13 +668,28 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
             a.tick();
         });
         a.flush();
-        warp_partials_shfl<kDF_DLT>(a.s, sh);
+        warp_partials_shfl<kDF_P2>(a.s, sh);
         __syncthreads();
     }
 
     // DLT, then the LM set-up and first trial, by the leader warp.
     if (leader) {
-        leader_sums<kDF_DLT, 0>(sh);
+        leader_sums<kDF_P2, 0>(sh);
+        const double d1 = sh.sum[kDF_DLT], d2 = sh.sum[kDF_DLT + 1];
+        const float s1 = d1 > 0.0 ? (float)(1.4142135623730951 * cnt / d1) : 1.0f;
+        const float s2 = d2 > 0.0 ? (float)(1.4142135623730951 * cnt / d2) : 1.0f;
+        if (lane < kDF_DLT) {
+            const int dm[6] = {2, 2, 2, 1, 1, 0}, dw[4] = {0, 1, 1, 2};
+            double f = 1.0;
+            for (int e = 0; e < dm[lane % 6]; ++e) f *= (double)s1;
+            for (int e = 0; e < dw[lane / 6]; ++e) f *= (double)s2;
+            sh.sum[lane] *= f;
+        }
+        if (lane == 0) {
+            sh.s1 = s1;
+            sh.s2 = s2;
+        }
+        __syncwarp();
         // FP64 to convergence when the DLT is the result; FP32 and three
         // steps (error ratio lambda1 / lambda2 per step) when it only starts
         // LM.  Pivot floors 2^-44 and 2^-20 of the largest diagonal entry:
