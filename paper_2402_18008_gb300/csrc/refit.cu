@@ -562,13 +562,31 @@ __device__ int32_t longest_first(const int64_t *__restrict__ offsets, int32_t P,
     __syncthreads();
     for (int32_t q = threadIdx.x; q < P; q += kThreads) atomicAdd(&hist[size_class(offsets[q + 1] - offsets[q])], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // class of rank b: classes in decreasing order
-        int32_t above = 0, kb = kClasses - 1;
-        for (; kb > 0 && above + hist[kb] <= b; --kb) above += hist[kb];
-        scratch[0] = kb;
-        scratch[1] = b - above;                                 // rank within the class
-        scratch[2] = -1;
+    if (threadIdx.x < 32) {
+        // class of rank b, classes in decreasing order: lane l holds classes
+        // 127 - 4l .. 124 - 4l; a warp scan gives the count above each
+        const int lane = threadIdx.x;
+        int32_t c[4], tot = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = hist[kClasses - 1 - 4 * lane - u];
+            tot += c[u];
+        }
+        int32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int32_t above = incl - tot;                             // counts of the classes before this lane's
+        const unsigned hit = __ballot_sync(0xffffffffu, above <= b && b < incl);
+        if (lane == __ffs(hit) - 1) {
+            int u = 0;
+            while (u < 3 && above + c[u] <= b) above += c[u++];
+            scratch[0] = kClasses - 1 - 4 * lane - u;
+            scratch[1] = b - above;                             // rank within the class
+            scratch[2] = -1;
+        }
     }
     __syncthreads();
     const int kb = scratch[0];
