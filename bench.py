@@ -602,8 +602,18 @@ def row_refit(torch, _lib, api, rb, stream, dev, fixed=None):
         for _ in range(3):
             plan.replay()
         times[name] = time_region(torch, plan.replay, 20, stream)
+    # the paper's stages 3-5 without knowing the inlier ratios: the online
+    # adaptive stop (99 %, cap 16384 per pair) and the refit, one graph
+    caps = torch.full((P,), ADAPTIVE_CAP, dtype=torch.int32, device=dev)
+    plan = api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, ADAPTIVE_CAP * P, confidence=0.99, refit_iters=10,
+                          **best).capture()
+    for _ in range(3):
+        plan.replay()
+    times["adaptive_plus_refit"] = time_region(torch, plan.replay, 20, stream)
     res.update(ms_ransac_with_mask=times["ransac_only"], ms_ransac_plus_refit=times["ransac_plus_refit"],
-               refit_share_of_pipeline=1.0 - times["ransac_only"] / times["ransac_plus_refit"])
+               refit_share_of_pipeline=1.0 - times["ransac_only"] / times["ransac_plus_refit"],
+               ms_adaptive_ransac_plus_refit=times["adaptive_plus_refit"],
+               us_per_pair_adaptive_ransac_plus_refit=times["adaptive_plus_refit"] * 1e3 / P)
     return {"refit_512": res}
 
 
