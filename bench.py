@@ -553,9 +553,12 @@ def row_adaptive(torch, api, rb, stream, dev, fixed=None):
     k = torch.from_numpy(rb.n_hyp).to(dev)
     make = lambda **kw: api.RansacPlan(corr, off, k, RANSAC_THR, SEED, int(rb.n_hyp.sum()), **kw)
     best = fixed or autotune.tune(make, P, int(rb.offsets[-1]), int(rb.n_hyp.sum()), device=dev)[0]
-    res = {"unit": "ms per batch", "pairs": P, "cap": ADAPTIVE_CAP, "confidence": 0.99, "tuning": best,
+    make_a = lambda **kw: api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, tot, confidence=0.99, **kw)
+    best_a = fixed or autotune.tune(make_a, P, int(rb.offsets[-1]), tot, device=dev, tag="adaptive")[0]
+    res = {"unit": "ms per batch", "pairs": P, "cap": ADAPTIVE_CAP, "confidence": 0.99, "tuning": best_a,
+           "tuning_fixed_count": best,
            "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9]; one graph replay each"}
-    plans = {"adaptive": api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, tot, confidence=0.99, **best),
+    plans = {"adaptive": make_a(**best_a),
              "fixed_cap": api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, tot, **best),
              "fixed_from_true_ratio": make(**best)}
     for name, plan in plans.items():

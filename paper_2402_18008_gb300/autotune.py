@@ -38,9 +38,9 @@ def _bucket(P: int, total_points: int, total_hyps: int) -> str:
     return f"P{lg(P)}-N{lg(total_points / max(1, P))}-K{lg(total_hyps / max(1, P))}"
 
 
-def _key(device, P, total_points, total_hyps) -> str:
+def _key(device, P, total_points, total_hyps, tag="") -> str:
     props = torch.cuda.get_device_properties(device)
-    return f"{props.name}|{props.multi_processor_count}|{_bucket(P, total_points, total_hyps)}"
+    return f"{props.name}|{props.multi_processor_count}|{_bucket(P, total_points, total_hyps)}" + (f"|{tag}" if tag else "")
 
 
 def _load():
@@ -76,11 +76,13 @@ def time_plan(plan, reps: int = 10) -> float:
 
 
 def tune(make_plan, P: int, total_points: int, total_hyps: int, device=None, candidates=None, reps: int = 10,
-         use_cache: bool = True):
+         use_cache: bool = True, tag: str = ""):
     """Return (best_params, {str(params): ms}).  make_plan(**params) builds a
-    RansacPlan for the workload with the given launch parameters."""
+    RansacPlan for the workload with the given launch parameters; `tag`
+    separates cache entries of different plan kinds (e.g. the adaptive stop)
+    for the same workload shape."""
     device = device if device is not None else torch.cuda.current_device()
-    key = _key(device, P, total_points, total_hyps)
+    key = _key(device, P, total_points, total_hyps, tag)
     with _lock:
         cache = _load() if use_cache else {}
         if key in cache:
