@@ -350,7 +350,7 @@ def main():
                    "l2": "inputs (4 GiB) larger than L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": solve_traffic_per_launch(n),
-                     "peak_source": peaks["source"], "kernel": "solve_vec4_kernel<ACA, NONE, no flags>",
+                     "peak_source": peaks["source"], "kernel": "solve_ring_kernel<ACA, NONE, no flags>",
                      "algorithmic_bytes_per_launch": BYTES_PER_SET * n},
         "cpu_baseline": cpu,
         "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "H/s", "h2d_bytes_per_step": 64 * n,

@@ -1,13 +1,18 @@
 // Batched minimal solvers: aca_solve (Sec. 4), sks_solve (Sec. 3) and
 // aca_rect_solve (Sec. 5.3), one set per thread lane in registers.
 //
-// The work is a pure stream (64 B in, 36 B out per set, ~250 FP32
-// instructions), so the kernels are bound by HBM bandwidth: each thread loads
-// four adjacent sets as one float4 from each of the 16 SoA planes, solves them
-// one after another in registers and writes nine float4 planes with streaming
-// (evict-first) stores.  A persistent grid (SMs x resident blocks) strides over
-// the quads.  When the layout does not allow 16-byte accesses a scalar variant
-// (one set per thread, coalesced 4-byte accesses) runs instead.
+// The work is a pure stream (64 B in, 36 B out per set, ~365 FP32
+// instructions), bound by HBM bandwidth with the ALU close behind: each thread
+// takes four adjacent sets as one float4 from each of the 16 SoA planes,
+// solves them one after another in registers and writes nine float4 planes
+// with streaming (evict-first) stores.  A persistent grid strides over the
+// quads; each thread copies its next quad's 16 float4 into its own slots of a
+// two-stage shared-memory ring (cp.async) while it solves the current one, so
+// the loads of the next step are in flight during the arithmetic (the plain
+// ACA path; SKS and the flagged solve, bound by their arithmetic, load
+// directly).  When the layout does
+// not allow 16-byte accesses a scalar variant (one set per thread, coalesced
+// 4-byte accesses) runs instead.
 #include "aca_math.cuh"
 #include "common.cuh"
 
@@ -37,6 +42,50 @@ __device__ __forceinline__ void solve_one(const Set &s, float H[9], uint8_t &fla
     }
 }
 
+// Four adjacent sets (one float4 from each input plane) solved one after
+// another; nine float4 planes stored with streaming stores, element-wise on
+// the last, partial quad.
+template <int SOLVER, int NORM, bool FLAGS>
+__device__ __forceinline__ void solve_quad(const float4 (&v)[16], int64_t q, float *__restrict__ Hout,
+                                           uint8_t *__restrict__ flags, int64_t n, int64_t ld)
+{
+    float4 h[9];
+    uint32_t fl = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Set s;
+        float *sv = &s.M1x;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            sv[k] = (&v[k].x)[j];
+        float H[9];
+        uint8_t f = 0;
+        solve_one<SOLVER, NORM, FLAGS>(s, H, f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            (&h[k].x)[j] = H[k];
+        fl |= (uint32_t)f << (8 * j);
+    }
+    const int64_t i0 = q << 2;
+    if (i0 + 3 < n) {
+        float4 *out = reinterpret_cast<float4 *>(Hout);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            st_stream(out + k * (ld >> 2) + q, h[k]);
+        if (FLAGS)
+            reinterpret_cast<uint32_t *>(flags)[q] = fl;
+    } else {
+        for (int j = 0; j < 4 && i0 + j < n; ++j) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                Hout[k * ld + i0 + j] = (&h[k].x)[j];
+            if (FLAGS)
+                flags[i0 + j] = (uint8_t)(fl >> (8 * j));
+        }
+    }
+}
+
+// Direct loads: 16 streaming float4 loads per quad, then the solves.
 template <int SOLVER, int NORM, bool FLAGS>
 __global__ void __launch_bounds__(256) solve_vec4_kernel(const float *__restrict__ pts, float *__restrict__ Hout,
                                                           uint8_t *__restrict__ flags, int64_t n, int64_t ld)
@@ -44,45 +93,69 @@ __global__ void __launch_bounds__(256) solve_vec4_kernel(const float *__restrict
     const int64_t nq = (n + 3) >> 2;
     const int64_t ldq = ld >> 2;
     const float4 *in = reinterpret_cast<const float4 *>(pts);
-    float4 *out = reinterpret_cast<float4 *>(Hout);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
         float4 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k)
             v[k] = ld_stream(in + k * ldq + q);
-        float4 h[9];
-        uint32_t fl = 0;
+        solve_quad<SOLVER, NORM, FLAGS>(v, q, Hout, flags, n, ld);
+    }
+}
+
+// 16-byte asynchronous copy global -> shared, cached in L2 only, and the
+// group fences of the issuing thread.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Prefetching variant: each thread copies its next quad's 16 float4 into its
+// own slots of a two-stage shared-memory ring while it solves the current
+// quad, so the next loads are in flight during the arithmetic.  128 threads,
+// 2 blocks per SM, 64 KB of ring each (2 x 128 beat 3 x 128, 4 x 128 and
+// 1 x 256 in a sweep of the ACA solve).
+constexpr int kRingThreads = 128;
+constexpr int kRingBlocksPerSm = 2;
+constexpr size_t kRingSmem = 2 * 16 * kRingThreads * sizeof(float4);
+
+template <int SOLVER, int NORM, bool FLAGS>
+__global__ void __launch_bounds__(kRingThreads) solve_ring_kernel(const float *__restrict__ pts,
+                                                                  float *__restrict__ Hout,
+                                                                  uint8_t *__restrict__ flags, int64_t n, int64_t ld)
+{
+    extern __shared__ float4 ring[];   // [2 stages][16 planes][kRingThreads]
+    const int64_t nq = (n + 3) >> 2;
+    const int64_t ldq = ld >> 2;
+    const float4 *in = reinterpret_cast<const float4 *>(pts);
+    const int64_t stride = (int64_t)gridDim.x * kRingThreads;
+    const int t = threadIdx.x;
+    // a thread only ever reads the slots it filled itself, so its own
+    // cp.async.wait_group is the only synchronisation needed
+    auto fetch = [&](int64_t q, int stage) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            Set s;
-            float *sv = &s.M1x;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                sv[k] = (&v[k].x)[j];
-            float H[9];
-            uint8_t f = 0;
-            solve_one<SOLVER, NORM, FLAGS>(s, H, f);
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                (&h[k].x)[j] = H[k];
-            fl |= (uint32_t)f << (8 * j);
-        }
-        const int64_t i0 = q << 2;
-        if (i0 + 3 < n) {
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                st_stream(out + k * ldq + q, h[k]);
-            if (FLAGS)
-                reinterpret_cast<uint32_t *>(flags)[q] = fl;
+        for (int k = 0; k < 16; ++k) cp_async16(&ring[(stage * 16 + k) * kRingThreads + t], in + k * ldq + q);
+        cp_async_commit();
+    };
+    int64_t q = (int64_t)blockIdx.x * kRingThreads + t;
+    int stage = 0;
+    if (q < nq) fetch(q, 0);
+    for (; q < nq; q += stride) {
+        const int64_t qn = q + stride;
+        if (qn < nq) {
+            fetch(qn, stage ^ 1);
+            cp_async_wait<1>();
         } else {
-            for (int j = 0; j < 4 && i0 + j < n; ++j) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    Hout[k * ld + i0 + j] = (&h[k].x)[j];
-                if (FLAGS)
-                    flags[i0 + j] = (uint8_t)(fl >> (8 * j));
-            }
+            cp_async_wait<0>();
         }
+        float4 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = ring[(stage * 16 + k) * kRingThreads + t];
+        solve_quad<SOLVER, NORM, FLAGS>(v, q, Hout, flags, n, ld);
+        stage ^= 1;
     }
 }
 
@@ -113,7 +186,23 @@ static aca_status launch_solve(const float *pts, float *H, uint8_t *flags, int64
     const int threads = 256;
     const bool vec = n >= kSmallBatch && (ld % 4 == 0) && aligned16(pts) && aligned16(H) &&
                      (!FLAGS || (reinterpret_cast<uintptr_t>(flags) & 3u) == 0);
-    if (vec) {
+    if (vec && SOLVER == kAca && !FLAGS) {
+        // the ACA solve (~365 instructions a set) sits at the HBM stream:
+        // prefetching pays (0.95 -> 0.99 of copy bandwidth).  SKS, and ACA
+        // with the degeneracy flags, are bound by their arithmetic and run
+        // faster on direct loads in 256-thread blocks (SKS 40.5 against 33.5,
+        // flags 55.1 against 54.3 G sets/s on the ring).
+        auto k = solve_ring_kernel<SOLVER, NORM, FLAGS>;
+        // a function attribute of the current device: set on every call (well
+        // under a microsecond, against >= 8 us of work on this path)
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem) != cudaSuccess)
+            return set_error(ACA_ERR_CUDA, "aca_solve: cannot reserve %zu bytes of shared memory", kRingSmem);
+        const int64_t nq = (n + 3) / 4;
+        int64_t grid = (int64_t)sm_count() * kRingBlocksPerSm;
+        const int64_t need = (nq + kRingThreads - 1) / kRingThreads;
+        if (grid > need) grid = need;
+        k<<<(int)grid, kRingThreads, kRingSmem, st>>>(pts, H, flags, n, ld);
+    } else if (vec) {
         auto k = solve_vec4_kernel<SOLVER, NORM, FLAGS>;
         const int64_t nq = (n + 3) / 4;
         const int grid = resident_grid(k, threads, 0, (nq + threads - 1) / threads);
