@@ -113,21 +113,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Prefetching variant: each thread copies its next quad's 16 float4 into its
-// own slots of a two-stage shared-memory ring while it solves the current
-// quad, so the next loads are in flight during the arithmetic.  128 threads,
-// 2 blocks per SM, 64 KB of ring each (2 x 128 beat 3 x 128, 4 x 128 and
-// 1 x 256 in a sweep of the ACA solve).
+// Prefetching stream over quads: each thread copies its next quad's PLANES
+// float4 into its own slots of a two-stage shared-memory ring while it
+// solves the current quad, so the next loads are in flight during the
+// arithmetic.  128 threads, 2 blocks per SM (2 x 128 beat 3 x 128, 4 x 128
+// and 1 x 256 in a sweep of the ACA solve).
 constexpr int kRingThreads = 128;
 constexpr int kRingBlocksPerSm = 2;
-constexpr size_t kRingSmem = 2 * 16 * kRingThreads * sizeof(float4);
+template <int PLANES>
+constexpr size_t ring_smem() { return 2 * PLANES * kRingThreads * sizeof(float4); }
 
-template <int SOLVER, int NORM, bool FLAGS>
-__global__ void __launch_bounds__(kRingThreads) solve_ring_kernel(const float *__restrict__ pts,
-                                                                  float *__restrict__ Hout,
-                                                                  uint8_t *__restrict__ flags, int64_t n, int64_t ld)
+template <int PLANES, typename QuadFn>
+__device__ __forceinline__ void ring_stream(const float *__restrict__ pts, int64_t n, int64_t ld, QuadFn &&solve)
 {
-    extern __shared__ float4 ring[];   // [2 stages][16 planes][kRingThreads]
+    extern __shared__ float4 ring[];   // [2 stages][PLANES][kRingThreads]
     const int64_t nq = (n + 3) >> 2;
     const int64_t ldq = ld >> 2;
     const float4 *in = reinterpret_cast<const float4 *>(pts);
@@ -137,7 +136,7 @@ __global__ void __launch_bounds__(kRingThreads) solve_ring_kernel(const float *_
     // cp.async.wait_group is the only synchronisation needed
     auto fetch = [&](int64_t q, int stage) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) cp_async16(&ring[(stage * 16 + k) * kRingThreads + t], in + k * ldq + q);
+        for (int k = 0; k < PLANES; ++k) cp_async16(&ring[(stage * PLANES + k) * kRingThreads + t], in + k * ldq + q);
         cp_async_commit();
     };
     int64_t q = (int64_t)blockIdx.x * kRingThreads + t;
@@ -151,12 +150,38 @@ __global__ void __launch_bounds__(kRingThreads) solve_ring_kernel(const float *_
         } else {
             cp_async_wait<0>();
         }
-        float4 v[16];
+        float4 v[PLANES];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = ring[(stage * 16 + k) * kRingThreads + t];
-        solve_quad<SOLVER, NORM, FLAGS>(v, q, Hout, flags, n, ld);
+        for (int k = 0; k < PLANES; ++k) v[k] = ring[(stage * PLANES + k) * kRingThreads + t];
+        solve(v, q);
         stage ^= 1;
     }
+}
+
+// Launch of a ring kernel: opt in to its dynamic shared memory (a function
+// attribute of the current device, set on every call: well under a
+// microsecond against >= 8 us of work on this path), persistent grid.
+template <int PLANES, int BLOCKS_PER_SM = kRingBlocksPerSm, typename K, typename... Args>
+static aca_status launch_ring(K kernel, const char *name, int64_t n, cudaStream_t st, Args... args)
+{
+    const size_t smem = ring_smem<PLANES>();
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return set_error(ACA_ERR_CUDA, "%s: cannot reserve %zu bytes of shared memory", name, smem);
+    const int64_t need = ((n + 3) / 4 + kRingThreads - 1) / kRingThreads;
+    int64_t grid = (int64_t)sm_count() * BLOCKS_PER_SM;
+    if (grid > need) grid = need;
+    kernel<<<(int)grid, kRingThreads, smem, st>>>(args...);
+    return ACA_OK;
+}
+
+template <int SOLVER, int NORM, bool FLAGS>
+__global__ void __launch_bounds__(kRingThreads) solve_ring_kernel(const float *__restrict__ pts,
+                                                                  float *__restrict__ Hout,
+                                                                  uint8_t *__restrict__ flags, int64_t n, int64_t ld)
+{
+    ring_stream<16>(pts, n, ld, [&](const float4 (&v)[16], int64_t q) {
+        solve_quad<SOLVER, NORM, FLAGS>(v, q, Hout, flags, n, ld);
+    });
 }
 
 template <int SOLVER, int NORM, bool FLAGS>
@@ -186,22 +211,19 @@ static aca_status launch_solve(const float *pts, float *H, uint8_t *flags, int64
     const int threads = 256;
     const bool vec = n >= kSmallBatch && (ld % 4 == 0) && aligned16(pts) && aligned16(H) &&
                      (!FLAGS || (reinterpret_cast<uintptr_t>(flags) & 3u) == 0);
-    if (vec && SOLVER == kAca && !FLAGS) {
-        // the ACA solve (~365 instructions a set) sits at the HBM stream:
-        // prefetching pays (0.95 -> 0.99 of copy bandwidth).  SKS, and ACA
-        // with the degeneracy flags, are bound by their arithmetic and run
-        // faster on direct loads in 256-thread blocks (SKS 40.5 against 33.5,
-        // flags 55.1 against 54.3 G sets/s on the ring).
-        auto k = solve_ring_kernel<SOLVER, NORM, FLAGS>;
-        // a function attribute of the current device: set on every call (well
-        // under a microsecond, against >= 8 us of work on this path)
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem) != cudaSuccess)
-            return set_error(ACA_ERR_CUDA, "aca_solve: cannot reserve %zu bytes of shared memory", kRingSmem);
-        const int64_t nq = (n + 3) / 4;
-        int64_t grid = (int64_t)sm_count() * kRingBlocksPerSm;
-        const int64_t need = (nq + kRingThreads - 1) / kRingThreads;
-        if (grid > need) grid = need;
-        k<<<(int)grid, kRingThreads, kRingSmem, st>>>(pts, H, flags, n, ld);
+    // the ACA solve (~365 instructions a set) sits at the HBM stream:
+    // prefetching pays (0.95 -> 0.98 of copy bandwidth).  SKS, and ACA with
+    // the degeneracy flags, are bound by their arithmetic and run faster on
+    // direct loads in 256-thread blocks (SKS 40.5 against 33.5, flags 55.1
+    // against 54.3 G sets/s on the ring).
+    constexpr bool kRing = SOLVER == kAca && !FLAGS;
+    if (kRing && vec) {
+        if constexpr (kRing) {
+            const aca_status r = launch_ring<16>(solve_ring_kernel<SOLVER, NORM, FLAGS>, "aca_solve", n, st, pts, H,
+                                                 flags, n, ld);
+            if (r != ACA_OK)
+                return r;
+        }
     } else if (vec) {
         auto k = solve_vec4_kernel<SOLVER, NORM, FLAGS>;
         const int64_t nq = (n + 3) / 4;
@@ -310,43 +332,42 @@ __device__ __forceinline__ void affine_one(const Set3 &s, float H[9])
 }
 
 template <int NORM>
-__global__ void __launch_bounds__(256) affine_vec4_kernel(const float *__restrict__ pts, float *__restrict__ Hout,
-                                                           int64_t n, int64_t ld)
+__device__ __forceinline__ void affine_quad(const float4 (&v)[12], int64_t q, float *__restrict__ Hout, int64_t n,
+                                            int64_t ld)
 {
-    const int64_t nq = (n + 3) >> 2, ldq = ld >> 2;
-    const float4 *in = reinterpret_cast<const float4 *>(pts);
-    float4 *out = reinterpret_cast<float4 *>(Hout);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
-        float4 v[12];
+    float4 h[9];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Set3 s;
+        float *sv = &s.M1x;
 #pragma unroll
         for (int k = 0; k < 12; ++k)
-            v[k] = ld_stream(in + k * ldq + q);
-        float4 h[9];
+            sv[k] = (&v[k].x)[j];
+        float H[9];
+        affine_one<NORM>(s, H);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            Set3 s;
-            float *sv = &s.M1x;
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-                sv[k] = (&v[k].x)[j];
-            float H[9];
-            affine_one<NORM>(s, H);
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                (&h[k].x)[j] = H[k];
-        }
-        const int64_t i0 = q << 2;
-        if (i0 + 3 < n) {
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                st_stream(out + k * ldq + q, h[k]);
-        } else {
-            for (int j = 0; j < 4 && i0 + j < n; ++j)
-#pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    Hout[k * ld + i0 + j] = (&h[k].x)[j];
-        }
+        for (int k = 0; k < 9; ++k)
+            (&h[k].x)[j] = H[k];
     }
+    const int64_t i0 = q << 2;
+    if (i0 + 3 < n) {
+        float4 *out = reinterpret_cast<float4 *>(Hout);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            st_stream(out + k * (ld >> 2) + q, h[k]);
+    } else {
+        for (int j = 0; j < 4 && i0 + j < n; ++j)
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                Hout[k * ld + i0 + j] = (&h[k].x)[j];
+    }
+}
+
+template <int NORM>
+__global__ void __launch_bounds__(kRingThreads) affine_ring_kernel(const float *__restrict__ pts,
+                                                                   float *__restrict__ Hout, int64_t n, int64_t ld)
+{
+    ring_stream<12>(pts, n, ld, [&](const float4 (&v)[12], int64_t q) { affine_quad<NORM>(v, q, Hout, n, ld); });
 }
 
 template <int NORM>
@@ -372,9 +393,9 @@ static aca_status launch_affine(const float *pts, float *H, int64_t n, int64_t l
 {
     const int threads = 256;
     if (n >= kSmallBatch && ld % 4 == 0 && aligned16(pts) && aligned16(H)) {
-        auto k = affine_vec4_kernel<NORM>;
-        const int grid = resident_grid(k, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
-        k<<<grid, threads, 0, st>>>(pts, H, n, ld);
+        const aca_status r = launch_ring<12>(affine_ring_kernel<NORM>, "aca_affine_solve", n, st, pts, H, n, ld);
+        if (r != ACA_OK)
+            return r;
     } else {
         auto k = affine_scalar_kernel<NORM>;
         const int grid = resident_grid(k, threads, 0, (n + threads - 1) / threads);
