@@ -39,7 +39,13 @@
 //    K being the required number of hypotheses; a chunk starting at or after
 //    the bound is skipped: the sequential loop is certain to stop before it
 //    (the best over hypotheses 0..h0-1 is at least c, so K at h0 is at most
-//    K(c) <= h0);
+//    K(c) <= h0).  A dead chunk stays dead, so the block that draws one checks
+//    the next 31 problems of the round as well and moves the work counter
+//    past the whole run of dead ones in a single atomicMax;
+//  - the scoring runs in two epochs: chunk 0 of every problem, then a
+//    one-block re-plan that keeps, per problem, only the chunks before its
+//    current bound (a bound only decreases, so a stale one keeps a superset
+//    of the live chunks), then the scoring of those;
 //  - the finish kernel finds the sequential stop index from the prefix
 //    maxima of the counts (the stop condition i >= K(best of 0..i-1) is
 //    monotone in i) and takes the argmax before it.
@@ -219,7 +225,8 @@ struct AdaptiveWs {
     int64_t *round_off;    // [rb+1] first item of round r
     int32_t *round_cnt;    // [rb+1] problems in round r (those with C_p > r)
     int32_t *cursor;       // [rb+1] counting-sort cursors
-    int32_t *rounds;       // [1] number of rounds (max C_p)
+    int32_t *rounds;       // [1] rounds of the current epoch
+    int32_t *chunk_lo;     // [1] chunk index of round 0 of the current epoch
     int32_t *kbound;       // [P] the stop is certain before this hypothesis index
     int32_t *chunk_done;   // [cb] completed slices per chunk
     int32_t *prefix;       // [capacity] inclusive prefix maxima of the counts (finish)
@@ -273,6 +280,7 @@ static void carve_adaptive(void *base, int32_t P, int64_t total, Workspace &w, A
     a.cursor = reinterpret_cast<int32_t *>(b + o);
     o += align256(sizeof(int32_t) * (size_t)(a.rb + 1));
     a.rounds = reinterpret_cast<int32_t *>(b + o);
+    a.chunk_lo = a.rounds + 1;
     o += 256;
     a.kbound = reinterpret_cast<int32_t *>(b + o);
     o += align256(sizeof(int32_t) * (size_t)P);
@@ -374,75 +382,42 @@ __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__rest
     }
 }
 
-// Set-up of the adaptive variant (one block of 1024 threads): the standard
-// offsets, the chunk offsets, the bounds (initially the cap), and the round
-// order: problems sorted by C_p, largest first (counting sort; the order
-// among equal C_p follows the atomics and only affects speed), so that round
-// r, which holds the problems with C_p > r, is a prefix of that order.
-__global__ void __launch_bounds__(1024) ransac_prep_adaptive_kernel(const int64_t *__restrict__ offsets,
-                                                                    const int32_t *__restrict__ max_hyp, int32_t P,
-                                                                    int HB, int T, Workspace ws, AdaptiveWs aw)
+// Round lists of one epoch of the adaptive variant (all 1024 threads of the
+// block): the epoch scores chunks lo .. hi-1 of each problem, and of those
+// only the ones before the problem's current bound (chunk c is dead once
+// c * HB >= kbound, and kbound only decreases, so a bound read at any time
+// drops dead chunks only).  Problem p gets C'_p = min(C_p, ceil(kbound / HB),
+// hi) - lo live chunks (at least 0); the problems are sorted by C'_p, largest
+// first (counting sort; the order among equal C'_p follows the atomics and
+// only affects speed), so that round r, which holds chunk lo + r of every
+// problem with C'_p > r, is a prefix of that order.  Resets the work counter.
+__device__ void build_rounds(const int64_t *__restrict__ offsets, int32_t P, int HB, int T, int32_t lo, int32_t hi,
+                             Workspace ws, AdaptiveWs aw, int64_t *wt_a, int64_t *wt_b, int64_t &carry_a,
+                             int64_t &carry_b, int32_t &s_rounds)
 {
-    __shared__ int64_t wt_a[32], wt_b[32], wt_c[32];
-    __shared__ int64_t carry_a, carry_b, carry_c;
-    __shared__ int32_t s_rounds;
-    grid_launch_dependents();
-    if (threadIdx.x == 0) {
-        carry_a = carry_b = carry_c = 0;
-        s_rounds = 0;
-        ws.hyp_off[0] = 0;
-        ws.item_off[0] = 0;
-        aw.chunk_off[0] = 0;
-        *ws.counter = 0ull;
-        *ws.flags = 0;
+    auto live_chunks = [&](int32_t p) -> int32_t {
+        const int64_t C = aw.chunk_off[p + 1] - aw.chunk_off[p];
+        const int64_t kb = aw.kbound[p];
+        int64_t c = (kb + HB - 1) / HB;
+        c = c < C ? c : C;
+        c = c < hi ? c : hi;
+        return c > lo ? (int32_t)(c - lo) : 0;
+    };
+    if (threadIdx.x == 0) s_rounds = 0;
+    __syncthreads();
+    for (int32_t p = threadIdx.x; p < P; p += 1024) {
+        const int32_t c = live_chunks(p);
+        if (c > 0) atomicMax(&s_rounds, c);
     }
     __syncthreads();
-    for (int32_t base = 0; base < P; base += 1024) {
-        const int32_t p = base + (int32_t)threadIdx.x;
-        int64_t k = 0, items = 0, C = 0;
-        if (p < P) {
-            k = max_hyp[p] > 0 ? max_hyp[p] : 0;
-            const int64_t N = offsets[p + 1] - offsets[p];
-            if (N >= 4 && k > 0) {
-                C = (k + HB - 1) / HB;
-                items = C * ((N + T - 1) / T);
-            }
-            aw.kbound[p] = (int32_t)k;
-            if (C > 0) atomicMax(&s_rounds, (int32_t)(C < 0x7fffffff ? C : 0x7fffffff));
-        }
-        const int64_t ia = block_scan_incl(k, wt_a);
-        const int64_t ib = block_scan_incl(items, wt_b);
-        const int64_t ic = block_scan_incl(C, wt_c);
-        if (p < P) {
-            ws.hyp_off[p + 1] = carry_a + ia;
-            ws.item_off[p + 1] = carry_b + ib;
-            aw.chunk_off[p + 1] = carry_c + ic;
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) {
-            carry_a += ia;
-            carry_b += ib;
-            carry_c += ic;
-        }
-        __syncthreads();
-    }
     const int32_t R = s_rounds;
-    if (carry_a > ws.capacity || (int64_t)R > aw.rb || carry_c > aw.cb) {
-        if (threadIdx.x == 0) {
-            *ws.flags = 1;
-            ws.item_off[P] = 0;   // nothing to score
-            *aw.rounds = 0;
-        }
-        return;
-    }
-    if (threadIdx.x == 0) *aw.rounds = R;
-    // histogram of C_p over 0..R
+    // histogram of C'_p over 0..R
     for (int32_t c = threadIdx.x; c <= R; c += 1024) aw.round_cnt[c] = 0;
     __syncthreads();
     for (int32_t p = threadIdx.x; p < P; p += 1024)
-        atomicAdd(&aw.round_cnt[aw.chunk_off[p + 1] - aw.chunk_off[p]], 1);
+        atomicAdd(&aw.round_cnt[live_chunks(p)], 1);
     __syncthreads();
-    // descending exclusive prefix: #{p : C_p > c}; it is both the size of
+    // descending exclusive prefix: #{p : C'_p > c}; it is both the size of
     // round c and the first position of bin c in the order
     if (threadIdx.x == 0) carry_a = 0;
     __syncthreads();
@@ -461,15 +436,15 @@ __global__ void __launch_bounds__(1024) ransac_prep_adaptive_kernel(const int64_
         __syncthreads();
     }
     for (int32_t p = threadIdx.x; p < P; p += 1024) {
-        const int32_t C = (int32_t)(aw.chunk_off[p + 1] - aw.chunk_off[p]);
-        if (C > 0) aw.order[atomicAdd(&aw.cursor[C], 1)] = p;
+        const int32_t c = live_chunks(p);
+        if (c > 0) aw.order[atomicAdd(&aw.cursor[c], 1)] = p;
     }
     __syncthreads();
     // slice prefix over the order, then the round offsets
     const int32_t n1 = R > 0 ? aw.round_cnt[0] : 0;
     if (threadIdx.x == 0) {
+        carry_a = 0;
         carry_b = 0;
-        carry_c = 0;
         aw.spref[0] = 0;
         aw.round_off[0] = 0;
     }
@@ -481,21 +456,96 @@ __global__ void __launch_bounds__(1024) ransac_prep_adaptive_kernel(const int64_
             const int32_t p = aw.order[j];
             v = (offsets[p + 1] - offsets[p] + T - 1) / T;
         }
-        const int64_t incl = block_scan_incl(v, wt_b);
-        if (j < n1) aw.spref[j + 1] = carry_b + incl;
+        const int64_t incl = block_scan_incl(v, wt_a);
+        if (j < n1) aw.spref[j + 1] = carry_a + incl;
         __syncthreads();
-        if (threadIdx.x == 1023) carry_b += incl;
+        if (threadIdx.x == 1023) carry_a += incl;
         __syncthreads();
     }
     for (int32_t base = 0; base < R; base += 1024) {
         const int32_t r = base + (int32_t)threadIdx.x;
         const int64_t v = r < R ? aw.spref[aw.round_cnt[r]] : 0;
-        const int64_t incl = block_scan_incl(v, wt_c);
-        if (r < R) aw.round_off[r + 1] = carry_c + incl;
+        const int64_t incl = block_scan_incl(v, wt_b);
+        if (r < R) aw.round_off[r + 1] = carry_b + incl;
         __syncthreads();
-        if (threadIdx.x == 1023) carry_c += incl;
+        if (threadIdx.x == 1023) carry_b += incl;
         __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        *aw.rounds = R;
+        *aw.chunk_lo = lo;
+        *ws.counter = 0ull;
+    }
+}
+
+// Set-up of the adaptive variant (one block of 1024 threads): the hypothesis
+// and chunk offsets, the bounds (initially the cap) and the round lists of
+// the first epoch (chunks 0 .. hi-1).
+__global__ void __launch_bounds__(1024) ransac_prep_adaptive_kernel(const int64_t *__restrict__ offsets,
+                                                                    const int32_t *__restrict__ max_hyp, int32_t P,
+                                                                    int HB, int T, int32_t hi, Workspace ws,
+                                                                    AdaptiveWs aw)
+{
+    __shared__ int64_t wt_a[32], wt_b[32];
+    __shared__ int64_t carry_a, carry_b;
+    __shared__ int32_t s_rounds;
+    grid_launch_dependents();
+    if (threadIdx.x == 0) {
+        carry_a = carry_b = 0;
+        s_rounds = 0;
+        ws.hyp_off[0] = 0;
+        aw.chunk_off[0] = 0;
+        *ws.counter = 0ull;
+        *ws.flags = 0;
+        *aw.rounds = 0;
+        aw.round_off[0] = 0;
+    }
+    __syncthreads();
+    for (int32_t base = 0; base < P; base += 1024) {
+        const int32_t p = base + (int32_t)threadIdx.x;
+        int64_t k = 0, C = 0;
+        if (p < P) {
+            k = max_hyp[p] > 0 ? max_hyp[p] : 0;
+            const int64_t N = offsets[p + 1] - offsets[p];
+            if (N >= 4 && k > 0)
+                C = (k + HB - 1) / HB;
+            aw.kbound[p] = (int32_t)k;
+            if (C > 0) atomicMax(&s_rounds, (int32_t)(C < 0x7fffffff ? C : 0x7fffffff));
+        }
+        const int64_t ia = block_scan_incl(k, wt_a);
+        const int64_t ic = block_scan_incl(C, wt_b);
+        if (p < P) {
+            ws.hyp_off[p + 1] = carry_a + ia;
+            aw.chunk_off[p + 1] = carry_b + ic;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            carry_a += ia;
+            carry_b += ic;
+        }
+        __syncthreads();
+    }
+    if (carry_a > ws.capacity || (int64_t)s_rounds > aw.rb || carry_b > aw.cb) {
+        if (threadIdx.x == 0) *ws.flags = 1;    // nothing is scored (rounds stay 0)
+        return;
+    }
+    __syncthreads();
+    build_rounds(offsets, P, HB, T, 0, hi, ws, aw, wt_a, wt_b, carry_a, carry_b, s_rounds);
+}
+
+// Round lists of a later epoch (chunks lo .. hi-1), from the bounds the
+// previous epochs left.  Waits for the previous kernel.
+__global__ void __launch_bounds__(1024) ransac_replan_adaptive_kernel(const int64_t *__restrict__ offsets, int32_t P,
+                                                                      int HB, int T, int32_t lo, int32_t hi,
+                                                                      Workspace ws, AdaptiveWs aw)
+{
+    __shared__ int64_t wt_a[32], wt_b[32];
+    __shared__ int64_t carry_a, carry_b;
+    __shared__ int32_t s_rounds;
+    grid_launch_dependents();
+    grid_dependency_wait();
+    if (*ws.flags) return;
+    build_rounds(offsets, P, HB, T, lo, hi, ws, aw, wt_a, wt_b, carry_a, carry_b, s_rounds);
 }
 
 // Clears the counts and the chunk completion counters of the adaptive variant.
@@ -530,7 +580,6 @@ struct ItemInfo {
     int32_t i0, ni; // points of this item
     int32_t slice;
     // adaptive variant only
-    int32_t skip;   // the stop is certain before h0: nothing to score
     int32_t S;      // slices of problem p
     int32_t k;      // hypothesis cap of problem p
     int64_t cid;    // chunk id (completion counter)
@@ -576,24 +625,53 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
 
     grid_launch_dependents();
     grid_dependency_wait();
-    const int64_t total = ws.item_off[P];
+    // adaptive: the items of the current epoch, round 0 = chunk lo
     const int32_t R = ADAPTIVE ? *aw.rounds : 0;
+    const int32_t lo = ADAPTIVE ? *aw.chunk_lo : 0;
+    const int64_t total = ADAPTIVE ? aw.round_off[R] : ws.item_off[P];
     for (;;) {
         if (wid == 0) {
-            int64_t item = 0;
-            if (lane == 0)
-                item = (int64_t)atomicAdd(ws.counter, 1ull);
-            item = __shfl_sync(0xffffffffu, item, 0);
-            if (item < total) {
+            for (;;) {
+                int64_t item = 0;
+                if (lane == 0)
+                    item = (int64_t)atomicAdd(ws.counter, 1ull);
+                item = __shfl_sync(0xffffffffu, item, 0);
+                if (item >= total) {
+                    if (lane == 0)
+                        info.item = item;
+                    break;
+                }
                 int32_t p = 0, chunk = 0, slice = 0;
                 if constexpr (ADAPTIVE) {
-                    // round r = chunk r of every problem with more than r chunks
+                    // round r = chunk lo + r of every problem with more than
+                    // r live chunks in this epoch
                     const int32_t r = find_problem(aw.round_off, R, item);
-                    const int64_t rem = item - aw.round_off[r];
-                    const int32_t j = find_problem(aw.spref, aw.round_cnt[r], rem);
+                    const int64_t rbase = aw.round_off[r];
+                    const int64_t rem = item - rbase;
+                    const int32_t cnt = aw.round_cnt[r];
+                    const int32_t j = find_problem(aw.spref, cnt, rem);
                     p = aw.order[j];
-                    chunk = r;
+                    chunk = lo + r;
                     slice = (int32_t)(rem - aw.spref[j]);
+                    if (chunk > 0) {
+                        // The stop is certain before hypothesis kbound[q] of
+                        // problem q, and kbound only decreases: a chunk at or
+                        // past it stays dead.  The lanes check problem j and
+                        // the next 31 of this round; if j is dead, the work
+                        // counter jumps past the run of dead problems (their
+                        // items of round r are contiguous), so nobody claims
+                        // them one by one.  Items of the run already claimed
+                        // by other blocks are dropped by them in the same way.
+                        const int32_t jj = j + lane;
+                        const bool dead = jj < cnt && chunk * HB >= __ldcg(&aw.kbound[aw.order[jj]]);
+                        const unsigned live = __ballot_sync(0xffffffffu, !dead);
+                        if (!(live & 1u)) {
+                            const int32_t run = live ? __ffs(live) - 1 : 32;   // dead: j .. j + run - 1
+                            if (lane == 0)
+                                atomicMax(ws.counter, (unsigned long long)(rbase + aw.spref[j + run]));
+                            continue;
+                        }
+                    }
                 } else {
                     p = find_problem(ws.item_off, P, item);
                 }
@@ -617,16 +695,13 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
                     info.i0 = slice * T;
                     info.ni = (int32_t)min((int64_t)T, (int64_t)N - (int64_t)slice * T);
                     info.slice = slice;
-                    info.skip = 0;
                     if constexpr (ADAPTIVE) {
                         info.S = S;
                         info.k = k;
                         info.cid = aw.chunk_off[p] + chunk;
-                        info.skip = chunk > 0 && chunk * HB >= __ldcg(&aw.kbound[p]);
                     }
                 }
-            } else if (lane == 0) {
-                info.item = item;
+                break;
             }
         }
         __syncthreads();
@@ -638,12 +713,6 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
         const uint32_t N = info.N;
         const int64_t hbase = info.hbase;
         const float4 *cp = corr + info.base;
-        if constexpr (ADAPTIVE) {
-            if (info.skip) {
-                __syncthreads();        // all have read `info`
-                continue;
-            }
-        }
 
         // hypotheses of this item -> shared memory (test form, see inlier)
         if ((int)threadIdx.x < HB) {
@@ -1126,7 +1195,15 @@ extern "C" aca_status ransac_aca_adaptive(const float *corr, const int64_t *offs
     carve_adaptive(workspace, P, total_max_hyps, ws, aw);
     aw.log_fail = log(1.0 - confidence);
 
-    ransac_prep_adaptive_kernel<<<1, 1024, 0, st>>>(offsets, max_hyp, P, HB, T, ws, aw);
+    // Epochs: chunk 0 of every problem first, then the chunks still before
+    // each problem's bound, re-planned from the bounds the first epoch left.
+    // Measured on 512 pairs with a cap of 16384: claiming the dead chunks of
+    // the full-cap item space one by one cost 13 % of the batch; the re-plan
+    // boundary costs about 4 %; a first epoch of 1, 2, 3 or 4 chunks gave
+    // the same time within 1 %, and a third epoch was slower.
+    constexpr int32_t kEpochEnd[] = {1, 0x7fffffff};
+    constexpr int kEpochs = (int)(sizeof(kEpochEnd) / sizeof(kEpochEnd[0]));
+    ransac_prep_adaptive_kernel<<<1, 1024, 0, st>>>(offsets, max_hyp, P, HB, T, kEpochEnd[0], ws, aw);
     aca_status s = check_launch("ransac_aca_adaptive (prep)");
     if (s != ACA_OK) return s;
     {
@@ -1139,22 +1216,25 @@ extern "C" aca_status ransac_aca_adaptive(const float *corr, const int64_t *offs
     const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
     const int threads = 32 * W;
     const float4 *c4 = reinterpret_cast<const float4 *>(corr);
-#define ACA_SCORE_ADAPTIVE(HPTV)                                                                               \
-    {                                                                                                          \
-        auto k = ransac_score_kernel<HPTV, true>;                                                              \
-        if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                                                     (int)smem) != cudaSuccess)                                \
-            return set_error(ACA_ERR_CUDA, "ransac_aca_adaptive: cannot reserve %zu bytes of shared memory",  \
-                             smem);                                                                            \
-        const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
-        launch_after_previous(k, dim3(grid), dim3(threads), smem, st, c4, offsets, max_hyp, P,                 \
-                              params->threshold_px, params->seed, params->problem_base, T, ws, aw);           \
+    auto score = [&](auto kernel) -> aca_status {
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return set_error(ACA_ERR_CUDA, "ransac_aca_adaptive: cannot reserve %zu bytes of shared memory", smem);
+        const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(kernel, threads, smem, 1 << 30);
+        launch_after_previous(kernel, dim3(grid), dim3(threads), smem, st, c4, offsets, max_hyp, P,
+                              params->threshold_px, params->seed, params->problem_base, T, ws, aw);
+        return check_launch("ransac_aca_adaptive (score)");
+    };
+    for (int e = 0; e < kEpochs; ++e) {
+        if (e > 0) {
+            launch_after_previous(ransac_replan_adaptive_kernel, dim3(1), dim3(1024), 0, st, offsets, P, HB, T,
+                                  kEpochEnd[e - 1], kEpochEnd[e], ws, aw);
+            if ((s = check_launch("ransac_aca_adaptive (replan)")) != ACA_OK) return s;
+        }
+        s = HPT == 1 ? score(ransac_score_kernel<1, true>)
+                     : HPT == 2 ? score(ransac_score_kernel<2, true>) : score(ransac_score_kernel<4, true>);
+        if (s != ACA_OK) return s;
     }
-    if (HPT == 1) ACA_SCORE_ADAPTIVE(1)
-    else if (HPT == 2) ACA_SCORE_ADAPTIVE(2)
-    else ACA_SCORE_ADAPTIVE(4)
-#undef ACA_SCORE_ADAPTIVE
-    if ((s = check_launch("ransac_aca_adaptive (score)")) != ACA_OK) return s;
     launch_after_previous(ransac_finish_adaptive_kernel, dim3(P), dim3(512), 0, st, c4, offsets, max_hyp,
                           params->threshold_px, params->seed, params->problem_base, ws, aw, best_H, best_count,
                           best_hyp, n_evaluated, hyp_counts, inlier_mask);

@@ -76,12 +76,20 @@ def test_full_size_workload_sampled_against_oracle():
 
 
 @pytest.mark.parametrize("solver", ["aca", "sks"])
-def test_vector_and_scalar_paths_agree_bitwise(solver):
-    # large batches (>= 2^18 sets) with ld % 4 == 0 take the float4 path,
-    # small batches, odd ld and misaligned bases the one-set-per-thread path
-    n = (1 << 18) + 5
+@pytest.mark.parametrize("n", [(1 << 18) + 5, (1 << 20) + 7])
+def test_vector_and_scalar_paths_agree_bitwise(solver, n):
+    # large batches (>= 2^18 sets) with ld % 4 == 0 take the float4 paths
+    # (ACA without flags: the prefetching ring, several quads per thread at
+    # 2^20 + 7 sets; with flags and SKS: direct loads), small batches, odd ld
+    # and misaligned bases the one-set-per-thread path
     ms = workloads.minimal_sets(n, seed=6)
-    H4, f4 = _solve(ms.pts, n, n + 3, solver=solver, flags=True)      # float4 path, ragged tail
+    ldv = (n + 4) & ~3                   # a multiple of 4 above n: float4 path with padding
+    for norm in (0, 1, 2):
+        Hv, _ = _solve(ms.pts, n, ldv, norm=norm, solver=solver)
+        Hs1, _ = _solve(ms.pts, n, n, norm=norm, solver=solver)
+        assert torch.equal(Hv[:, :n], Hs1[:, :n]), norm
+        assert torch.all(Hv[:, n:] == 12345.0)
+    H4, f4 = _solve(ms.pts, n, ldv, solver=solver, flags=True)        # float4 path, ragged tail
     H1, f1 = _solve(ms.pts, n, n, solver=solver, flags=True)          # ld odd -> scalar path
     assert torch.equal(H4[:, :n], H1[:, :n])
     assert torch.equal(f4[:n], f1[:n])
@@ -220,6 +228,25 @@ def test_affine_three_point_solver_parity(n, ld):
         assert np.max(np.hypot(X - s[6 + 2 * k], Y - s[7 + 2 * k])) < 1e-2
 
 
+def test_affine_ring_and_scalar_paths_agree_bitwise():
+    # 2^20 + 7 sets: the prefetching ring (ld % 4 == 0, several quads per
+    # thread, ragged last quad) against the one-set-per-thread path (odd ld)
+    n = (1 << 20) + 7
+    p12 = _affine_planes(workloads.minimal_sets(n, seed=11))
+    out = []
+    for ld in ((n + 4) & ~3, n):
+        pts = torch.zeros((12, ld), dtype=torch.float32, device="cuda")
+        pts[:, :n] = cuda(p12)
+        for norm in (0, 1, 2):
+            H = torch.full((9, ld), 12345.0, dtype=torch.float32, device="cuda")
+            _lib.aca_affine_solve(pts, H, n=n, norm=norm)
+            out.append(H)
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert torch.equal(out[k][:, :n], out[3 + k][:, :n]), k
+        assert torch.all(out[k][:, n:] == 12345.0)
+
+
 @pytest.mark.parametrize("n", [1000, (1 << 18) + 5])
 def test_solve_on_pinned_host_buffers_matches_device_buffers(n):
     # zero-copy: the kernel reads the sets from and writes H and the flags to
@@ -235,6 +262,10 @@ def test_solve_on_pinned_host_buffers_matches_device_buffers(n):
     _lib.aca_solve(pts_h, H_h, f_h)
     torch.cuda.synchronize()
     assert torch.equal(H_h, H_d.cpu()) and torch.equal(f_h, f_d.cpu())
+    H_h2 = torch.full((9, n), 7.0).pin_memory()               # no flags: the prefetching ring at large n
+    _lib.aca_solve(pts_h, H_h2)
+    torch.cuda.synchronize()
+    assert torch.equal(H_h2, H_d.cpu())
     with pytest.raises(ValueError):
         _lib.aca_solve(torch.from_numpy(ms.pts), H_h)        # pageable host memory is refused
 
