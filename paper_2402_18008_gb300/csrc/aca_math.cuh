@@ -18,6 +18,9 @@
 // Unnormalised output (ACA_NORM_NONE) is the paper's division-free H of
 // Eq. 24 with the scale of Eq. 28-29, the function the backward kernels
 // differentiate.
+// The ACA and SKS solves are written over a value type (fp32.cuh): float for
+// one set, or packed pairs for two sets per instruction, with the same bits
+// per lane.
 #pragma once
 #include <stdint.h>
 
@@ -25,10 +28,13 @@
 
 namespace aca {
 
-struct Set {
-    float M1x, M1y, N1x, N1y, P1x, P1y, Q1x, Q1y;
-    float M2x, M2y, N2x, N2y, P2x, P2y, Q2x, Q2y;
+// One set (V = float) or two sets side by side (V = P2, see fp32.cuh).
+template <class V>
+struct SetT {
+    V M1x, M1y, N1x, N1y, P1x, P1y, Q1x, Q1y;
+    V M2x, M2y, N2x, N2y, P2x, P2y, Q2x, Q2y;
 };
+using Set = SetT<float>;
 
 // Per-set flag bits (see include/aca.h).
 enum : uint8_t {
@@ -39,19 +45,23 @@ enum : uint8_t {
 };
 
 // Intermediates of the ACA chain kept for the flags and the backward pass.
-struct AcaParts {
-    float MN1x, MN1y, MP1x, MP1y, NP1x, NP1y;
-    float MN2x, MN2y, MP2x, MP2y, MQ2x, MQ2y, NP2x, NP2y, NQ2x, NQ2y;
-    float fA1, fA2, Q3x, Q3y, Q4x, Q4y, t1, t2;
-    float MQ1x, MQ1y, NQ1x, NQ1y;
+template <class V>
+struct AcaPartsT {
+    V MN1x, MN1y, MP1x, MP1y, NP1x, NP1y;
+    V MN2x, MN2y, MP2x, MP2y, MQ2x, MQ2y, NP2x, NP2y, NQ2x, NQ2y;
+    V fA1, fA2, Q3x, Q3y, Q4x, Q4y, t1, t2;
+    V MQ1x, MQ1y, NQ1x, NQ1y;
 };
+using AcaParts = AcaPartsT<float>;
 
 // Eq. 20-27 (vectors, f_A, Q3, Q4, t1, t2) for one set.  Edge vectors are
 // exact differences (value + remainder) and every cross product takes the
 // remainders into account (cross2x), so f_A, Q3, Q4, t1, t2 are accurate to
 // about one rounding of their exact values for the given inputs.
-ACA_HD void aca_parts(const Set &s, AcaParts &p)
+template <class V>
+ACA_HD void aca_parts(const SetT<V> &s, AcaPartsT<V> &p)
 {
+    using Diff = DiffT<V>;
     const Diff mn1x = diff(s.N1x, s.M1x), mn1y = diff(s.N1y, s.M1y);
     const Diff mp1x = diff(s.P1x, s.M1x), mp1y = diff(s.P1y, s.M1y);
     const Diff mq1x = diff(s.Q1x, s.M1x), mq1y = diff(s.Q1y, s.M1y);
@@ -81,6 +91,9 @@ ACA_HD void aca_parts(const Set &s, AcaParts &p)
 ACA_HD float fmax3_(float a, float b, float c);
 ACA_HD float pow2_inv_scale(float x);
 
+// Power-of-two factor bringing the largest of |a|, |b|, |c| into [1, 2).
+ACA_HD float prescale_factor(float a, float b, float c) { return pow2_inv_scale(fmax3_(a, b, c)); }
+
 // Core (Eq. 29) and composition (Eq. 24) from the parts, H row-major.
 // The core c11, c22, c33 and the products of the local-frame homography
 //   L = H_A2^-1(M2 frame) * H_C * H_A1(M1 frame)
@@ -97,35 +110,37 @@ ACA_HD float pow2_inv_scale(float x);
 // a power of two (exact) so that the largest has magnitude in [1, 2): H
 // changes by that exact factor only, and normalised outputs stay clear of
 // overflow.
-ACA_HD void aca_compose(const Set &s, const AcaParts &p, bool prescale, float H[9])
+template <class V>
+ACA_HD void aca_compose(const SetT<V> &s, const AcaPartsT<V> &p, bool prescale, V H[9])
 {
+    using DF = DFT<V>;
     DF c11 = df_mul(df_prod(p.t1, p.Q3y), p.Q4x);
     DF c22 = df_mul(df_prod(p.t1, p.Q3x), p.Q4y);
     DF c33 = df_mul(df_prod(p.t2, p.Q3x), p.Q3y);
     if (prescale) {
-        const float sc = pow2_inv_scale(fmax3_(c11.h, c22.h, c33.h));
-        c11 = DF{F_MUL(c11.h, sc), F_MUL(c11.l, sc)};
-        c22 = DF{F_MUL(c22.h, sc), F_MUL(c22.l, sc)};
-        c33 = DF{F_MUL(c33.h, sc), F_MUL(c33.l, sc)};
+        const V sc = prescale_factor(c11.h, c22.h, c33.h);
+        c11 = DF{vmul(c11.h, sc), vmul(c11.l, sc)};
+        c22 = DF{vmul(c22.h, sc), vmul(c22.l, sc)};
+        c33 = DF{vmul(c33.h, sc), vmul(c33.l, sc)};
     }
     const DF k0x = df_mul(c11, p.MN2x), k0y = df_mul(c11, p.MN2y);
     const DF k1x = df_mul(c22, p.MP2x), k1y = df_mul(c22, p.MP2y);
-    const float L00 = df_round(df_sub(df_mul(k0x, p.MP1y), df_mul(k1x, p.MN1y)));
-    const float L01 = df_round(df_sub(df_mul(k1x, p.MN1x), df_mul(k0x, p.MP1x)));
-    const float L10 = df_round(df_sub(df_mul(k0y, p.MP1y), df_mul(k1y, p.MN1y)));
-    const float L11 = df_round(df_sub(df_mul(k1y, p.MN1x), df_mul(k0y, p.MP1x)));
-    const float L20 = df_round(df_sub(df_sub(df_mul(c11, p.MP1y), df_mul(c22, p.MN1y)), df_mul(c33, p.NP1y)));
-    const float L21 = df_round(df_add(df_sub(df_mul(c22, p.MN1x), df_mul(c11, p.MP1x)), df_mul(c33, p.NP1x)));
-    const float L22 = df_round(df_mul(c33, p.fA1));
-    const float G02 = -F_FMA(s.M1x, L00, F_MUL(s.M1y, L01));
-    const float G12 = -F_FMA(s.M1x, L10, F_MUL(s.M1y, L11));
-    const float G22 = F_FMA(-s.M1x, L20, F_FMA(-s.M1y, L21, L22));
-    H[0] = F_FMA(s.M2x, L20, L00);
-    H[1] = F_FMA(s.M2x, L21, L01);
-    H[2] = F_FMA(s.M2x, G22, G02);
-    H[3] = F_FMA(s.M2y, L20, L10);
-    H[4] = F_FMA(s.M2y, L21, L11);
-    H[5] = F_FMA(s.M2y, G22, G12);
+    const V L00 = df_round(df_sub(df_mul(k0x, p.MP1y), df_mul(k1x, p.MN1y)));
+    const V L01 = df_round(df_sub(df_mul(k1x, p.MN1x), df_mul(k0x, p.MP1x)));
+    const V L10 = df_round(df_sub(df_mul(k0y, p.MP1y), df_mul(k1y, p.MN1y)));
+    const V L11 = df_round(df_sub(df_mul(k1y, p.MN1x), df_mul(k0y, p.MP1x)));
+    const V L20 = df_round(df_sub(df_sub(df_mul(c11, p.MP1y), df_mul(c22, p.MN1y)), df_mul(c33, p.NP1y)));
+    const V L21 = df_round(df_add(df_sub(df_mul(c22, p.MN1x), df_mul(c11, p.MP1x)), df_mul(c33, p.NP1x)));
+    const V L22 = df_round(df_mul(c33, p.fA1));
+    const V G02 = vneg(vfma(s.M1x, L00, vmul(s.M1y, L01)));
+    const V G12 = vneg(vfma(s.M1x, L10, vmul(s.M1y, L11)));
+    const V G22 = vfma(vneg(s.M1x), L20, vfma(vneg(s.M1y), L21, L22));
+    H[0] = vfma(s.M2x, L20, L00);
+    H[1] = vfma(s.M2x, L21, L01);
+    H[2] = vfma(s.M2x, G22, G02);
+    H[3] = vfma(s.M2y, L20, L10);
+    H[4] = vfma(s.M2y, L21, L11);
+    H[5] = vfma(s.M2y, G22, G12);
     H[6] = L20;
     H[7] = L21;
     H[8] = G22;
@@ -269,21 +284,23 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 // Differences are exact (TwoSum) and dot / cross products of them carry
 // their remainders.
 // ---------------------------------------------------------------------------
+template <class V>
 struct SksSide {
-    Diff onx, ony;           // ON = M N / 2
-    float fS;                // |ON|^2
-    float P3x, P3y, Q3x, Q3y;
-    float cQP;               // ON x Q P (= P3.y - Q3.y)
+    DiffT<V> onx, ony;       // ON = M N / 2
+    V fS;                    // |ON|^2
+    V P3x, P3y, Q3x, Q3y;
+    V cQP;                   // ON x Q P (= P3.y - Q3.y)
 };
 
-ACA_HD void sks_side(float Mx, float My, float Nx, float Ny, float Px, float Py, float Qx, float Qy, SksSide &o)
+template <class V>
+ACA_HD void sks_side(V Mx, V My, V Nx, V Ny, V Px, V Py, V Qx, V Qy, SksSide<V> &o)
 {
     o.onx = half(diff(Nx, Mx));
     o.ony = half(diff(Ny, My));
-    const Diff mpx = diff(Px, Mx), mpy = diff(Py, My);
-    const Diff mqx = diff(Qx, Mx), mqy = diff(Qy, My);
-    const Diff qpx = diff(Px, Qx), qpy = diff(Py, Qy);
-    const DF fS = dot2x_df(o.onx, o.ony, o.onx, o.ony);
+    const DiffT<V> mpx = diff(Px, Mx), mpy = diff(Py, My);
+    const DiffT<V> mqx = diff(Qx, Mx), mqy = diff(Qy, My);
+    const DiffT<V> qpx = diff(Px, Qx), qpy = diff(Py, Qy);
+    const DFT<V> fS = dot2x_df(o.onx, o.ony, o.onx, o.ony);
     o.fS = df_round(fS);
     o.P3y = cross2x(o.onx, o.ony, mpx, mpy);
     o.Q3y = cross2x(o.onx, o.ony, mqx, mqy);
@@ -292,27 +309,29 @@ ACA_HD void sks_side(float Mx, float My, float Nx, float Ny, float Px, float Py,
     o.cQP = cross2x(o.onx, o.ony, qpx, qpy);
 }
 
-ACA_HD void sks_solve(const Set &s, float H[9])
+template <class V>
+ACA_HD void sks_solve(const SetT<V> &s, V H[9])
 {
-    SksSide a, b;
+    using DF = DFT<V>;
+    SksSide<V> a, b;
     sks_side(s.M1x, s.M1y, s.N1x, s.N1y, s.P1x, s.P1y, s.Q1x, s.Q1y, a);
     sks_side(s.M2x, s.M2y, s.N2x, s.N2y, s.P2x, s.P2y, s.Q2x, s.Q2y, b);
     // Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11)
-    const float n7x = det2(a.Q3x, a.P3x, a.Q3y, a.P3y), n7y = F_MUL(a.fS, a.cQP), d7 = F_MUL(a.Q3y, a.P3y);
-    const float n8x = det2(b.Q3x, b.P3x, b.Q3y, b.P3y), n8y = F_MUL(b.fS, b.cQP), d8 = F_MUL(b.Q3y, b.P3y);
+    const V n7x = det2(a.Q3x, a.P3x, a.Q3y, a.P3y), n7y = vmul(a.fS, a.cQP), d7 = vmul(a.Q3y, a.P3y);
+    const V n8x = det2(b.Q3x, b.P3x, b.Q3y, b.P3y), n8y = vmul(b.fS, b.cQP), d8 = vmul(b.Q3y, b.P3y);
     // Eq. 11 solved for a_K = a_G, b_K = b_G
-    const float den = F_MUL(d8, F_MUL(F_SUB(n7x, n7y), F_ADD(n7x, n7y)));
-    const float aK = F_DIV(F_MUL(d7, det2(n8x, n8y, n7y, n7x)), den);
-    const float bK = F_DIV(F_MUL(d7, det2(n8y, n8x, n7y, n7x)), den);
+    const V den = vmul(d8, vmul(vsub(n7x, n7y), vadd(n7x, n7y)));
+    const V aK = vdiv(vmul(d7, det2(n8x, n8y, n7y, n7x)), den);
+    const V bK = vdiv(vmul(d7, det2(n8y, n8x, n7y, n7x)), den);
     // Eq. 13 with P5 = (P3.x, f_S1) / P3.y, P6 = (P4.x, f_S2) / P4.y
-    const float P5x = F_DIV(a.P3x, a.P3y), P5y = F_DIV(a.fS, a.P3y);
-    const float P6x = F_DIV(b.P3x, b.P3y), P6y = F_DIV(b.fS, b.P3y);
-    const float uK = F_SUB(P6x, F_FMA(aK, P5x, F_MUL(bK, P5y)));
-    const float vK = F_SUB(P6y, F_FMA(bK, P5x, F_MUL(aK, P5y)));
+    const V P5x = vdiv(a.P3x, a.P3y), P5y = vdiv(a.fS, a.P3y);
+    const V P6x = vdiv(b.P3x, b.P3y), P6y = vdiv(b.fS, b.P3y);
+    const V uK = vsub(P6x, vfma(aK, P5x, vmul(bK, P5y)));
+    const V vK = vsub(P6y, vfma(bK, P5x, vmul(aK, P5y)));
     // Eq. 14 in the M frames: H = T(M2) L T(-M1) with
     // L = T(ON2) R2^-1 K R1 T(-ON1), R1 = [[ONx, ONy, 0], [-ONy, ONx, 0], [0, 0, fS1]],
     // R2^-1 = [[ONx, -ONy, 0], [ONy, ONx, 0], [0, 0, 1]], K = [[aK, uK, bK], [0, 1, 0], [bK, vK, aK]].
-    const float o1x = a.onx.h, o1y = a.ony.h, o2x = b.onx.h, o2y = b.ony.h;
+    const V o1x = a.onx.h, o1y = a.ony.h, o2x = b.onx.h, o2y = b.ony.h;
     // K R1 (rows), in double-float
     const DF A00 = df_sub(df_prod(aK, o1x), df_prod(uK, o1y));
     const DF A01 = df_add(df_prod(aK, o1y), df_prod(uK, o1x));
@@ -338,18 +357,19 @@ ACA_HD void sks_solve(const Set &s, float H[9])
     const DF J12 = df_add(G12, df_mul(G22, o2y));
     // J is the homography in the M frames, rounded once per entry; then
     // H = T(M2) J T(-M1) in FP32, as for ACA
-    const float j00 = df_round(J00), j01 = df_round(J01), j02 = df_round(J02);
-    const float j10 = df_round(J10), j11 = df_round(J11), j12 = df_round(J12);
-    const float j20 = df_round(A20), j21 = df_round(A21), j22 = df_round(G22);
-    const float K02 = F_FMA(-s.M1x, j00, F_FMA(-s.M1y, j01, j02));
-    const float K12 = F_FMA(-s.M1x, j10, F_FMA(-s.M1y, j11, j12));
-    const float K22 = F_FMA(-s.M1x, j20, F_FMA(-s.M1y, j21, j22));
-    H[0] = F_FMA(s.M2x, j20, j00);
-    H[1] = F_FMA(s.M2x, j21, j01);
-    H[2] = F_FMA(s.M2x, K22, K02);
-    H[3] = F_FMA(s.M2y, j20, j10);
-    H[4] = F_FMA(s.M2y, j21, j11);
-    H[5] = F_FMA(s.M2y, K22, K12);
+    const V j00 = df_round(J00), j01 = df_round(J01), j02 = df_round(J02);
+    const V j10 = df_round(J10), j11 = df_round(J11), j12 = df_round(J12);
+    const V j20 = df_round(A20), j21 = df_round(A21), j22 = df_round(G22);
+    const V nM1x = vneg(s.M1x), nM1y = vneg(s.M1y);
+    const V K02 = vfma(nM1x, j00, vfma(nM1y, j01, j02));
+    const V K12 = vfma(nM1x, j10, vfma(nM1y, j11, j12));
+    const V K22 = vfma(nM1x, j20, vfma(nM1y, j21, j22));
+    H[0] = vfma(s.M2x, j20, j00);
+    H[1] = vfma(s.M2x, j21, j01);
+    H[2] = vfma(s.M2x, K22, K02);
+    H[3] = vfma(s.M2y, j20, j10);
+    H[4] = vfma(s.M2y, j21, j11);
+    H[5] = vfma(s.M2y, K22, K12);
     H[6] = j20;
     H[7] = j21;
     H[8] = K22;

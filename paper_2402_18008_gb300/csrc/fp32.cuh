@@ -35,37 +35,123 @@
 
 namespace aca {
 
+// ---------------------------------------------------------------------------
+// Value types.  The arithmetic below is written once over a value type V:
+//  * float: one FP32 value, the explicitly rounded operations above;
+//  * P2 (device code only): two FP32 values in one 64-bit register, operated
+//    on by the packed f32x2 instructions of sm_100 and later.  Each lane of
+//    a packed add, sub, mul or fma is rounded to nearest even exactly like
+//    the scalar instruction, so a function evaluated on pairs gives, lane by
+//    lane, the bits it gives on floats, with half the instructions issued.
+// Negation goes through vneg so that both types share one formula (on float
+// it is the sign flip the compiler folds into the consuming instruction).
+// ---------------------------------------------------------------------------
+ACA_HD float vmul(float a, float b) { return F_MUL(a, b); }
+ACA_HD float vadd(float a, float b) { return F_ADD(a, b); }
+ACA_HD float vsub(float a, float b) { return F_SUB(a, b); }
+ACA_HD float vfma(float a, float b, float c) { return F_FMA(a, b, c); }
+ACA_HD float vdiv(float a, float b) { return F_DIV(a, b); }
+ACA_HD float vneg(float a) { return -a; }
+
+// the constant x in the value type of `like`
+ACA_HD float vconst(float /*like*/, float x) { return x; }
+
+#if defined(__CUDACC__)
+struct P2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ P2 vpack(float a, float b)
+{
+    P2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void vunpack(P2 x, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ float vlo(P2 x)
+{
+    float a, b;
+    vunpack(x, a, b);
+    return a;
+}
+__device__ __forceinline__ float vhi(P2 x)
+{
+    float a, b;
+    vunpack(x, a, b);
+    return b;
+}
+__device__ __forceinline__ P2 vmul(P2 a, P2 b)
+{
+    P2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ P2 vadd(P2 a, P2 b)
+{
+    P2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ P2 vsub(P2 a, P2 b)
+{
+    P2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ P2 vfma(P2 a, P2 b, P2 c)
+{
+    P2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+// no packed divide: two correctly rounded scalar divisions
+__device__ __forceinline__ P2 vdiv(P2 a, P2 b)
+{
+    return vpack(F_DIV(vlo(a), vlo(b)), F_DIV(vhi(a), vhi(b)));
+}
+__device__ __forceinline__ P2 vneg(P2 a) { return P2{a.v ^ 0x8000000080000000ull}; }
+__device__ __forceinline__ P2 vconst(P2 /*like*/, float x) { return vpack(x, x); }
+#endif
+
 // a*d - b*c with Kahan's FMA algorithm (error analysis: Jeannerod, Louvet and
 // Muller, "Further analysis of Kahan's algorithm for the accurate computation
 // of 2x2 determinants", Math. Comp. 2013): w = b*c rounded, e = w - b*c
 // exactly, result = (a*d - w) + e, within 2 ulp of the exact value even
 // under cancellation.
-ACA_HD float det2(float a, float b, float c, float d)
+template <class V>
+ACA_HD V det2(V a, V b, V c, V d)
 {
-    const float w = F_MUL(b, c);
-    const float e = F_FMA(-b, c, w);
-    const float f = F_FMA(a, d, -w);
-    return F_ADD(f, e);
+    const V w = vmul(b, c);
+    const V e = vfma(vneg(b), c, w);
+    const V f = vfma(a, d, vneg(w));
+    return vadd(f, e);
 }
 
 // u.x*v.y - u.y*v.x
-ACA_HD float cross2(float ux, float uy, float vx, float vy)
+template <class V>
+ACA_HD V cross2(V ux, V uy, V vx, V vy)
 {
     return det2(ux, uy, vx, vy);
 }
 
 // Exact difference: a - b = d + e exactly (Knuth's TwoSum on a and -b).
-struct Diff {
-    float h, l;
+template <class V>
+struct DiffT {
+    V h, l;
 };
+using Diff = DiffT<float>;
 
-ACA_HD Diff diff(float a, float b)
+template <class V>
+ACA_HD DiffT<V> diff(V a, V b)
 {
-    const float d = F_SUB(a, b);
-    const float bv = F_SUB(d, a);       // the part of d that came from -b
-    const float av = F_SUB(d, bv);      // the part of d that came from a
-    const float er = F_ADD(F_SUB(a, av), F_SUB(-b, bv));
-    return Diff{d, er};
+    const V d = vsub(a, b);
+    const V bv = vsub(d, a);       // the part of d that came from -b
+    const V av = vsub(d, bv);      // the part of d that came from a
+    const V er = vadd(vsub(a, av), vsub(vneg(b), bv));
+    return DiffT<V>{d, er};
 }
 
 // cross(u, v) of two exact differences u = uh + ul, v = vh + vl: Kahan's
@@ -73,61 +159,77 @@ ACA_HD Diff diff(float a, float b)
 // (the dropped ul*vl terms are ~u^2 relative).  Close to the correctly
 // rounded cross product of the exact input differences, so a near-collinear
 // triple loses no accuracy to the rounding of its edge vectors.
-ACA_HD float cross2x(Diff ux, Diff uy, Diff vx, Diff vy)
+template <class V>
+ACA_HD V cross2x(DiffT<V> ux, DiffT<V> uy, DiffT<V> vx, DiffT<V> vy)
 {
-    const float w = F_MUL(uy.h, vx.h);
-    const float e = F_FMA(-uy.h, vx.h, w);
-    const float f = F_FMA(ux.h, vy.h, -w);
-    const float c = F_FMA(ux.h, vy.l, F_FMA(ux.l, vy.h, F_FMA(-uy.h, vx.l, F_MUL(-uy.l, vx.h))));
-    return F_ADD(f, F_ADD(e, c));
+    const V nuyh = vneg(uy.h);
+    const V w = vmul(uy.h, vx.h);
+    const V e = vfma(nuyh, vx.h, w);
+    const V f = vfma(ux.h, vy.h, vneg(w));
+    const V c = vfma(ux.h, vy.l, vfma(ux.l, vy.h, vfma(nuyh, vx.l, vmul(vneg(uy.l), vx.h))));
+    return vadd(f, vadd(e, c));
 }
 
 // Double-float arithmetic (value = h + l, |l| <= ulp(h) roughly): products
 // by TwoProduct (one FMA recovers the rounding error exactly), sums by
 // TwoSum; the low parts are accumulated without renormalisation, which keeps
 // ~45 significant bits through the short chains used here.
-struct DF {
-    float h, l;
+template <class V>
+struct DFT {
+    V h, l;
 };
+using DF = DFT<float>;
 
-ACA_HD DF df_prod(float a, float b)
+template <class V>
+ACA_HD DFT<V> df_prod(V a, V b)
 {
-    const float p = F_MUL(a, b);
-    return DF{p, F_FMA(a, b, -p)};
+    const V p = vmul(a, b);
+    return DFT<V>{p, vfma(a, b, vneg(p))};
 }
 
 // (x.h + x.l) * b
-ACA_HD DF df_mul(DF x, float b)
+template <class V>
+ACA_HD DFT<V> df_mul(DFT<V> x, V b)
 {
-    const float p = F_MUL(x.h, b);
-    return DF{p, F_FMA(x.l, b, F_FMA(x.h, b, -p))};
+    const V p = vmul(x.h, b);
+    return DFT<V>{p, vfma(x.l, b, vfma(x.h, b, vneg(p)))};
 }
 
-ACA_HD DF df_add(DF x, DF y)
+template <class V>
+ACA_HD DFT<V> df_add(DFT<V> x, DFT<V> y)
 {
-    const float s = F_ADD(x.h, y.h);
-    const float bv = F_SUB(s, x.h);
-    const float av = F_SUB(s, bv);
-    const float e = F_ADD(F_SUB(x.h, av), F_SUB(y.h, bv));
-    return DF{s, F_ADD(e, F_ADD(x.l, y.l))};
+    const V s = vadd(x.h, y.h);
+    const V bv = vsub(s, x.h);
+    const V av = vsub(s, bv);
+    const V e = vadd(vsub(x.h, av), vsub(y.h, bv));
+    return DFT<V>{s, vadd(e, vadd(x.l, y.l))};
 }
 
-ACA_HD DF df_neg(DF x) { return DF{-x.h, -x.l}; }
+template <class V>
+ACA_HD DFT<V> df_neg(DFT<V> x) { return DFT<V>{vneg(x.h), vneg(x.l)}; }
 
-ACA_HD DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
+template <class V>
+ACA_HD DFT<V> df_sub(DFT<V> x, DFT<V> y) { return df_add(x, df_neg(y)); }
 
-ACA_HD float df_round(DF x) { return F_ADD(x.h, x.l); }
+template <class V>
+ACA_HD V df_round(DFT<V> x) { return vadd(x.h, x.l); }
 
 // u . v of two exact differences (value + remainder), as a double-float:
 // exact products of the leading parts plus first-order remainder terms.
-ACA_HD DF dot2x_df(Diff ux, Diff uy, Diff vx, Diff vy)
+template <class V>
+ACA_HD DFT<V> dot2x_df(DiffT<V> ux, DiffT<V> uy, DiffT<V> vx, DiffT<V> vy)
 {
-    const DF a = df_prod(ux.h, vx.h), b = df_prod(uy.h, vy.h);
-    const DF s = df_add(a, b);
-    const float c = F_FMA(ux.h, vx.l, F_FMA(ux.l, vx.h, F_FMA(uy.h, vy.l, F_MUL(uy.l, vy.h))));
-    return DF{s.h, F_ADD(s.l, c)};
+    const DFT<V> a = df_prod(ux.h, vx.h), b = df_prod(uy.h, vy.h);
+    const DFT<V> s = df_add(a, b);
+    const V c = vfma(ux.h, vx.l, vfma(ux.l, vx.h, vfma(uy.h, vy.l, vmul(uy.l, vy.h))));
+    return DFT<V>{s.h, vadd(s.l, c)};
 }
 
-ACA_HD Diff half(Diff d) { return Diff{F_MUL(0.5f, d.h), F_MUL(0.5f, d.l)}; }
+template <class V>
+ACA_HD DiffT<V> half(DiffT<V> d)
+{
+    const V k = vconst(d.h, 0.5f);
+    return DiffT<V>{vmul(k, d.h), vmul(k, d.l)};
+}
 
 }  // namespace aca

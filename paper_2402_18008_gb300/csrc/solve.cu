@@ -10,7 +10,7 @@
 // two-stage shared-memory ring (cp.async) while it solves the current one, so
 // the loads of the next step are in flight during the arithmetic (the plain
 // ACA path; SKS and the flagged solve, bound by their arithmetic, load
-// directly).  When the layout does
+// directly, and SKS runs two sets per packed f32x2 instruction).  When the layout does
 // not allow 16-byte accesses a scalar variant (one set per thread, coalesced
 // 4-byte accesses) runs instead.
 #include "aca_math.cuh"
@@ -42,29 +42,73 @@ __device__ __forceinline__ void solve_one(const Set &s, float H[9], uint8_t &fla
     }
 }
 
-// Four adjacent sets (one float4 from each input plane) solved one after
-// another; nine float4 planes stored with streaming stores, element-wise on
-// the last, partial quad.
+// SKS on two sets at once, as packed pairs (fp32.cuh); the optional
+// normalisation, which compares and divides, finishes per lane in scalar
+// code, as in solve_one.
+template <int NORM>
+__device__ __forceinline__ void sks_solve_two(const SetT<P2> &s, P2 H[9])
+{
+    sks_solve(s, H);
+    if (NORM != ACA_NORM_NONE) {
+#pragma unroll
+        for (int lane = 0; lane < 2; ++lane) {
+            float h[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) h[k] = lane ? vhi(H[k]) : vlo(H[k]);
+            if (NORM == ACA_NORM_H33) normalize_h33(h);
+            if (NORM == ACA_NORM_FROB) normalize_frob(h);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) H[k] = lane ? vpack(vlo(H[k]), h[k]) : vpack(h[k], vhi(H[k]));
+        }
+    }
+}
+
+// Four adjacent sets (one float4 from each input plane); nine float4 planes
+// stored with streaming stores, element-wise on the last, partial quad.
+// SKS without flags solves them as two packed pairs (sets 0-1 from the .x/.y
+// lanes, sets 2-3 from .z/.w): 43.0 against 40.5 G sets/s one by one.  The
+// ACA solve sits at the HBM stream either way (packed it measured 1 % lower),
+// and the flagged solves lose more to the per-lane finish and to 210-240
+// registers than packing saves (44.7 against 55.1 G sets/s), so they take
+// the sets one by one.  Both forms give the same bits (fp32.cuh).
 template <int SOLVER, int NORM, bool FLAGS>
 __device__ __forceinline__ void solve_quad(const float4 (&v)[16], int64_t q, float *__restrict__ Hout,
                                            uint8_t *__restrict__ flags, int64_t n, int64_t ld)
 {
     float4 h[9];
     uint32_t fl = 0;
+    if constexpr (SOLVER == kSks && !FLAGS) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        Set s;
-        float *sv = &s.M1x;
+        for (int jp = 0; jp < 2; ++jp) {
+            SetT<P2> s;
+            P2 *sv = &s.M1x;
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            sv[k] = (&v[k].x)[j];
-        float H[9];
-        uint8_t f = 0;
-        solve_one<SOLVER, NORM, FLAGS>(s, H, f);
+            for (int k = 0; k < 16; ++k)
+                sv[k] = jp ? vpack(v[k].z, v[k].w) : vpack(v[k].x, v[k].y);
+            P2 H[9];
+            sks_solve_two<NORM>(s, H);
 #pragma unroll
-        for (int k = 0; k < 9; ++k)
-            (&h[k].x)[j] = H[k];
-        fl |= (uint32_t)f << (8 * j);
+            for (int k = 0; k < 9; ++k) {
+                if (jp) vunpack(H[k], h[k].z, h[k].w);
+                else vunpack(H[k], h[k].x, h[k].y);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Set s;
+            float *sv = &s.M1x;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                sv[k] = (&v[k].x)[j];
+            float H[9];
+            uint8_t f = 0;
+            solve_one<SOLVER, NORM, FLAGS>(s, H, f);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                (&h[k].x)[j] = H[k];
+            fl |= (uint32_t)f << (8 * j);
+        }
     }
     const int64_t i0 = q << 2;
     if (i0 + 3 < n) {
