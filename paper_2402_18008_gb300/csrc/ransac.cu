@@ -916,7 +916,7 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
     int32_t *__restrict__ best_count, int32_t *__restrict__ best_hyp, int32_t *__restrict__ n_eval,
     int32_t *__restrict__ hyp_counts, uint8_t *__restrict__ mask)
 {
-    constexpr int kTile = 2048, kPer = 4;
+    constexpr int kPer = 16, kTile = kPer * 512;
     grid_launch_dependents();
     grid_dependency_wait();
     const int32_t p = blockIdx.x;
@@ -926,7 +926,7 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
     const bool overflow = *ws.flags != 0;
     const int64_t hb = overflow ? 0 : ws.hyp_off[p];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ int32_t s_wmax[16], s_carry, s_stop, s_end, s_istar, s_bi;
+    __shared__ int32_t s_wmax[16], s_carry, s_end, s_istar, s_bi;
     __shared__ float sH[9];
     const int32_t *cnt = ws.counts + hb;
     int32_t *pre = aw.prefix + hb;
@@ -940,12 +940,17 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
     __syncthreads();
     const bool active = !overflow && N >= 4 && k > 0;
     if (active) {
-        for (int32_t t0 = 0; t0 < k; t0 += kTile) {
+        // The stop is at or before the bound the scoring left: at i = kbound
+        // the best of 0..i-1 is at least the count c_j that set it, and K is
+        // non-increasing, so K(best) <= K(c_j) <= kbound.  The prefix maxima
+        // are needed up to there only (every chunk before it was scored).
+        const int32_t lim = min(k, max(1, aw.kbound[p]));
+        for (int32_t t0 = 0; t0 < lim; t0 += kTile) {
             const int32_t b = t0 + kPer * (int32_t)threadIdx.x;
             int32_t m[kPer], run = -2;
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
-                const int32_t c = b + q < k ? cnt[b + q] : -2;
+                const int32_t c = b + q < lim ? cnt[b + q] : -2;
                 run = max(run, c);
                 m[q] = run;
             }
@@ -964,18 +969,15 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
             if (lane > 0) before = max(before, excl);
 #pragma unroll
             for (int q = 0; q < kPer; ++q)
-                if (b + q < k) pre[b + q] = max(before, m[q]);
+                if (b + q < lim) pre[b + q] = max(before, m[q]);
             __syncthreads();
             if (threadIdx.x == 0) {
                 int32_t tile_max = s_carry;
                 for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tile_max = max(tile_max, s_wmax[w]);
                 s_carry = tile_max;
-                const int32_t e = min(t0 + kTile, k);
-                s_end = e;
-                s_stop = e == k || e >= adaptive_k(pre[e - 1], N, k, aw.log_fail);
+                s_end = lim;
             }
             __syncthreads();
-            if (s_stop) break;
         }
         // first i in [1, end] with the stop condition (it holds at end)
         if (wid == 0) {
@@ -994,20 +996,32 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
             if (lane == 0) s_istar = lo;
         }
         __syncthreads();
-        // first index of the best count before the stop
-        const int32_t istar = s_istar, best = pre[istar - 1];
-        int32_t bi = 0x7fffffff;
-        for (int32_t h = threadIdx.x; h < istar; h += blockDim.x)
-            if (cnt[h] == best) { bi = h; break; }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bi = min(bi, __shfl_xor_sync(0xffffffffu, bi, o));
-        if (lane == 0) atomicMin(&s_bi, bi);
+        // first index of the best count before the stop: the first h with
+        // pre[h] >= best (the prefix maxima do not decrease, and first reach
+        // the best where it first occurs; it holds at istar - 1)
+        if (wid == 0) {
+            const int32_t best = pre[s_istar - 1];
+            int32_t lo = 0, hi = s_istar - 1;
+            while (lo < hi) {
+                const int32_t st = (hi - lo + 30) / 31;
+                const int32_t q = lo + lane * st;
+                const bool ok = q >= hi || pre[q] >= best;
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                const int f = __ffs(bal) - 1;
+                const int32_t nhi = min(hi, lo + f * st);
+                lo = f > 0 ? lo + (f - 1) * st + 1 : lo;
+                hi = nhi;
+            }
+            if (lane == 0) s_bi = lo;
+        }
     }
     __syncthreads();
     const int32_t istar = s_istar;
-    if (hyp_counts && !overflow)
+    if (hyp_counts && !overflow) {
+#pragma unroll 4
         for (int32_t h = threadIdx.x; h < k; h += blockDim.x)
             hyp_counts[hb + h] = !active ? -1 : (h < istar ? cnt[h] : -2);
+    }
     if (threadIdx.x == 0) {
         int32_t bi = -1, bc = 0;
         if (overflow) {
