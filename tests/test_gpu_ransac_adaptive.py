@@ -97,7 +97,10 @@ def test_adaptive_equals_fixed_ransac_over_the_evaluated_prefix():
 
 @pytest.mark.parametrize("tuning", [dict(block_warps=4, hyps_per_thread=4, tile_points=2048),
                                     dict(block_warps=8, hyps_per_thread=1, tile_points=256),
-                                    dict(block_warps=2, hyps_per_thread=2, tile_points=64, grid_blocks=7)])
+                                    dict(block_warps=2, hyps_per_thread=2, tile_points=64, grid_blocks=7),
+                                    # one block takes every item of both epochs (chunk 0 of all
+                                    # problems, then the re-planned live chunks)
+                                    dict(block_warps=4, hyps_per_thread=1, tile_points=512, grid_blocks=1)])
 def test_adaptive_outputs_do_not_depend_on_tuning_or_skipped_work(tuning):
     rb = workloads.ransac_batch(P=40, seed=9, n_max=4000)
     caps = np.full(40, 4096, np.int32)
