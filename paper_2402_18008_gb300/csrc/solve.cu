@@ -8,9 +8,9 @@
 // with streaming (evict-first) stores.  A persistent grid strides over the
 // quads; each thread copies its next quad's 16 float4 into its own slots of a
 // two-stage shared-memory ring (cp.async) while it solves the current one, so
-// the loads of the next step are in flight during the arithmetic (the plain
-// ACA path; SKS and the flagged solve, bound by their arithmetic, load
-// directly, and SKS runs two sets per packed f32x2 instruction).  When the layout does
+// the loads of the next step are in flight during the arithmetic (the ACA
+// paths; SKS, bound by its arithmetic, loads directly and runs two sets per
+// packed f32x2 instruction).  When the layout does
 // not allow 16-byte accesses a scalar variant (one set per thread, coalesced
 // 4-byte accesses) runs instead.
 #include "aca_math.cuh"
@@ -255,16 +255,18 @@ static aca_status launch_solve(const float *pts, float *H, uint8_t *flags, int64
     const int threads = 256;
     const bool vec = n >= kSmallBatch && (ld % 4 == 0) && aligned16(pts) && aligned16(H) &&
                      (!FLAGS || (reinterpret_cast<uintptr_t>(flags) & 3u) == 0);
-    // the ACA solve (~365 instructions a set) sits at the HBM stream:
-    // prefetching pays (0.95 -> 0.98 of copy bandwidth).  SKS, and ACA with
-    // the degeneracy flags, are bound by their arithmetic and run faster on
-    // direct loads in 256-thread blocks (SKS 40.5 against 33.5, flags 55.1
-    // against 54.3 G sets/s on the ring).
-    constexpr bool kRing = SOLVER == kAca && !FLAGS;
+    // The ACA solve (~365 instructions a set) sits at the HBM stream:
+    // prefetching pays (0.95 -> 0.98 of copy bandwidth) at 2 blocks of 128
+    // threads per SM.  With the flags (~490 instructions) the arithmetic
+    // leads and a third block per SM pays (58.8 against 55.1 G sets/s with
+    // direct loads).  SKS, bound by its arithmetic, runs best on direct loads
+    // in 256-thread blocks (43.0 against 42.2 on the ring at 3 blocks).
+    constexpr bool kRing = SOLVER == kAca;
+    constexpr int kRingBlocks = FLAGS ? 3 : kRingBlocksPerSm;
     if (kRing && vec) {
         if constexpr (kRing) {
-            const aca_status r = launch_ring<16>(solve_ring_kernel<SOLVER, NORM, FLAGS>, "aca_solve", n, st, pts, H,
-                                                 flags, n, ld);
+            const aca_status r = launch_ring<16, kRingBlocks>(solve_ring_kernel<SOLVER, NORM, FLAGS>, "aca_solve", n,
+                                                              st, pts, H, flags, n, ld);
             if (r != ACA_OK)
                 return r;
         }
