@@ -265,9 +265,11 @@ aca_status aca_sample_indices(int64_t N, int32_t n_hyp, uint64_t seed, uint32_t 
  *   workspace  at least ransac_aca_adaptive_workspace_size(P, total_max_hyps)
  *              bytes, 256-byte aligned.
  * Other arguments, outputs and errors as ransac_aca; confidence outside
- * (0, 1) is ACA_ERR_INVALID_ARG.  Work order: the items of all problems are
- * taken in rounds (round r = hypothesis block r of every problem that has
- * one), so that a problem's earlier blocks finish while its later ones wait.
+ * (0, 1) is ACA_ERR_INVALID_ARG.  Work order: the first hypothesis block of
+ * every problem, then, re-planned from the bounds that block set, the blocks
+ * still before each problem's bound, taken in rounds (round r = block r of
+ * every problem that has one), so that a problem's earlier blocks finish
+ * while its later ones wait.
  */
 size_t ransac_aca_adaptive_workspace_size(int32_t P, int64_t total_max_hyps);
 
