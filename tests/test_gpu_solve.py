@@ -76,7 +76,7 @@ def test_full_size_workload_sampled_against_oracle():
 
 
 @pytest.mark.parametrize("solver", ["aca", "sks"])
-@pytest.mark.parametrize("n", [(1 << 18) + 5, (1 << 20) + 7])
+@pytest.mark.parametrize("n", [1 << 18, (1 << 18) + 5, (1 << 20) + 7])
 def test_vector_and_scalar_paths_agree_bitwise(solver, n):
     # large batches (>= 2^18 sets) with ld % 4 == 0 take the float4 paths
     # (ACA without flags: the prefetching ring, several quads per thread at
@@ -84,13 +84,14 @@ def test_vector_and_scalar_paths_agree_bitwise(solver, n):
     # and misaligned bases the one-set-per-thread path
     ms = workloads.minimal_sets(n, seed=6)
     ldv = (n + 4) & ~3                   # a multiple of 4 above n: float4 path with padding
+    lds = n | 1                          # odd: the one-set-per-thread path
     for norm in (0, 1, 2):
         Hv, _ = _solve(ms.pts, n, ldv, norm=norm, solver=solver)
-        Hs1, _ = _solve(ms.pts, n, n, norm=norm, solver=solver)
+        Hs1, _ = _solve(ms.pts, n, lds, norm=norm, solver=solver)
         assert torch.equal(Hv[:, :n], Hs1[:, :n]), norm
         assert torch.all(Hv[:, n:] == 12345.0)
     H4, f4 = _solve(ms.pts, n, ldv, solver=solver, flags=True)        # float4 path, ragged tail
-    H1, f1 = _solve(ms.pts, n, n, solver=solver, flags=True)          # ld odd -> scalar path
+    H1, f1 = _solve(ms.pts, n, lds, solver=solver, flags=True)        # ld odd -> scalar path
     assert torch.equal(H4[:, :n], H1[:, :n])
     assert torch.equal(f4[:n], f1[:n])
     assert torch.all(H4[:, n:] == 12345.0) and torch.all(f4[n:] == 0xEE)
@@ -228,13 +229,14 @@ def test_affine_three_point_solver_parity(n, ld):
         assert np.max(np.hypot(X - s[6 + 2 * k], Y - s[7 + 2 * k])) < 1e-2
 
 
-def test_affine_ring_and_scalar_paths_agree_bitwise():
-    # 2^20 + 7 sets: the prefetching ring (ld % 4 == 0, several quads per
-    # thread, ragged last quad) against the one-set-per-thread path (odd ld)
-    n = (1 << 20) + 7
+@pytest.mark.parametrize("n", [1 << 18, (1 << 20) + 7])
+def test_affine_ring_and_scalar_paths_agree_bitwise(n):
+    # the prefetching ring (ld % 4 == 0; at 2^20 + 7 several quads per thread
+    # and a ragged last quad; 2^18 is the smallest batch it takes) against
+    # the one-set-per-thread path (odd ld)
     p12 = _affine_planes(workloads.minimal_sets(n, seed=11))
     out = []
-    for ld in ((n + 4) & ~3, n):
+    for ld in ((n + 4) & ~3, n | 1):
         pts = torch.zeros((12, ld), dtype=torch.float32, device="cuda")
         pts[:, :n] = cuda(p12)
         for norm in (0, 1, 2):
