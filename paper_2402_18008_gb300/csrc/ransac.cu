@@ -548,16 +548,18 @@ __global__ void __launch_bounds__(1024) ransac_replan_adaptive_kernel(const int6
     build_rounds(offsets, P, HB, T, lo, hi, ws, aw, wt_a, wt_b, carry_a, carry_b, s_rounds);
 }
 
-// Clears the counts and the chunk completion counters of the adaptive variant.
-__global__ void zero_adaptive_kernel(Workspace ws, AdaptiveWs aw, int32_t P)
+// Clears the counts and the chunk completion counters of the adaptive
+// variant.  Their sizes are the workspace's, known before the set-up kernel
+// runs, so the clearing overlaps the set-up; each block awaits the set-up's
+// completion before it exits, and the scoring kernel awaits this one.
+__global__ void zero_adaptive_kernel(Workspace ws, AdaptiveWs aw)
 {
     grid_launch_dependents();
-    grid_dependency_wait();
-    if (*ws.flags) return;
-    const int64_t nc = ws.hyp_off[P], nk = aw.chunk_off[P];
+    const int64_t nc = ws.capacity, nk = aw.cb;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) ws.counts[i] = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += stride) aw.chunk_done[i] = 0;
+    grid_dependency_wait();
 }
 
 __global__ void zero_counts_kernel(Workspace ws, int32_t P)
@@ -1224,7 +1226,7 @@ extern "C" aca_status ransac_aca_adaptive(const float *corr, const int64_t *offs
         const int threads = 256;
         const int64_t work = total_max_hyps > aw.cb ? total_max_hyps : aw.cb;
         const int grid = resident_grid(zero_adaptive_kernel, threads, 0, (work + threads - 1) / threads);
-        launch_after_previous(zero_adaptive_kernel, dim3(grid), dim3(threads), 0, st, ws, aw, P);
+        launch_after_previous(zero_adaptive_kernel, dim3(grid), dim3(threads), 0, st, ws, aw);
         if ((s = check_launch("ransac_aca_adaptive (zero)")) != ACA_OK) return s;
     }
     const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
