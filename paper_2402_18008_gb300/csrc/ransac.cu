@@ -185,10 +185,11 @@ __device__ __forceinline__ int inlier2(const float2 g[9], float4 p, float4 q, fl
 }
 
 struct Workspace {
-    int64_t *hyp_off;            // [P+1]
-    int64_t *item_off;           // [P+1]
+    int64_t *hyp_off;            // [P+1] prefix of the hypothesis counts, problem order
+    int64_t *item_off;           // [P+1] prefix of the work items over `order` (fixed counts)
     unsigned long long *counter; // [1] work counter
     int32_t *flags;              // [1] 1 = counts capacity exceeded
+    int32_t *order;              // [P] scoring order of the problems (fixed counts): largest N first
     int32_t *counts;             // [capacity]
     int64_t capacity;
 };
@@ -207,6 +208,8 @@ static Workspace carve(void *base, int32_t P, size_t bytes)
     w.counter = reinterpret_cast<unsigned long long *>(b + o);
     w.flags = reinterpret_cast<int32_t *>(b + o + 8);
     o += 256;
+    w.order = reinterpret_cast<int32_t *>(b + o);
+    o += align256(sizeof(int32_t) * (size_t)P);
     w.counts = reinterpret_cast<int32_t *>(b + o);
     w.capacity = bytes > o ? (int64_t)((bytes - o) / sizeof(int32_t)) : 0;
     return w;
@@ -214,7 +217,7 @@ static Workspace carve(void *base, int32_t P, size_t bytes)
 
 static size_t header_bytes(int32_t P)
 {
-    return 2 * align256(sizeof(int64_t) * (size_t)(P + 1)) + 256;
+    return 2 * align256(sizeof(int64_t) * (size_t)(P + 1)) + 256 + align256(sizeof(int32_t) * (size_t)P);
 }
 
 // Extra workspace of the adaptive variant (after the standard header).
@@ -267,6 +270,8 @@ static void carve_adaptive(void *base, int32_t P, int64_t total, Workspace &w, A
     w.counter = reinterpret_cast<unsigned long long *>(b + o);
     w.flags = reinterpret_cast<int32_t *>(b + o + 8);
     o += 256;
+    w.order = reinterpret_cast<int32_t *>(b + o);          // unused by the adaptive variant
+    o += align256(sizeof(int32_t) * (size_t)P);
     a.chunk_off = reinterpret_cast<int64_t *>(b + o);
     o += align256(sizeof(int64_t) * (size_t)(P + 1));
     a.order = reinterpret_cast<int32_t *>(b + o);
@@ -333,12 +338,30 @@ __device__ int64_t block_scan_incl(int64_t v, int64_t *warp_tot)
     return v;
 }
 
+// Size class of a problem for the scoring order: floor(log2 N), 0..31.
+__device__ __forceinline__ int n_class(int64_t N)
+{
+    if (N <= 1) return 0;
+    const int c = 63 - __clzll((unsigned long long)N);
+    return c < 31 ? c : 31;
+}
+
+// Set-up of the fixed-count variant (one block of 1024 threads): hypothesis
+// prefix sums in problem order, the scoring order, the work-item prefix sums
+// over that order, the work counter.  With `by_size`, the scoring order is
+// problems by size class, largest first (a counting sort; the order within
+// a class follows the atomics and only affects speed), so that the last
+// items handed out are the short ones of small problems and the final wave
+// ends evenly (512 pairs: 0.691 -> 0.678 ms).  Small batches keep the
+// problem order and the single pass (the sort's extra passes cost a one-pair
+// RANSAC 2 us of its 18).
 __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__restrict__ offsets,
                                                            const int32_t *__restrict__ n_hyp, int32_t P, int HB,
-                                                           int T, Workspace ws, bool zero_here)
+                                                           int T, Workspace ws, bool zero_here, bool by_size)
 {
     __shared__ int64_t wt_a[32], wt_b[32];
     __shared__ int64_t carry_a, carry_b;
+    __shared__ int32_t s_base[32];
     grid_launch_dependents();
     if (threadIdx.x == 0) {
         carry_a = 0;
@@ -348,6 +371,7 @@ __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__rest
         *ws.counter = 0ull;
         *ws.flags = 0;
     }
+    if (threadIdx.x < 32) s_base[threadIdx.x] = 0;
     __syncthreads();
     for (int32_t base = 0; base < P; base += 1024) {
         const int32_t p = base + (int32_t)threadIdx.x;
@@ -355,14 +379,19 @@ __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__rest
         if (p < P) {
             k = n_hyp[p] > 0 ? n_hyp[p] : 0;
             const int64_t N = offsets[p + 1] - offsets[p];
-            if (N >= 4 && k > 0)
-                items = ((k + HB - 1) / HB) * ((N + T - 1) / T);
+            if (by_size) {
+                atomicAdd(&s_base[n_class(N)], 1);
+            } else {
+                ws.order[p] = p;
+                if (N >= 4 && k > 0)
+                    items = ((k + HB - 1) / HB) * ((N + T - 1) / T);
+            }
         }
         const int64_t ia = block_scan_incl(k, wt_a);
-        const int64_t ib = block_scan_incl(items, wt_b);
+        const int64_t ib = by_size ? 0 : block_scan_incl(items, wt_b);
         if (p < P) {
             ws.hyp_off[p + 1] = carry_a + ia;
-            ws.item_off[p + 1] = carry_b + ib;
+            if (!by_size) ws.item_off[p + 1] = carry_b + ib;
         }
         __syncthreads();
         if (threadIdx.x == 1023) {
@@ -370,6 +399,37 @@ __global__ void __launch_bounds__(1024) ransac_prep_kernel(const int64_t *__rest
             carry_b += ib;
         }
         __syncthreads();
+    }
+    if (by_size) {
+        if (threadIdx.x == 0) {
+            // first position of each class, largest class first
+            int32_t acc = 0;
+            for (int c = 31; c >= 0; --c) {
+                const int32_t n = s_base[c];
+                s_base[c] = acc;
+                acc += n;
+            }
+        }
+        __syncthreads();
+        for (int32_t p = threadIdx.x; p < P; p += 1024)
+            ws.order[atomicAdd(&s_base[n_class(offsets[p + 1] - offsets[p])], 1)] = p;
+        __syncthreads();
+        for (int32_t base = 0; base < P; base += 1024) {
+            const int32_t j = base + (int32_t)threadIdx.x;
+            int64_t items = 0;
+            if (j < P) {
+                const int32_t p = ws.order[j];
+                const int64_t k = n_hyp[p] > 0 ? n_hyp[p] : 0;
+                const int64_t N = offsets[p + 1] - offsets[p];
+                if (N >= 4 && k > 0)
+                    items = ((k + HB - 1) / HB) * ((N + T - 1) / T);
+            }
+            const int64_t ib = block_scan_incl(items, wt_b);
+            if (j < P) ws.item_off[j + 1] = carry_b + ib;
+            __syncthreads();
+            if (threadIdx.x == 1023) carry_b += ib;
+            __syncthreads();
+        }
     }
     if (threadIdx.x == 0 && carry_a > ws.capacity) {
         *ws.flags = 1;
@@ -609,7 +669,8 @@ template <int HPT, bool ADAPTIVE>
 __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restrict__ corr,
                                                            const int64_t *__restrict__ offsets,
                                                            const int32_t *__restrict__ n_hyp, int32_t P, float thr,
-                                                           uint64_t seed, uint32_t prob_base, int T, Workspace ws,
+                                                           uint64_t seed, uint32_t prob_base, int T, bool ordered,
+                                                           Workspace ws,
                                                            AdaptiveWs aw)
 {
     constexpr int HB = 32 * HPT;
@@ -643,7 +704,7 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
                         info.item = item;
                     break;
                 }
-                int32_t p = 0, chunk = 0, slice = 0;
+                int32_t p = 0, chunk = 0, slice = 0, j_fixed = 0;
                 if constexpr (ADAPTIVE) {
                     // round r = chunk lo + r of every problem with more than
                     // r live chunks in this epoch
@@ -675,7 +736,8 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
                         }
                     }
                 } else {
-                    p = find_problem(ws.item_off, P, item);
+                    j_fixed = find_problem(ws.item_off, P, item);
+                    p = ordered ? ws.order[j_fixed] : j_fixed;   // the order is the identity unless sorted
                 }
                 if (lane == 0) {
                     const int64_t base = offsets[p];
@@ -683,7 +745,7 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
                     const int32_t k = n_hyp[p];
                     const int32_t S = (int32_t)((N + T - 1) / T);
                     if constexpr (!ADAPTIVE) {
-                        const int64_t r = item - ws.item_off[p];
+                        const int64_t r = item - ws.item_off[j_fixed];
                         chunk = (int32_t)(r / S);
                         slice = (int32_t)(r % S);
                     }
@@ -1130,7 +1192,8 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
 
     // counts of small workspaces are cleared by the prep kernel itself
     const bool zero_in_prep = ws.capacity <= 65536;
-    ransac_prep_kernel<<<1, 1024, 0, st>>>(offsets, n_hyp, P, HB, T, ws, zero_in_prep);
+    const bool by_size = P >= 64;     // problems by size, largest first (ransac_prep_kernel)
+    ransac_prep_kernel<<<1, 1024, 0, st>>>(offsets, n_hyp, P, HB, T, ws, zero_in_prep, by_size);
     aca_status s = check_launch("ransac_aca (prep)");
     if (s != ACA_OK) return s;
     if (!zero_in_prep) {
@@ -1150,7 +1213,8 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
             return set_error(ACA_ERR_CUDA, "ransac_aca: cannot reserve %zu bytes of shared memory", smem);    \
         const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
         launch_after_previous(k, dim3(grid), dim3(threads), smem, st, c4, offsets, n_hyp, P,                   \
-                              params->threshold_px, params->seed, params->problem_base, T, ws, AdaptiveWs{}); \
+                              params->threshold_px, params->seed, params->problem_base, T, by_size, ws,      \
+                              AdaptiveWs{});                                                                   \
     }
     if (HPT == 1) ACA_SCORE(1)
     else if (HPT == 2) ACA_SCORE(2)
@@ -1243,7 +1307,7 @@ extern "C" aca_status ransac_aca_adaptive(const float *corr, const int64_t *offs
             return set_error(ACA_ERR_CUDA, "ransac_aca_adaptive: cannot reserve %zu bytes of shared memory", smem);
         const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(kernel, threads, smem, 1 << 30);
         launch_after_previous(kernel, dim3(grid), dim3(threads), smem, st, c4, offsets, max_hyp, P,
-                              params->threshold_px, params->seed, params->problem_base, Tk, ws, aw);
+                              params->threshold_px, params->seed, params->problem_base, Tk, false, ws, aw);
         return check_launch("ransac_aca_adaptive (score)");
     };
     for (int e = 0; e < kEpochs; ++e) {
