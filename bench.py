@@ -607,15 +607,19 @@ def row_refit(torch, _lib, api, rb, stream, dev, fixed=None):
         times[name] = time_region(torch, plan.replay, 20, stream)
     # the paper's stages 3-5 without knowing the inlier ratios: the online
     # adaptive stop (99 %, cap 16384 per pair) and the refit, one graph
+    # (with the adaptive plan's own launch shape: the tuner's entry for it,
+    # cached by the adaptive row when that ran first)
     caps = torch.full((P,), ADAPTIVE_CAP, dtype=torch.int32, device=dev)
+    make_a = lambda **kw: api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, ADAPTIVE_CAP * P, confidence=0.99, **kw)
+    best_a = fixed or autotune.tune(make_a, P, int(rb.offsets[-1]), ADAPTIVE_CAP * P, device=dev, tag="adaptive")[0]
     plan = api.RansacPlan(corr, off, caps, RANSAC_THR, SEED, ADAPTIVE_CAP * P, confidence=0.99, refit_iters=10,
-                          **best).capture()
+                          **best_a).capture()
     for _ in range(3):
         plan.replay()
     times["adaptive_plus_refit"] = time_region(torch, plan.replay, 20, stream)
     res.update(ms_ransac_with_mask=times["ransac_only"], ms_ransac_plus_refit=times["ransac_plus_refit"],
                refit_share_of_pipeline=1.0 - times["ransac_only"] / times["ransac_plus_refit"],
-               ms_adaptive_ransac_plus_refit=times["adaptive_plus_refit"],
+               ms_adaptive_ransac_plus_refit=times["adaptive_plus_refit"], tuning_adaptive=best_a,
                us_per_pair_adaptive_ransac_plus_refit=times["adaptive_plus_refit"] * 1e3 / P)
     return {"refit_512": res}
 
