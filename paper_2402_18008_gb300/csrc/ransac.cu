@@ -116,34 +116,41 @@ __device__ __forceinline__ bool make_hypothesis(const float4 *__restrict__ c, ui
 // e = (X w - u)^2 + (Y w - v)^2 - thr^2 w^2 and the point is an inlier when
 // e < 0, i.e. ||(X, Y) - (u/w, v/w)|| < thr (e < 0 forces w != 0).  The FP32
 // evaluation is strict; a point with e == 0 exactly lies within rounding of
-// the threshold.  The hypothesis is kept as G = (-h11, -h12, -h13, -h21,
-// -h22, -h23, h31, h32, h33) and nthr2 = -thr^2 so that no negation is
-// needed:
-//   w = g6 x + g7 y + g8, -u = g0 x + g1 y + g2, -v = g3 x + g4 y + g5,
-//   du = X w - u, dv = Y w - v, e = du^2 + (dv^2 + (nthr2 w) w).
-// e is never -0 (each step adds a non-negative square to a sum that is not
-// -0), so its sign bit is exactly (e < 0) and counting is a shift and an add.
-// The same operations, in the same order, run lane-wise on f32x2 pairs in
-// the scoring loop (inlier2) and on scalars in the epilogue (inlier): packed
-// FP32 instructions round each lane exactly like the scalar ones, so counts
-// and masks agree bit for bit.
-__device__ __forceinline__ void to_test_form(float G[9], const float H[9])
+// the threshold.  The threshold is folded into the data so that the FMA pipe,
+// which bounds the scoring loop, does 11 operations per pair of tests
+// instead of 12: the hypothesis is kept as G = (-h11, -h12, -h13, -h21, -h22,
+// -h23, t h31, t h32, t h33) with t = thr (so w' = t w), and the target point
+// as (Xs, Ys) = (X, Y) RN(1/t), so that Xs w' = X w up to two roundings
+// (about 1e-7 relative, far inside the parity band):
+//   w' = g6 x + g7 y + g8, -u = g0 x + g1 y + g2, -v = g3 x + g4 y + g5,
+//   du = Xs w' - u, dv = Ys w' - v, e = du^2 + (dv^2 + w' (-w')),
+// the sign flip of w' being an integer operation.  e is never -0 (each step
+// adds a non-negative square to a sum that is not -0), so its sign bit is
+// exactly (e < 0) and counting is a shift and an add.  The same operations,
+// in the same order, run lane-wise on f32x2 pairs in the scoring loop
+// (inlier2) and on scalars in the epilogue (inlier): packed FP32
+// instructions round each lane exactly like the scalar ones, so counts and
+// masks agree bit for bit.
+__device__ __forceinline__ void to_test_form(float G[9], const float H[9], float thr)
 {
 #pragma unroll
     for (int i = 0; i < 6; ++i) G[i] = -H[i];
-    G[6] = H[6];
-    G[7] = H[7];
-    G[8] = H[8];
+    G[6] = F_MUL(thr, H[6]);
+    G[7] = F_MUL(thr, H[7]);
+    G[8] = F_MUL(thr, H[8]);
 }
 
-__device__ __forceinline__ int inlier(const float G[9], float4 c, float nthr2)
+// RN(1/thr), the factor of the stored target coordinates.
+__device__ __forceinline__ float target_scale(float thr) { return F_DIV(1.0f, thr); }
+
+__device__ __forceinline__ int inlier(const float G[9], float4 c, float rthr)
 {
     const float w = F_FMA(G[6], c.x, F_FMA(G[7], c.y, G[8]));
     const float nu = F_FMA(G[0], c.x, F_FMA(G[1], c.y, G[2]));
     const float nv = F_FMA(G[3], c.x, F_FMA(G[4], c.y, G[5]));
-    const float du = F_FMA(c.z, w, nu);
-    const float dv = F_FMA(c.w, w, nv);
-    const float e = F_FMA(du, du, F_FMA(dv, dv, F_MUL(F_MUL(nthr2, w), w)));
+    const float du = F_FMA(F_MUL(c.z, rthr), w, nu);
+    const float dv = F_FMA(F_MUL(c.w, rthr), w, nv);
+    const float e = F_FMA(du, du, F_FMA(dv, dv, F_MUL(w, -w)));
     return (int)(__float_as_uint(e) >> 31);
 }
 
@@ -169,9 +176,17 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b)
     return d;
 }
 
+// Sign flip of both lanes (an integer operation, off the FMA pipe).
+__device__ __forceinline__ float2 neg2(float2 a)
+{
+    return make_float2(__uint_as_float(__float_as_uint(a.x) ^ 0x80000000u),
+                       __uint_as_float(__float_as_uint(a.y) ^ 0x80000000u));
+}
+
 // Two points (lane a, lane b) against one hypothesis given as broadcast pairs
-// g[i] = (G[i], G[i]); p = (x_a, x_b, y_a, y_b), q = (X_a, X_b, Y_a, Y_b).
-__device__ __forceinline__ int inlier2(const float2 g[9], float4 p, float4 q, float2 nthr2)
+// g[i] = (G[i], G[i]); p = (x_a, x_b, y_a, y_b), q = (Xs_a, Xs_b, Ys_a, Ys_b)
+// with the scaled target coordinates of the test form above.
+__device__ __forceinline__ int inlier2(const float2 g[9], float4 p, float4 q)
 {
     const float2 x = make_float2(p.x, p.y), y = make_float2(p.z, p.w);
     const float2 X = make_float2(q.x, q.y), Y = make_float2(q.z, q.w);
@@ -180,7 +195,7 @@ __device__ __forceinline__ int inlier2(const float2 g[9], float4 p, float4 q, fl
     const float2 nv = fma2(g[3], x, fma2(g[4], y, g[5]));
     const float2 du = fma2(X, w, nu);
     const float2 dv = fma2(Y, w, nv);
-    const float2 e = fma2(du, du, fma2(dv, dv, mul2(mul2(nthr2, w), w)));
+    const float2 e = fma2(du, du, fma2(dv, dv, mul2(w, neg2(w))));
     return (int)((__float_as_uint(e.x) >> 31) + (__float_as_uint(e.y) >> 31));
 }
 
@@ -682,8 +697,7 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
     int32_t *red = reinterpret_cast<int32_t *>(Hs + HB * 12);               // [W][HB]
     __shared__ ItemInfo info;
     __shared__ int32_t s_last;
-    const float nthr2s = -F_MUL(thr, thr);
-    const float2 nthr2 = make_float2(nthr2s, nthr2s);
+    const float rthr = target_scale(thr);
     const float nanv = __int_as_float(0x7fc00000);
 
     grid_launch_dependents();
@@ -792,7 +806,7 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
 #pragma unroll
                 for (int i = 0; i < 9; ++i) H[i] = 0.0f;   // scores nothing (w == 0)
             }
-            to_test_form(G, H);
+            to_test_form(G, H, thr);
 #pragma unroll
             for (int i = 0; i < 9; ++i) Hs[t * 12 + i] = G[i];
             Hs[t * 12 + 9] = valid ? 1.0f : 0.0f;
@@ -804,7 +818,7 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
             const float4 a = cp[i0 + 2 * q];
             const float4 b = (2 * q + 1 < ni) ? cp[i0 + 2 * q + 1] : make_float4(nanv, nanv, nanv, nanv);
             tile[2 * q] = make_float4(a.x, b.x, a.y, b.y);
-            tile[2 * q + 1] = make_float4(a.z, b.z, a.w, b.w);
+            tile[2 * q + 1] = make_float4(F_MUL(a.z, rthr), F_MUL(b.z, rthr), F_MUL(a.w, rthr), F_MUL(b.w, rthr));
         }
         __syncthreads();
 
@@ -825,12 +839,12 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
             const float4 p1 = tile[2 * (q + W)], q1 = tile[2 * (q + W) + 1];
 #pragma unroll
             for (int j = 0; j < HPT; ++j)
-                cnt[j] += inlier2(g[j], p0, q0, nthr2) + inlier2(g[j], p1, q1, nthr2);
+                cnt[j] += inlier2(g[j], p0, q0) + inlier2(g[j], p1, q1);
         }
         for (; q < npairs; q += W) {
             const float4 p0 = tile[2 * q], q0 = tile[2 * q + 1];
 #pragma unroll
-            for (int j = 0; j < HPT; ++j) cnt[j] += inlier2(g[j], p0, q0, nthr2);
+            for (int j = 0; j < HPT; ++j) cnt[j] += inlier2(g[j], p0, q0);
         }
 #pragma unroll
         for (int j = 0; j < HPT; ++j) red[wid * HB + lane + 32 * j] = cnt[j];
@@ -872,7 +886,7 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
 
 // Inlier mask of one problem under the test-form hypothesis G, the block's
 // threads striding over the points with four loads in flight each.
-__device__ void write_mask(const float G[9], const float4 *__restrict__ c, int64_t N, float nthr2, bool any,
+__device__ void write_mask(const float G[9], const float4 *__restrict__ c, int64_t N, float rthr, bool any,
                            uint8_t *__restrict__ out)
 {
     for (int64_t i0 = threadIdx.x; i0 < N; i0 += 4 * (int64_t)blockDim.x) {
@@ -885,7 +899,7 @@ __device__ void write_mask(const float G[9], const float4 *__restrict__ c, int64
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t i = i0 + u * (int64_t)blockDim.x;
-            if (i < N) out[i] = any ? (uint8_t)inlier(G, q[u], nthr2) : (uint8_t)0;
+            if (i < N) out[i] = any ? (uint8_t)inlier(G, q[u], rthr) : (uint8_t)0;
         }
     }
 }
@@ -962,9 +976,8 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
         float H[9], G[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) H[i] = sH[i];
-        to_test_form(G, H);
-        const float nthr2 = -F_MUL(thr, thr);
-        write_mask(G, corr + base, N, nthr2, s_best >= 0, mask + base);
+        to_test_form(G, H, thr);
+        write_mask(G, corr + base, N, target_scale(thr), s_best >= 0, mask + base);
     }
 }
 
@@ -1112,9 +1125,8 @@ __global__ void __launch_bounds__(512) ransac_finish_adaptive_kernel(
         float H[9], G[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) H[i] = sH[i];
-        to_test_form(G, H);
-        const float nthr2 = -F_MUL(thr, thr);
-        write_mask(G, corr + base, N, nthr2, s_bi >= 0, mask + base);
+        to_test_form(G, H, thr);
+        write_mask(G, corr + base, N, target_scale(thr), s_bi >= 0, mask + base);
     }
 }
 
