@@ -239,7 +239,8 @@ ACA_HD bool near_collinear(float cr, float la, float lb, float lc)
 }
 
 
-ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
+// Flag bits 1, 2 and 4 (the near-collinear triples).
+ACA_HD uint8_t aca_geom_flags(const Set &s, const AcaParts &p)
 {
     uint8_t f = 0;
     const float lMN1 = sq2(p.MN1x, p.MN1y), lMP1 = sq2(p.MP1x, p.MP1y), lNP1 = sq2(p.NP1x, p.NP1y);
@@ -254,7 +255,14 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
         near_collinear(p.t1, lNP1, lNQ1, lPQ1) || near_collinear(p.Q4x, lMQ2, lMP2, lPQ2) ||
         near_collinear(p.Q4y, lMN2, lMQ2, lNQ2) || near_collinear(p.t2, lNP2, lNQ2, lPQ2))
         f |= kFlagOtherTriple;
-    // x * 0 is 0 for every finite x and NaN otherwise: one FMA per value
+    return f;
+}
+
+// All flag bits; bit 8 marks a non-finite input or output: x * 0 + z is z for
+// every finite x and NaN otherwise, so one FMA per value decides it.
+ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
+{
+    uint8_t f = aca_geom_flags(s, p);
     const float *sv = &s.M1x;
     float z = 0.0f;
     for (int i = 0; i < 16; ++i) z = F_FMA(sv[i], 0.0f, z);

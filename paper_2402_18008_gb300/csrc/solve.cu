@@ -20,7 +20,9 @@ namespace aca {
 
 enum Solver { kAca = 0, kSks = 1 };
 
-template <int SOLVER, int NORM, bool FLAGS>
+// With FINITE = false the flags leave out bit 8 (non-finite), which the
+// caller then decides for several sets at once (solve_quad).
+template <int SOLVER, int NORM, bool FLAGS, bool FINITE = true>
 __device__ __forceinline__ void solve_one(const Set &s, float H[9], uint8_t &flag)
 {
     if (SOLVER == kAca) {
@@ -29,7 +31,7 @@ __device__ __forceinline__ void solve_one(const Set &s, float H[9], uint8_t &fla
         aca_compose(s, p, NORM != ACA_NORM_NONE, H);
         if (NORM == ACA_NORM_H33) normalize_h33(H);
         if (NORM == ACA_NORM_FROB) normalize_frob(H);
-        if (FLAGS) flag = aca_flags(s, p, H);
+        if (FLAGS) flag = FINITE ? aca_flags(s, p, H) : aca_geom_flags(s, p);
     } else {
         sks_solve(s, H);
         if (NORM == ACA_NORM_H33) normalize_h33(H);
@@ -37,7 +39,7 @@ __device__ __forceinline__ void solve_one(const Set &s, float H[9], uint8_t &fla
         if (FLAGS) {
             AcaParts p;
             aca_parts(s, p);
-            flag = aca_flags(s, p, H);
+            flag = FINITE ? aca_flags(s, p, H) : aca_geom_flags(s, p);
         }
     }
 }
@@ -94,6 +96,18 @@ __device__ __forceinline__ void solve_quad(const float4 (&v)[16], int64_t q, flo
             }
         }
     } else {
+        // bit 8 (non-finite) of the four sets at once, in aca_flags' test
+        // x * 0 + z, on packed pairs (sets 0-1 in the .x/.y lanes, 2-3 in
+        // .z/.w) at half the instructions: the inputs first, the outputs below
+        const P2 zero = vpack(0.0f, 0.0f);
+        P2 z01 = zero, z23 = zero;
+        if (FLAGS) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                z01 = vfma(vpack(v[k].x, v[k].y), zero, z01);
+                z23 = vfma(vpack(v[k].z, v[k].w), zero, z23);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             Set s;
@@ -103,11 +117,24 @@ __device__ __forceinline__ void solve_quad(const float4 (&v)[16], int64_t q, flo
                 sv[k] = (&v[k].x)[j];
             float H[9];
             uint8_t f = 0;
-            solve_one<SOLVER, NORM, FLAGS>(s, H, f);
+            solve_one<SOLVER, NORM, FLAGS, false>(s, H, f);
 #pragma unroll
             for (int k = 0; k < 9; ++k)
                 (&h[k].x)[j] = H[k];
             fl |= (uint32_t)f << (8 * j);
+        }
+        if (FLAGS) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                z01 = vfma(vpack(h[k].x, h[k].y), zero, z01);
+                z23 = vfma(vpack(h[k].z, h[k].w), zero, z23);
+            }
+            float z[4];
+            vunpack(z01, z[0], z[1]);
+            vunpack(z23, z[2], z[3]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (!(z[j] == 0.0f)) fl |= (uint32_t)kFlagNonFinite << (8 * j);
         }
     }
     const int64_t i0 = q << 2;
