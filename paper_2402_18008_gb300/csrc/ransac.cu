@@ -5,7 +5,9 @@
 //
 // Kernels (all on the caller's stream, no host synchronisation):
 //  1. ransac_prep_kernel    one block: per-problem prefix sums of hypotheses
-//                           and work items, resets the work counter;
+//                           and work items (with 64 or more problems, items
+//                           laid out largest problem first), resets the work
+//                           counter;
 //  2. zero_counts_kernel    clears the per-hypothesis counts;
 //  3. ransac_score_kernel   persistent grid; each block repeatedly takes an
 //                           item (problem p, hypotheses h0..h0+HB-1, points
