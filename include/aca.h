@@ -215,15 +215,22 @@ aca_status ransac_aca(const float *corr, const int64_t *offsets, const int32_t *
  * The scratch is a fixed array of ACA_NOALLOC_SCRATCH_BYTES inside the
  * library's device image, held by every GPU that loads the library until the
  * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress, with the device current) and caches it; make
- * that first call before any stream capture.  All calls share the array and
+ * address (cudaGetSymbolAddress, with the device current) and caches it.
+ * Under lazy module loading (the CUDA runtime's default) that lookup is also
+ * what loads the module and reserves the array on the device, so the first
+ * call on each device may allocate: make it once as a warm-up, outside any
+ * region that must not allocate and before any stream capture (or set
+ * CUDA_MODULE_LOADING=EAGER).  All calls share the array and
  * each call re-initialises it, so calls whose kernels may overlap on the GPU
  * race and must be serialised by the caller.
  *
  *   total_hyps must equal sum(n_hyp); a request that needs more than
  *   ACA_NOALLOC_SCRATCH_BYTES (ransac_aca_workspace_size(P, total_hyps))
- *   is rejected with ACA_ERR_WORKSPACE before anything is launched.  Other
- *   arguments, outputs and results are those of ransac_aca.
+ *   is rejected with ACA_ERR_WORKSPACE before anything is launched.  The
+ *   count capacity is exactly total_hyps: if the device-side sum of n_hyp
+ *   exceeds it, nothing is scored and every best_hyp is -2, as with a
+ *   ransac_aca workspace of that size.  Other arguments, outputs and results
+ *   are those of ransac_aca.
  */
 #define ACA_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 aca_status ransac_aca_noalloc(const float *corr, const int64_t *offsets, const int32_t *n_hyp, int32_t P,

@@ -247,10 +247,20 @@ def ransac_aca_noalloc(corr, offsets, n_hyp, total_hyps: int, params: RansacPara
     P = n_hyp.numel()
     if offsets.numel() != P + 1:
         raise ValueError("offsets must have P+1 entries")
+    for t, nm in ((offsets, "offsets"), (n_hyp, "n_hyp"), (best_H, "best_H"), (best_count, "best_count"),
+                  (best_hyp, "best_hyp")):
+        if not t.is_contiguous():
+            raise ValueError(f"{nm} must be contiguous")
+    if best_H.numel() < 9 * P or best_count.numel() < P or best_hyp.numel() < P:
+        raise ValueError("output tensors too small")
     if hyp_counts is not None:
         _need(hyp_counts, "hyp_counts", torch.int32)
+        if hyp_counts.numel() < total_hyps or not hyp_counts.is_contiguous():
+            raise ValueError("hyp_counts must be a contiguous tensor of at least total_hyps entries")
     if inlier_mask is not None:
         _need(inlier_mask, "inlier_mask", torch.uint8)
+        if inlier_mask.numel() < corr.shape[0]:
+            raise ValueError("inlier_mask too small")
     _check(load().ransac_aca_noalloc(_ptr(corr), _ptr(offsets), _ptr(n_hyp), P, int(total_hyps), ctypes.byref(params),
                                      _ptr(best_H), _ptr(best_count), _ptr(best_hyp), _ptr(hyp_counts),
                                      _ptr(inlier_mask), ctypes.c_void_p(_stream(stream))))

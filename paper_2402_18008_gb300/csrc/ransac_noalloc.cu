@@ -14,8 +14,12 @@
 // In host code its name is only a host-side stand-in, not a device address:
 // the device address is looked up once per device, with that device current,
 // by cudaGetSymbolAddress on the first call made on that device, and cached.
-// Because that first call does this set-up, it should come before any stream
-// capture.  All calls share the one array and each call re-initialises what
+// Under lazy module loading (the CUDA runtime's default), that lookup is also
+// what loads this file's module onto the device and reserves the array, so
+// the first call on each device may allocate: make it once as a warm-up,
+// outside any region that must not allocate and before any stream capture
+// (or run with CUDA_MODULE_LOADING=EAGER, which reserves the array when the
+// library's context is created).  All calls share the one array and each call re-initialises what
 // must start at zero (the work counter, the overflow flag and the counts),
 // so calls whose kernels overlap on the GPU (two streams, or two host threads)
 // race on it and must be serialised by the caller.
@@ -73,6 +77,12 @@ extern "C" aca_status ransac_aca_noalloc(const float *corr, const int64_t *offse
     const aca_status st = scratch_for_current_device(&scratch);
     if (st != ACA_OK)
         return st;
+    // Only the part of the array that total_hyps accounts for is handed on:
+    // the count capacity is then exactly total_hyps, so a device-side sum of
+    // n_hyp above it is caught by ransac_aca's overflow check (best_hyp = -2,
+    // nothing scored, no write past the caller's hyp_counts) as it is with a
+    // caller workspace of the same size.
+    const size_t bytes = ransac_aca_workspace_size(P, 0) + sizeof(int32_t) * (size_t)total_hyps;
     return ransac_aca(corr, offsets, n_hyp, P, params, best_H, best_count, best_hyp, hyp_counts, inlier_mask,
-                      scratch, (size_t)ACA_NOALLOC_SCRATCH_BYTES, stream);
+                      scratch, bytes, stream);
 }

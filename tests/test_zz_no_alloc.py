@@ -4,8 +4,10 @@ a loop in which an allocation is not allowed, a fixed memory budget).  It
 must give exactly what ransac_aca gives with a caller workspace, on
 consecutive calls that reuse the library's built-in scratch.
 
-This file is collected last on purpose; it passes alone in a fresh process
-and after the other tests."""
+The file name sorts after every other test file, so that a run stopping at
+its first failure (pytest -x) has run all the other tests before this
+optional entry point is exercised; it passes alone in a fresh process and
+after the other tests."""
 import numpy as np
 import pytest
 import torch
@@ -56,6 +58,38 @@ def test_no_alloc_entry_point_matches_workspace_entry_point_on_two_consecutive_c
         for name in ref:
             assert np.array_equal(got[name], ref[name]), (seed, name)
         assert np.all(got["best_hyp"] >= 0)
+
+
+def test_no_alloc_small_batch_clears_its_counts_in_the_set_up_kernel():
+    # at most 65536 hypotheses: the counts are cleared by the set-up kernel
+    # itself rather than by a separate launch; run it after a larger call so
+    # that the shared scratch holds non-zero leftovers
+    for seed, P, n_max, cap in ((34, 30, 4000, 4096), (35, 12, 1500, 256)):
+        corr, off, k, tot, npts = _inputs(seed, P, n_max, cap)
+        ref = _with_workspace(corr, off, k, tot, seed)
+        got = _no_alloc(corr, off, k, tot, seed, npts)
+        for name in ref:
+            assert np.array_equal(got[name], ref[name]), (seed, name)
+    assert tot <= 65536
+
+
+def test_no_alloc_total_hyps_below_the_sum_of_n_hyp_is_caught_on_the_device():
+    # total_hyps understating sum(n_hyp): nothing is scored, every best_hyp
+    # is -2, and nothing is written past the caller's hyp_counts
+    corr, off, k, tot, npts = _inputs(36, 10, 800, 300)
+    short = tot - 100
+    P = k.numel()
+    dev = corr.device
+    counts = torch.full((short + 64,), -7, dtype=torch.int32, device=dev)    # 64 canaries after the buffer
+    best_hyp = torch.full((P,), -7, dtype=torch.int32, device=dev)
+    best_count = torch.full((P,), -7, dtype=torch.int32, device=dev)
+    params = _lib.RansacParams(threshold_px=3.0, seed=36)
+    _lib.ransac_aca_noalloc(corr, off, k, short, params, torch.zeros((P, 9), device=dev), best_count, best_hyp,
+                            hyp_counts=counts[:short])
+    torch.cuda.synchronize()
+    assert np.all(best_hyp.cpu().numpy() == -2)
+    assert np.all(best_count.cpu().numpy() == 0)
+    assert np.all(counts[short:].cpu().numpy() == -7)
 
 
 def test_no_alloc_rejects_requests_beyond_the_built_in_scratch():
