@@ -12,11 +12,16 @@ Philox sampling, brute-force RANSAC scoring, the online adaptive stop of
 Sec. 6.2 and the analytic Jacobian);
 ``exact.py`` holds exact-rational versions used by the pins;
 ``inlier_refit.py`` the float64 refit on all inliers (normalised DLT, then
-Levenberg-Marquardt: the global optimisation of Sec. 6.2, stage 5).
+Levenberg-Marquardt: the global optimisation of Sec. 6.2, stage 5);
+``fp32_bounds.c`` the tolerance model of the parity tests: first-order
+rounding-error bounds of the library's stated FP32 evaluation orders (ACA,
+SKS, the RANSAC inlier test), from which the solver gate and the per-point
+ambiguity band of the RANSAC counts follow.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (exact agreement with an independent DLT, invariants, special cases, cuRAND's
-Philox, brute-force enumeration).  None is "parity unpinned".
+Philox, brute-force enumeration; the bounds against exact rational arithmetic
+and an FP32 host evaluation).  None is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -31,6 +36,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_BOUNDS = os.path.join(_HERE, "fp32_bounds.c")
 _lock = threading.Lock()
 _lib = None
 
@@ -45,10 +51,11 @@ _u8 = ctypes.POINTER(ctypes.c_uint8)
 def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (plain C, FP64, OpenMP, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_BOUNDS))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-                               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+                               "-ffp-contract=off", "-fno-fast-math", _SRC, _SRC_BOUNDS, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -77,18 +84,27 @@ def lib():
             L.oracle_sample_degenerate.restype = ctypes.c_int
             L.oracle_normalize_frob.argtypes = [_d]
             L.oracle_score_problem.argtypes = [_f, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
-                                               ctypes.c_uint64, ctypes.c_uint32, _i32, _i32, ctypes.c_double,
-                                               ctypes.c_double]
+                                               ctypes.c_uint64, ctypes.c_uint32, _i32, _i32, _i32, ctypes.c_double]
             L.oracle_ransac.argtypes = [_f, _i64, _i32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
-                                        ctypes.c_uint32, _d, _i32, _i32, _i32, _i32, ctypes.c_double,
-                                        ctypes.c_double, _u8]
+                                        ctypes.c_uint32, _d, _i32, _i32, _i32, _i32, _i32, ctypes.c_double, _u8]
             L.oracle_adaptive_k.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_double]
             L.oracle_adaptive_k.restype = ctypes.c_int32
             L.oracle_adaptive_stop.argtypes = [_i32, ctypes.c_int32, ctypes.c_int64, ctypes.c_double]
             L.oracle_adaptive_stop.restype = ctypes.c_int32
             L.oracle_ransac_adaptive.argtypes = [_f, _i64, _i32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
                                                  ctypes.c_uint32, ctypes.c_double, _d, _i32, _i32, _i32, _i32,
-                                                 _i32, ctypes.c_double, ctypes.c_double, _u8]
+                                                 _i32, _i32, ctypes.c_double, _u8]
+            for name in ("oracle_aca_fp32_bound", "oracle_sks_fp32_bound"):
+                getattr(L, name).argtypes = [_d, _d, _d, _d, ctypes.c_int64]
+                getattr(L, name).restype = None
+            L.oracle_score_band.argtypes = [_d, _f, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _u8]
+            L.oracle_score_band.restype = ctypes.c_int64
+            L.oracle_score_band_px.argtypes = [_d, _f, ctypes.c_int64, ctypes.c_double, _d]
+            L.oracle_score_band_px.restype = None
+            L.oracle_fp32_rule_bound.argtypes = [ctypes.c_int, _d, _d]
+            L.oracle_fp32_rule_bound.restype = ctypes.c_double
+            L.oracle_score_bound_E.argtypes = [_d, _f, ctypes.c_int64, ctypes.c_double, _d, _d]
+            L.oracle_score_bound_E.restype = None
             _lib = L
     return _lib
 
@@ -225,23 +241,28 @@ def normalize_frob(H) -> np.ndarray:
     return H
 
 
-def score_problem(corr, n_hyp: int, thr: float, seed: int, prob: int = 0, band_px: float = 1e-4,
-                  herr: float = 0.0):
-    """Per-hypothesis counts (-1 = degenerate sample) and band counts (see
-    oracle_score_problem: band_px plus, when herr > 0, the first-order
-    effect of an FP32-solver error of herr * kappa_h * 2^-24 + 2^-23 on H)."""
+def score_problem(corr, n_hyp: int, thr: float, seed: int, prob: int = 0, band_px: float = 1e-4):
+    """Per-hypothesis counts (-1 = degenerate sample) and the ambiguous
+    points of each hypothesis (oracle_score_problem): those within band_px
+    of the threshold or within the first-order rounding bound of the FP32
+    test (fp32_bounds.c), split by the exact decision.  Returns
+    (counts, amb_in, amb_out); an FP32 count c is consistent when
+    counts - amb_in <= c <= counts + amb_out."""
     c = np.ascontiguousarray(corr, dtype=np.float32)
     N = c.shape[0]
     cnt = np.empty(n_hyp, dtype=np.int32)
-    band = np.empty(n_hyp, dtype=np.int32)
-    lib().oracle_score_problem(_ptr(c, _f), N, n_hyp, thr, seed, prob, _ptr(cnt, _i32), _ptr(band, _i32), band_px,
-                               herr)
-    return cnt, band
+    ai = np.empty(n_hyp, dtype=np.int32)
+    ao = np.empty(n_hyp, dtype=np.int32)
+    lib().oracle_score_problem(_ptr(c, _f), N, n_hyp, thr, seed, prob, _ptr(cnt, _i32), _ptr(ai, _i32),
+                               _ptr(ao, _i32), band_px)
+    return cnt, ai, ao
 
 
 def ransac(corr, offsets, n_hyp, thr: float, seed: int, problem_base: int = 0, band_px: float = 1e-4,
-           want_counts: bool = True, want_mask: bool = False, herr: float = 0.0) -> dict:
-    """Brute-force RANSAC over CSR problems; see oracle_ransac in oracle.c."""
+           want_counts: bool = True, want_mask: bool = False) -> dict:
+    """Brute-force RANSAC over CSR problems; see oracle_ransac in oracle.c.
+    band_in / band_out: ambiguous points per hypothesis (score_problem);
+    band_counts = their sum."""
     c = np.ascontiguousarray(corr, dtype=np.float32)
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     k = np.ascontiguousarray(n_hyp, dtype=np.int32)
@@ -251,14 +272,14 @@ def ransac(corr, offsets, n_hyp, thr: float, seed: int, problem_base: int = 0, b
     best_count = np.empty(P, dtype=np.int32)
     best_hyp = np.empty(P, dtype=np.int32)
     counts = np.empty(tot, dtype=np.int32) if want_counts else None
-    band = np.empty(tot, dtype=np.int32) if want_counts else None
+    ai = np.empty(tot, dtype=np.int32) if want_counts else None
+    ao = np.empty(tot, dtype=np.int32) if want_counts else None
     mask = np.empty(c.shape[0], dtype=np.uint8) if want_mask else None
     lib().oracle_ransac(_ptr(c, _f), _ptr(off, _i64), _ptr(k, _i32), P, thr, seed, problem_base,
                         _ptr(best_H, _d), _ptr(best_count, _i32), _ptr(best_hyp, _i32),
-                        _ptr(counts, _i32), _ptr(band, _i32), band_px, herr, _ptr(mask, _u8))
-    return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, hyp_counts=counts,
-                band_counts=band, inlier_mask=mask)
-
+                        _ptr(counts, _i32), _ptr(ai, _i32), _ptr(ao, _i32), band_px, _ptr(mask, _u8))
+    return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, hyp_counts=counts, band_in=ai,
+                band_out=ao, band_counts=None if ai is None else ai + ao, inlier_mask=mask)
 
 
 def adaptive_k(c: int, N: int, cap: int, confidence: float = 0.99) -> int:
@@ -275,11 +296,10 @@ def adaptive_stop(counts, N: int, confidence: float = 0.99) -> int:
 
 
 def ransac_adaptive(corr, offsets, max_hyp, thr: float, seed: int, confidence: float = 0.99,
-                    problem_base: int = 0, band_px: float = 1e-4, want_mask: bool = False,
-                    herr: float = 0.0) -> dict:
-    """RANSAC with the online stop (oracle_ransac_adaptive): counts and band
-    counts of all max_hyp hypotheses, n_eval, and the best over the evaluated
-    ones."""
+                    problem_base: int = 0, band_px: float = 1e-4, want_mask: bool = False) -> dict:
+    """RANSAC with the online stop (oracle_ransac_adaptive): counts and
+    ambiguous points (band_in / band_out, as in ransac) of all max_hyp
+    hypotheses, n_eval, and the best over the evaluated ones."""
     c = np.ascontiguousarray(corr, dtype=np.float32)
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     k = np.ascontiguousarray(max_hyp, dtype=np.int32)
@@ -290,14 +310,81 @@ def ransac_adaptive(corr, offsets, max_hyp, thr: float, seed: int, confidence: f
     best_hyp = np.empty(P, dtype=np.int32)
     n_eval = np.empty(P, dtype=np.int32)
     counts = np.empty(tot, dtype=np.int32)
-    band = np.empty(tot, dtype=np.int32)
+    ai = np.empty(tot, dtype=np.int32)
+    ao = np.empty(tot, dtype=np.int32)
     mask = np.empty(c.shape[0], dtype=np.uint8) if want_mask else None
     lib().oracle_ransac_adaptive(_ptr(c, _f), _ptr(off, _i64), _ptr(k, _i32), P, thr, seed, problem_base,
                                  confidence, _ptr(best_H, _d), _ptr(best_count, _i32), _ptr(best_hyp, _i32),
-                                 _ptr(n_eval, _i32), _ptr(counts, _i32), _ptr(band, _i32), band_px, herr,
+                                 _ptr(n_eval, _i32), _ptr(counts, _i32), _ptr(ai, _i32), _ptr(ao, _i32), band_px,
                                  _ptr(mask, _u8))
     return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, n_eval=n_eval, hyp_counts=counts,
-                band_counts=band, inlier_mask=mask)
+                band_in=ai, band_out=ao, band_counts=ai + ao, inlier_mask=mask)
 
 
 from .inlier_refit import hartley_normalization, refit, refit_dlt, refit_lm, refit_tolerance, reprojection_cost  # noqa: E402,F401
+
+
+def _fp32_bound(name, pts16, n=None, per_entry=False):
+    a = sets_aos(pts16, n)
+    m = a.shape[0]
+    beta = np.empty(m)
+    Hv = np.empty((m, 9)) if per_entry else None
+    He = np.empty((m, 9)) if per_entry else None
+    getattr(lib(), name)(_ptr(a, _d), _ptr(beta, _d), _ptr(Hv, _d), _ptr(He, _d), m)
+    return (beta, Hv, He) if per_entry else beta
+
+
+def aca_fp32_bound(pts16, n=None, per_entry=False):
+    """First-order bound on the error of the library's FP32 ACA evaluation
+    order (running error analysis, fp32_bounds.c): beta per set, the bound on
+    max |H^_fp32 - H^| at unit Frobenius norm; with per_entry, also the exact
+    H of that order (n, 9) and per-entry absolute bounds (n, 9)."""
+    return _fp32_bound("oracle_aca_fp32_bound", pts16, n, per_entry)
+
+
+def sks_fp32_bound(pts16, n=None, per_entry=False):
+    """As aca_fp32_bound, for the library's FP32 SKS evaluation order."""
+    return _fp32_bound("oracle_sks_fp32_bound", pts16, n, per_entry)
+
+
+def score_band(s16, corr, thr: float, band_px: float = 1e-4):
+    """Per-point ambiguity of one hypothesis (minimal set s16, 16 coordinates)
+    over corr (N, 4) float32: 1 where the FP32 inlier test may decide
+    otherwise than the exact test, or where the exact residual is within
+    band_px of the threshold.  Returns a (N,) uint8 array."""
+    s = np.ascontiguousarray(np.asarray(s16, dtype=np.float64).ravel())
+    c = np.ascontiguousarray(corr, dtype=np.float32)
+    amb = np.empty(c.shape[0], np.uint8)
+    lib().oracle_score_band(_ptr(s, _d), _ptr(c, _f), c.shape[0], float(thr), float(band_px), _ptr(amb, _u8))
+    return amb
+
+
+def score_band_px(s16, corr, thr: float):
+    """The FP32 test's bound at each point in pixels of |r - thr| (N,)."""
+    s = np.ascontiguousarray(np.asarray(s16, dtype=np.float64).ravel())
+    c = np.ascontiguousarray(corr, dtype=np.float32)
+    px = np.empty(c.shape[0])
+    lib().oracle_score_band_px(_ptr(s, _d), _ptr(c, _f), c.shape[0], float(thr), _ptr(px, _d))
+    return px
+
+
+def fp32_rule_bound(op: int, args):
+    """Bound of one rounding rule of fp32_bounds.c on FP32 operands (see
+    oracle_fp32_rule_bound): returns (exact value, bound on |fl - exact|)."""
+    a = np.zeros(8)
+    a[:len(args)] = np.asarray(args, dtype=np.float32).astype(np.float64)
+    v = np.zeros(1)
+    b = lib().oracle_fp32_rule_bound(int(op), _ptr(a, _d), _ptr(v, _d))
+    return float(v[0]), float(b)
+
+
+def score_bound_E(s16, corr, thr: float):
+    """Exact E = w^2 (r^2 - thr^2) of the inlier test at every point under the
+    hypothesis of minimal set s16, and the first-order bound on the error of
+    its FP32 evaluation (solve included).  Returns (E, B), each (N,)."""
+    s = np.ascontiguousarray(np.asarray(s16, dtype=np.float64).ravel())
+    c = np.ascontiguousarray(corr, dtype=np.float32)
+    E = np.empty(c.shape[0])
+    B = np.empty(c.shape[0])
+    lib().oracle_score_bound_E(_ptr(s, _d), _ptr(c, _f), c.shape[0], float(thr), _ptr(E, _d), _ptr(B, _d))
+    return E, B

@@ -1,0 +1,731 @@
+/*
+ * First-order rounding-error bounds for the FP32 evaluation orders that the
+ * CUDA library documents for its ACA and SKS minimal solvers and for its
+ * division-free RANSAC inlier test.  TEST INFRASTRUCTURE ONLY: this is the
+ * tolerance model of the parity tests (how far an FP32 result may lie from
+ * the exact one), not a solver; the library never calls it and it includes
+ * nothing of the library.
+ *
+ * Method: running error analysis (Wilkinson, "Rounding Errors in Algebraic
+ * Processes", 1963; Higham, "Accuracy and Stability of Numerical
+ * Algorithms", 2nd ed., 2002, Sec. 3.3).  Every quantity q of an FP32
+ * evaluation carries
+ *   v  its exact value (computed here in FP64; that rounding, ~1e-16
+ *      relative, is neglected against u = 2^-24),
+ *   e  a bound on |fl(q) - v|, valid to first order in u,
+ *   m  its magnitude: the same expression evaluated on absolute values
+ *      (used only by the u^2 terms of the double-float steps).
+ * Rules (u = 2^-24, round to nearest, no underflow or overflow):
+ *   exact FP32 input                 e = 0
+ *   exact difference (TwoSum pair)   e = e_a + e_b (no rounding)
+ *   rounded + - * fma /              propagated first-order terms + u |v|
+ *   Kahan's FMA determinant ad - bc  propagated terms + 2u |v|
+ *       (Jeannerod, Louvet and Muller, Math. Comp. 82, 2013: relative
+ *       error at most 2u for exact operands)
+ *   cross product of two exact differences given as value + remainder,
+ *   evaluated as Kahan's determinant of the values plus the four
+ *   first-order remainder products          2u |v| + 16 u^2 (|ux vy| + |uy vx|)
+ *       (the dropped remainder-by-remainder products are at most
+ *       u^2 (|ux vy| + |uy vx|), the four remainder products are summed with
+ *       at most 4 roundings of a sum bounded by 2u (|ux vy| + |uy vx|), and
+ *       the two final additions add u |v| plus u^2 terms)
+ *   double-float product / sum       propagated terms + 16 u^2 m
+ *       (TwoProduct and TwoSum are exact; the low parts, themselves of size
+ *       at most a few u m, are added with one or two roundings)
+ *   rounding a double-float to FP32  + u |v|
+ * Each final bound gets an allowance of 64 u^2 m for the neglected products
+ * of first-order terms.
+ *
+ * The evaluation orders (which quantities are rounded where) are those the
+ * library states for its solvers: ACA in local frames anchored at M1 / M2
+ * with exact edge differences, the eight cross products of Eq. 21, 25 and 27
+ * (t1 as cross(N1P1, N1Q1)) each from exact differences, the core of
+ * Eq. 28-29 and the local-frame product of Eq. 24 in double-float rounded
+ * once per entry, the translation back in FP32; SKS (Eq. 4-14) with exact
+ * differences, the similarity images P3, Q3 as compensated dot and cross
+ * products, the cleared-denominator form of Eq. 11-13, the composition of
+ * Eq. 14 in double-float rounded once per entry and the translation back in
+ * FP32; the inlier test in its threshold-folded form.  A bound that fails
+ * to cover the library's FP32 result therefore means that either the
+ * library or its stated evaluation order is wrong.
+ *
+ * Pinned by tests/test_oracle_fp32_bounds.py: every rule against exact
+ * rational arithmetic on random and cancellation-heavy FP32 operands, and
+ * the whole chains against an FP32 host evaluation of the same orders.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* One tape per chain: node k holds its exact value v, its magnitude m, the
+ * size C of its own rounding event (fl(q) = q + eps with |eps| <= u C, the
+ * eps of different nodes independent) and the partial derivatives of v
+ * with respect to up to four earlier nodes. */
+#define TAPE_MAX 640
+typedef struct {
+    double v, m, C;
+    int p[4];
+    double w[4];
+    int np;
+} node;
+typedef struct {
+    node n[TAPE_MAX];
+    int len;
+} tape;
+
+static const double U = 0x1p-24;
+
+static int push(tape *t, double v, double m, double C)
+{
+    node *q = &t->n[t->len];
+    q->v = v;
+    q->m = m;
+    q->C = C;
+    q->np = 0;
+    return t->len++;
+}
+static void dep(tape *t, int k, int p, double w)
+{
+    node *q = &t->n[k];
+    q->p[q->np] = p;
+    q->w[q->np] = w;
+    q->np++;
+}
+#define V(i) (t->n[i].v)
+#define M(i) (t->n[i].m)
+
+static int in(tape *t, double x) { return push(t, x, fabs(x), 0.0); }
+static int neg(tape *t, int a)
+{
+    const int k = push(t, -V(a), M(a), 0.0);
+    dep(t, k, a, -1.0);
+    return k;
+}
+/* exact sum / difference (an exact TwoSum pair) */
+static int xadd(tape *t, int a, int b, double sb)
+{
+    const double v = V(a) + sb * V(b);
+    const int k = push(t, v, fabs(v), 0.0);
+    dep(t, k, a, 1.0);
+    dep(t, k, b, sb);
+    return k;
+}
+static int xsub(tape *t, int a, int b) { return xadd(t, a, b, -1.0); }
+/* exact product by a constant that is a power of two */
+static int xscale(tape *t, int a, double c)
+{
+    const int k = push(t, c * V(a), fabs(c * V(a)), 0.0);
+    dep(t, k, a, c);
+    return k;
+}
+/* the value of a, rounded once to FP32 */
+static int rn(tape *t, int a)
+{
+    const int k = push(t, V(a), fabs(V(a)), fabs(V(a)));
+    dep(t, k, a, 1.0);
+    return k;
+}
+/* rounded FP32 operations */
+static int add(tape *t, int a, int b)
+{
+    const double v = V(a) + V(b);
+    const int k = push(t, v, fabs(v), fabs(v));
+    dep(t, k, a, 1.0);
+    dep(t, k, b, 1.0);
+    return k;
+}
+static int sub(tape *t, int a, int b)
+{
+    const double v = V(a) - V(b);
+    const int k = push(t, v, fabs(v), fabs(v));
+    dep(t, k, a, 1.0);
+    dep(t, k, b, -1.0);
+    return k;
+}
+static int mul(tape *t, int a, int b)
+{
+    const double v = V(a) * V(b);
+    const int k = push(t, v, fabs(v), fabs(v));
+    dep(t, k, a, V(b));
+    dep(t, k, b, V(a));
+    return k;
+}
+static int fma3(tape *t, int a, int b, int c)
+{
+    const double v = V(a) * V(b) + V(c);
+    const int k = push(t, v, fabs(v), fabs(v));
+    dep(t, k, a, V(b));
+    dep(t, k, b, V(a));
+    dep(t, k, c, 1.0);
+    return k;
+}
+static int dv(tape *t, int a, int b)
+{
+    const double v = V(a) / V(b);
+    const int k = push(t, v, fabs(v), fabs(v));
+    dep(t, k, a, 1.0 / V(b));
+    dep(t, k, b, -v / V(b));
+    return k;
+}
+/* Kahan's determinant a d - b c */
+static int det2(tape *t, int a, int b, int c, int d)
+{
+    const double v = V(a) * V(d) - V(b) * V(c);
+    const int k = push(t, v, fabs(v), 2.0 * fabs(v));
+    dep(t, k, a, V(d));
+    dep(t, k, d, V(a));
+    dep(t, k, b, -V(c));
+    dep(t, k, c, -V(b));
+    return k;
+}
+/* ux vy - uy vx of exact differences (value + remainder) */
+static int cross_x(tape *t, int ux, int uy, int vx, int vy)
+{
+    const double A = fabs(V(ux) * V(vy)) + fabs(V(uy) * V(vx));
+    const double v = V(ux) * V(vy) - V(uy) * V(vx);
+    const int k = push(t, v, fabs(v), 2.0 * fabs(v) + 16.0 * U * A);
+    dep(t, k, ux, V(vy));
+    dep(t, k, vy, V(ux));
+    dep(t, k, uy, -V(vx));
+    dep(t, k, vx, -V(uy));
+    return k;
+}
+/* double-float steps: exact value, event of size 16 u m with m the
+ * magnitude accumulated within the double-float chain (an FP32 operand
+ * enters it with m = |value|) */
+static int dfmul(tape *t, int a, int b)
+{
+    const double m = M(a) * M(b);
+    const int k = push(t, V(a) * V(b), m, 16.0 * U * m);
+    dep(t, k, a, V(b));
+    dep(t, k, b, V(a));
+    return k;
+}
+static int dfadd(tape *t, int a, int b)
+{
+    const double m = M(a) + M(b);
+    const int k = push(t, V(a) + V(b), m, 16.0 * U * m);
+    dep(t, k, a, 1.0);
+    dep(t, k, b, 1.0);
+    return k;
+}
+static int dfsub(tape *t, int a, int b)
+{
+    const double m = M(a) + M(b);
+    const int k = push(t, V(a) - V(b), m, 16.0 * U * m);
+    dep(t, k, a, 1.0);
+    dep(t, k, b, -1.0);
+    return k;
+}
+/* u . v of exact differences as a double-float */
+static int dot_x(tape *t, int ux, int uy, int vx, int vy)
+{
+    const double v = V(ux) * V(vx) + V(uy) * V(vy);
+    const double m = fabs(V(ux) * V(vx)) + fabs(V(uy) * V(vy));
+    const int k = push(t, v, m, 16.0 * U * m);
+    dep(t, k, ux, V(vx));
+    dep(t, k, vx, V(ux));
+    dep(t, k, uy, V(vy));
+    dep(t, k, vy, V(uy));
+    return k;
+}
+/* token allowance for the neglected second-order terms of an output */
+static int final_(tape *t, int a)
+{
+    const int k = push(t, V(a), fabs(V(a)), 64.0 * U * fabs(V(a)));
+    dep(t, k, a, 1.0);
+    return k;
+}
+
+/* Reverse sweep: adj[k] = dF/d(node k) for F = sum_j g[j] * node out[j]. */
+static void sweep(const tape *t, const int *out, const double *g, int nout, double *adj)
+{
+    memset(adj, 0, sizeof(double) * (size_t)t->len);
+    for (int j = 0; j < nout; ++j) adj[out[j]] += g[j];
+    for (int k = t->len - 1; k >= 0; --k) {
+        const double a = adj[k];
+        if (a == 0.0) continue;
+        const node *q = &t->n[k];
+        for (int i = 0; i < q->np; ++i) adj[q->p[i]] += a * q->w[i];
+    }
+}
+
+/* u * sum_k |adj[k]| C_k: the first-order bound on |fl(F) - F| */
+static double event_sum(const tape *t, const double *adj)
+{
+    double s = 0;
+    for (int k = 0; k < t->len; ++k) s += fabs(adj[k]) * t->n[k].C;
+    return U * s;
+}
+
+/* ------------------------------------------------------------------ */
+/* ACA (Eq. 20-29) in the library's evaluation order; H[9] receives the */
+/* tape indices of the nine output entries.                             */
+/* ------------------------------------------------------------------ */
+static void aca_chain(tape *t, const double *s, int H[9])
+{
+    int x[16];
+    for (int k = 0; k < 16; ++k) x[k] = in(t, s[k]);
+    const int M1x = x[0], M1y = x[1], N1x = x[2], N1y = x[3], P1x = x[4], P1y = x[5], Q1x = x[6], Q1y = x[7];
+    const int M2x = x[8], M2y = x[9], N2x = x[10], N2y = x[11], P2x = x[12], P2y = x[13], Q2x = x[14], Q2y = x[15];
+    /* exact edge differences */
+    const int mn1x = xsub(t, N1x, M1x), mn1y = xsub(t, N1y, M1y), mp1x = xsub(t, P1x, M1x), mp1y = xsub(t, P1y, M1y);
+    const int mq1x = xsub(t, Q1x, M1x), mq1y = xsub(t, Q1y, M1y), np1x = xsub(t, P1x, N1x), np1y = xsub(t, P1y, N1y);
+    const int nq1x = xsub(t, Q1x, N1x), nq1y = xsub(t, Q1y, N1y);
+    const int mn2x = xsub(t, N2x, M2x), mn2y = xsub(t, N2y, M2y), mp2x = xsub(t, P2x, M2x), mp2y = xsub(t, P2y, M2y);
+    const int mq2x = xsub(t, Q2x, M2x), mq2y = xsub(t, Q2y, M2y), np2x = xsub(t, P2x, N2x), np2y = xsub(t, P2y, N2y);
+    const int nq2x = xsub(t, Q2x, N2x), nq2y = xsub(t, Q2y, N2y);
+    /* Eq. 21, 25, 27 from the exact differences */
+    const int fA1 = cross_x(t, mn1x, mn1y, mp1x, mp1y);
+    const int Q3x = cross_x(t, mq1x, mq1y, mp1x, mp1y), Q3y = cross_x(t, mn1x, mn1y, mq1x, mq1y);
+    const int Q4x = cross_x(t, mq2x, mq2y, mp2x, mp2y), Q4y = cross_x(t, mn2x, mn2y, mq2x, mq2y);
+    const int t1 = cross_x(t, np1x, np1y, nq1x, nq1y), t2 = cross_x(t, np2x, np2y, nq2x, nq2y);
+    /* the composition uses the edge vectors rounded once */
+    const int MN1x = rn(t, mn1x), MN1y = rn(t, mn1y), MP1x = rn(t, mp1x), MP1y = rn(t, mp1y);
+    const int NP1x = rn(t, np1x), NP1y = rn(t, np1y);
+    const int MN2x = rn(t, mn2x), MN2y = rn(t, mn2y), MP2x = rn(t, mp2x), MP2y = rn(t, mp2y);
+    /* Eq. 29 and the local-frame product of Eq. 24, double-float */
+    const int c11 = dfmul(t, dfmul(t, t1, Q3y), Q4x), c22 = dfmul(t, dfmul(t, t1, Q3x), Q4y);
+    const int c33 = dfmul(t, dfmul(t, t2, Q3x), Q3y);
+    const int k0x = dfmul(t, c11, MN2x), k0y = dfmul(t, c11, MN2y), k1x = dfmul(t, c22, MP2x), k1y = dfmul(t, c22, MP2y);
+    const int L00 = rn(t, dfsub(t, dfmul(t, k0x, MP1y), dfmul(t, k1x, MN1y)));
+    const int L01 = rn(t, dfsub(t, dfmul(t, k1x, MN1x), dfmul(t, k0x, MP1x)));
+    const int L10 = rn(t, dfsub(t, dfmul(t, k0y, MP1y), dfmul(t, k1y, MN1y)));
+    const int L11 = rn(t, dfsub(t, dfmul(t, k1y, MN1x), dfmul(t, k0y, MP1x)));
+    const int L20 = rn(t, dfsub(t, dfsub(t, dfmul(t, c11, MP1y), dfmul(t, c22, MN1y)), dfmul(t, c33, NP1y)));
+    const int L21 = rn(t, dfadd(t, dfsub(t, dfmul(t, c22, MN1x), dfmul(t, c11, MP1x)), dfmul(t, c33, NP1x)));
+    const int L22 = rn(t, dfmul(t, c33, fA1));
+    /* H = T(M2) L T(-M1) in FP32 */
+    const int G02 = neg(t, fma3(t, M1x, L00, mul(t, M1y, L01)));
+    const int G12 = neg(t, fma3(t, M1x, L10, mul(t, M1y, L11)));
+    const int G22 = fma3(t, neg(t, M1x), L20, fma3(t, neg(t, M1y), L21, L22));
+    H[0] = fma3(t, M2x, L20, L00);
+    H[1] = fma3(t, M2x, L21, L01);
+    H[2] = fma3(t, M2x, G22, G02);
+    H[3] = fma3(t, M2y, L20, L10);
+    H[4] = fma3(t, M2y, L21, L11);
+    H[5] = fma3(t, M2y, G22, G12);
+    H[6] = L20;
+    H[7] = L21;
+    H[8] = G22;
+    for (int i = 0; i < 9; ++i) H[i] = final_(t, H[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* SKS (Eq. 4-14) in the library's evaluation order.                    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int onx, ony;        /* ON = MN / 2, exact (value + remainder) */
+    int fS_df, fS;       /* |ON|^2: double-float, and rounded */
+    int P3x, P3y, Q3x, Q3y, cQP;
+} sks_side_t;
+
+static void sks_side(tape *t, int Mx, int My, int Nx, int Ny, int Px, int Py, int Qx, int Qy, sks_side_t *o)
+{
+    o->onx = xscale(t, xsub(t, Nx, Mx), 0.5);
+    o->ony = xscale(t, xsub(t, Ny, My), 0.5);
+    const int mpx = xsub(t, Px, Mx), mpy = xsub(t, Py, My), mqx = xsub(t, Qx, Mx), mqy = xsub(t, Qy, My);
+    const int qpx = xsub(t, Px, Qx), qpy = xsub(t, Py, Qy);
+    o->fS_df = dot_x(t, o->onx, o->ony, o->onx, o->ony);
+    o->fS = rn(t, o->fS_df);
+    o->P3y = cross_x(t, o->onx, o->ony, mpx, mpy);
+    o->Q3y = cross_x(t, o->onx, o->ony, mqx, mqy);
+    o->P3x = rn(t, dfsub(t, dot_x(t, o->onx, o->ony, mpx, mpy), o->fS_df));
+    o->Q3x = rn(t, dfsub(t, dot_x(t, o->onx, o->ony, mqx, mqy), o->fS_df));
+    o->cQP = cross_x(t, o->onx, o->ony, qpx, qpy);
+}
+
+static void sks_chain(tape *t, const double *s, int H[9])
+{
+    int x[16];
+    for (int k = 0; k < 16; ++k) x[k] = in(t, s[k]);
+    sks_side_t a, b;
+    sks_side(t, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], &a);
+    sks_side(t, x[8], x[9], x[10], x[11], x[12], x[13], x[14], x[15], &b);
+    /* Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11) */
+    const int n7x = det2(t, a.Q3x, a.P3x, a.Q3y, a.P3y), n7y = mul(t, a.fS, a.cQP), d7 = mul(t, a.Q3y, a.P3y);
+    const int n8x = det2(t, b.Q3x, b.P3x, b.Q3y, b.P3y), n8y = mul(t, b.fS, b.cQP), d8 = mul(t, b.Q3y, b.P3y);
+    /* Eq. 11 */
+    const int den = mul(t, d8, mul(t, sub(t, n7x, n7y), add(t, n7x, n7y)));
+    const int aK = dv(t, mul(t, d7, det2(t, n8x, n8y, n7y, n7x)), den);
+    const int bK = dv(t, mul(t, d7, det2(t, n8y, n8x, n7y, n7x)), den);
+    /* Eq. 13 */
+    const int P5x = dv(t, a.P3x, a.P3y), P5y = dv(t, a.fS, a.P3y);
+    const int P6x = dv(t, b.P3x, b.P3y), P6y = dv(t, b.fS, b.P3y);
+    const int uK = sub(t, P6x, fma3(t, aK, P5x, mul(t, bK, P5y)));
+    const int vK = sub(t, P6y, fma3(t, bK, P5x, mul(t, aK, P5y)));
+    /* Eq. 14 in the M frames, double-float; ON rounded once where used */
+    const int o1x = rn(t, a.onx), o1y = rn(t, a.ony), o2x = rn(t, b.onx), o2y = rn(t, b.ony);
+    const int A00 = dfsub(t, dfmul(t, aK, o1x), dfmul(t, uK, o1y));
+    const int A01 = dfadd(t, dfmul(t, aK, o1y), dfmul(t, uK, o1x));
+    const int A02 = dfmul(t, bK, a.fS);
+    const int A20 = dfsub(t, dfmul(t, bK, o1x), dfmul(t, vK, o1y));
+    const int A21 = dfadd(t, dfmul(t, bK, o1y), dfmul(t, vK, o1x));
+    const int A22 = dfmul(t, aK, a.fS);
+    const int L00 = dfadd(t, dfmul(t, A00, o2x), dfmul(t, o2y, o1y));
+    const int L01 = dfsub(t, dfmul(t, A01, o2x), dfmul(t, o2y, o1x));
+    const int L02 = dfmul(t, A02, o2x);
+    const int L10 = dfsub(t, dfmul(t, A00, o2y), dfmul(t, o2x, o1y));
+    const int L11 = dfadd(t, dfmul(t, A01, o2y), dfmul(t, o2x, o1x));
+    const int L12 = dfmul(t, A02, o2y);
+    const int G02 = dfsub(t, dfsub(t, L02, dfmul(t, L00, o1x)), dfmul(t, L01, o1y));
+    const int G12 = dfsub(t, dfsub(t, L12, dfmul(t, L10, o1x)), dfmul(t, L11, o1y));
+    const int G22 = dfsub(t, dfsub(t, A22, dfmul(t, A20, o1x)), dfmul(t, A21, o1y));
+    const int j00 = rn(t, dfadd(t, L00, dfmul(t, A20, o2x))), j01 = rn(t, dfadd(t, L01, dfmul(t, A21, o2x)));
+    const int j02 = rn(t, dfadd(t, G02, dfmul(t, G22, o2x)));
+    const int j10 = rn(t, dfadd(t, L10, dfmul(t, A20, o2y))), j11 = rn(t, dfadd(t, L11, dfmul(t, A21, o2y)));
+    const int j12 = rn(t, dfadd(t, G12, dfmul(t, G22, o2y)));
+    const int j20 = rn(t, A20), j21 = rn(t, A21), j22 = rn(t, G22);
+    const int nM1x = neg(t, x[0]), nM1y = neg(t, x[1]);
+    const int K02 = fma3(t, nM1x, j00, fma3(t, nM1y, j01, j02));
+    const int K12 = fma3(t, nM1x, j10, fma3(t, nM1y, j11, j12));
+    const int K22 = fma3(t, nM1x, j20, fma3(t, nM1y, j21, j22));
+    H[0] = fma3(t, x[8], j20, j00);
+    H[1] = fma3(t, x[8], j21, j01);
+    H[2] = fma3(t, x[8], K22, K02);
+    H[3] = fma3(t, x[9], j20, j10);
+    H[4] = fma3(t, x[9], j21, j11);
+    H[5] = fma3(t, x[9], K22, K12);
+    H[6] = j20;
+    H[7] = j21;
+    H[8] = K22;
+    for (int i = 0; i < 9; ++i) H[i] = final_(t, H[i]);
+}
+
+/* Per-entry bounds E_i on |H_fp32,i - H_i| and the bound on
+ * max_i |H^_fp32,i - H^_i| at unit Frobenius norm (both normalised
+ * exactly, signs aligned): to first order H^' - H^ = (D - H^ <H^, D>) / |H|
+ * for the error D, a linear functional of the rounding events per i. */
+static double chain_bounds(const tape *t, const int H[9], double *Hv, double *He)
+{
+    double adj[TAPE_MAX], h[9], n2 = 0;
+    for (int i = 0; i < 9; ++i) {
+        h[i] = t->n[H[i]].v;
+        n2 += h[i] * h[i];
+    }
+    const double n = sqrt(n2);
+    double beta = 0;
+    for (int i = 0; i < 9; ++i) {
+        double g[9];
+        const double one = 1.0;
+        sweep(t, &H[i], &one, 1, adj);
+        if (He) He[i] = event_sum(t, adj);
+        if (Hv) Hv[i] = h[i];
+        for (int k = 0; k < 9; ++k) g[k] = ((k == i ? 1.0 : 0.0) - h[i] * h[k] / n2) / n;
+        sweep(t, H, g, 9, adj);
+        const double b = event_sum(t, adj);
+        beta = b > beta ? b : beta;
+    }
+    return beta;
+}
+
+/* Per set: the unit-Frobenius bound beta[i]; Hv / He (nullable): the exact H
+ * of the evaluation order and per-entry absolute bounds, 9 values per set. */
+void oracle_aca_fp32_bound(const double *pts, double *beta, double *Hv, double *He, int64_t n)
+{
+#pragma omp parallel
+    {
+        tape *t = (tape *)malloc(sizeof(tape));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            int H[9];
+            t->len = 0;
+            aca_chain(t, pts + 16 * i, H);
+            beta[i] = chain_bounds(t, H, Hv ? Hv + 9 * i : NULL, He ? He + 9 * i : NULL);
+        }
+        free(t);
+    }
+}
+
+void oracle_sks_fp32_bound(const double *pts, double *beta, double *Hv, double *He, int64_t n)
+{
+#pragma omp parallel
+    {
+        tape *t = (tape *)malloc(sizeof(tape));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            int H[9];
+            t->len = 0;
+            sks_chain(t, pts + 16 * i, H);
+            beta[i] = chain_bounds(t, H, Hv ? Hv + 9 * i : NULL, He ? He + 9 * i : NULL);
+        }
+        free(t);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* The RANSAC inlier test (forward transfer error, Sec. 6.2) in its     */
+/* threshold-folded FP32 form:                                          */
+/*   G = (-h11, -h12, -h13, -h21, -h22, -h23, RN(t h31), RN(t h32),     */
+/*        RN(t h33)),  (Xs, Ys) = (RN(X RN(1/t)), RN(Y RN(1/t))),       */
+/*   w' = fma(G6, x, fma(G7, y, G8)), -u = fma(G0, x, fma(G1, y, G2)),  */
+/*   -v likewise, du = fma(Xs, w', -u), dv = fma(Ys, w', -v),           */
+/*   e = fma(du, du, fma(dv, dv, RN(w' (-w')))),                        */
+/* whose exact value is E = (X w - u)^2 + (Y w - v)^2 - t^2 w^2         */
+/* = w^2 (r^2 - t^2), r the forward transfer error of the exact H.  The  */
+/* hypothesis H is itself the FP32 ACA result, so the bound counts the   */
+/* rounding events of its solve as well (exact power-of-two scalings of  */
+/* H change neither the sign of E nor the ratio of E to its bound).  A   */
+/* point is decided alike by the FP32 test and the exact one whenever    */
+/* |E| exceeds the bound.                                               */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    tape *t;
+    int H[9];
+    int nev;          /* rounding events of the solve */
+    int *ev;          /* their tape indices */
+    double *J;        /* [9][nev]: dH_k / d(event node) */
+} hyp_model;
+
+static void hyp_model_init(hyp_model *h, const double *s16)
+{
+    h->t = (tape *)malloc(sizeof(tape));
+    h->t->len = 0;
+    aca_chain(h->t, s16, h->H);
+    tape *t = h->t;
+    h->ev = (int *)malloc(sizeof(int) * (size_t)t->len);
+    h->nev = 0;
+    for (int k = 0; k < t->len; ++k)
+        if (t->n[k].C > 0) h->ev[h->nev++] = k;
+    h->J = (double *)malloc(sizeof(double) * 9 * (size_t)(h->nev > 0 ? h->nev : 1));
+    double adj[TAPE_MAX];
+    for (int i = 0; i < 9; ++i) {
+        const double one = 1.0;
+        sweep(t, &h->H[i], &one, 1, adj);
+        for (int j = 0; j < h->nev; ++j) h->J[i * h->nev + j] = adj[h->ev[j]];
+    }
+}
+
+static void hyp_model_free(hyp_model *h)
+{
+    free(h->J);
+    free(h->ev);
+    free(h->t);
+}
+
+/* The test's quantities at point c under hypothesis h, on a small tape whose
+ * inputs are the nine entries of H.  e = du^2 + dv^2 - w'^2 is quadratic in
+ * du, dv, w', whose exact values vanish together at points that H maps
+ * exactly (du = dv = 0) near its vanishing line (w' -> 0): there E itself
+ * is of second order, and so are the squares of the errors of du, dv, w'.
+ * The bound therefore is
+ *   B = B1(e) + B(du)^2 + B(dv)^2 + B(w')^2,
+ * B1(e) the first-order bound of e and B(q) those of du, dv, w' (the
+ * remaining second-order products are of relative size u against B1). */
+typedef struct {
+    double E;
+    double crude;     /* upper bound of the exact B (per-entry bounds of H) */
+    double own[4];    /* u sum |adj| C over the test's own events: e, du, dv, w' */
+    double g[4][9];   /* d(e, du, dv, w') / dH_k */
+} test_parts;
+
+static void test_parts_of(const hyp_model *h, const double *Eh, double thr, const float *c, test_parts *o)
+{
+    tape tt;
+    tape *t = &tt;
+    t->len = 0;
+    int Hn[9];
+    for (int k = 0; k < 9; ++k) Hn[k] = in(t, h->t->n[h->H[k]].v);
+    const int x = in(t, c[0]), y = in(t, c[1]), X = in(t, c[2]), Y = in(t, c[3]), T = in(t, thr);
+    const int rt = dv(t, in(t, 1.0), T);
+    const int Xs = mul(t, X, rt), Ys = mul(t, Y, rt);
+    const int w = fma3(t, mul(t, T, Hn[6]), x, fma3(t, mul(t, T, Hn[7]), y, mul(t, T, Hn[8])));
+    const int nu = fma3(t, neg(t, Hn[0]), x, fma3(t, neg(t, Hn[1]), y, neg(t, Hn[2])));
+    const int nv = fma3(t, neg(t, Hn[3]), x, fma3(t, neg(t, Hn[4]), y, neg(t, Hn[5])));
+    const int du = fma3(t, Xs, w, nu), dvv = fma3(t, Ys, w, nv);
+    const int e = final_(t, fma3(t, du, du, fma3(t, dvv, dvv, mul(t, w, neg(t, w)))));
+    o->E = V(e);
+    const int tgt[4] = {e, du, dvv, w};
+    double adj[64], cr[4];
+    for (int q = 0; q < 4; ++q) {
+        const double one = 1.0;
+        sweep(t, &tgt[q], &one, 1, adj);
+        o->own[q] = event_sum(t, adj);
+        cr[q] = o->own[q];
+        for (int k = 0; k < 9; ++k) {
+            o->g[q][k] = adj[Hn[k]];
+            cr[q] += fabs(adj[Hn[k]]) * Eh[k];
+        }
+    }
+    o->crude = cr[0] + cr[1] * cr[1] + cr[2] * cr[2] + cr[3] * cr[3];
+}
+
+/* the exact first-order sums with the solve's events, completed as above */
+static double test_exact_bound(const hyp_model *h, const test_parts *o)
+{
+    double b[4];
+    for (int q = 0; q < 4; ++q) {
+        double s = 0;
+        for (int j = 0; j < h->nev; ++j) {
+            double d = 0;
+            for (int k = 0; k < 9; ++k) d += o->g[q][k] * h->J[k * h->nev + j];
+            s += fabs(d) * h->t->n[h->ev[j]].C;
+        }
+        b[q] = o->own[q] + U * s;
+    }
+    return b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
+}
+
+/* per-entry bounds of H (the crude filter's input) */
+static void entry_bounds(const hyp_model *h, double *Eh)
+{
+    for (int k = 0; k < 9; ++k) {
+        double e = 0;
+        for (int j = 0; j < h->nev; ++j) e += fabs(h->J[k * h->nev + j]) * h->t->n[h->ev[j]].C;
+        Eh[k] = U * e;
+    }
+}
+
+/* bound on |fl(e) - E| for point c under hypothesis h; *E = exact value */
+static double test_bound(const hyp_model *h, double thr, const float *c, double *E)
+{
+    double Eh[9];
+    entry_bounds(h, Eh);
+    test_parts o;
+    test_parts_of(h, Eh, thr, c, &o);
+    *E = o.E;
+    return test_exact_bound(h, &o);
+}
+
+/* Ambiguity of one point under one hypothesis model: 1 if the FP32 test may
+ * decide it otherwise than the exact test.  The bound is first computed
+ * with the per-entry bounds of H (an upper bound of the exact sum); only
+ * points that this cheaper bound cannot decide get the exact sum. */
+static int point_ambiguous(const hyp_model *h, const double *Eh, double thr, const float *c)
+{
+    test_parts o;
+    test_parts_of(h, Eh, thr, c, &o);
+    if (!isfinite(o.E)) return 1;
+    if (fabs(o.E) > o.crude) return 0;
+    return !(fabs(o.E) > test_exact_bound(h, &o));
+}
+#undef V
+#undef M
+
+/* Opaque per-hypothesis model for the brute-force scorer in oracle.c. */
+typedef struct {
+    hyp_model h;
+    double Eh[9];
+} test_model;
+
+void *oracle_fp32_test_model_new(const double *s16)
+{
+    test_model *m = (test_model *)malloc(sizeof(test_model));
+    hyp_model_init(&m->h, s16);
+    entry_bounds(&m->h, m->Eh);
+    return m;
+}
+
+int oracle_fp32_test_ambiguous(const void *model, double thr, const float *c)
+{
+    const test_model *m = (const test_model *)model;
+    return point_ambiguous(&m->h, m->Eh, thr, c);
+}
+
+void oracle_fp32_test_model_free(void *model)
+{
+    test_model *m = (test_model *)model;
+    hyp_model_free(&m->h);
+    free(m);
+}
+
+/* Scoring band of one hypothesis over N points: amb[i] = 1 if the FP32 test
+ * may decide point i otherwise than the exact test (|E| <= its bound, or E
+ * not finite) or if its exact residual lies within band_px of the threshold
+ * (|r - t| < band_px, the stated count tolerance), else 0.  s16 is the hypothesis's
+ * minimal set (16 FP32 coordinates as doubles).  Returns the number of
+ * ambiguous points. */
+int64_t oracle_score_band(const double *s16, const float *corr, int64_t N, double thr, double band_px,
+                          uint8_t *amb)
+{
+    hyp_model h;
+    hyp_model_init(&h, s16);
+    const tape *t = h.t;
+    double Hv[9];
+    for (int k = 0; k < 9; ++k) Hv[k] = t->n[h.H[k]].v;
+    int64_t nb = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        const float *c = corr + 4 * i;
+        double E;
+        const double B = test_bound(&h, thr, c, &E);
+        int a = !(fabs(E) > B);
+        if (!a && band_px > 0) {
+            const double x = c[0], y = c[1];
+            const double u = Hv[0] * x + Hv[1] * y + Hv[2];
+            const double v = Hv[3] * x + Hv[4] * y + Hv[5];
+            const double w = Hv[6] * x + Hv[7] * y + Hv[8];
+            const double r = hypot(c[2] - u / w, c[3] - v / w);
+            a = !(fabs(r - thr) >= band_px);
+        }
+        amb[i] = (uint8_t)a;
+        nb += a;
+    }
+    hyp_model_free(&h);
+    return nb;
+}
+
+/* The FP32 test's bound alone at each point, in pixels of |r - t|:
+ * B / (w^2 (r + t)), with w, r from the exact H. */
+void oracle_score_band_px(const double *s16, const float *corr, int64_t N, double thr, double *px)
+{
+    hyp_model h;
+    hyp_model_init(&h, s16);
+    double Hv[9];
+    for (int k = 0; k < 9; ++k) Hv[k] = h.t->n[h.H[k]].v;
+    for (int64_t i = 0; i < N; ++i) {
+        const float *c = corr + 4 * i;
+        double E;
+        const double B = test_bound(&h, thr, c, &E);
+        const double x = c[0], y = c[1];
+        const double u = Hv[0] * x + Hv[1] * y + Hv[2];
+        const double v = Hv[3] * x + Hv[4] * y + Hv[5];
+        const double w = Hv[6] * x + Hv[7] * y + Hv[8];
+        const double r = hypot(c[2] - u / w, c[3] - v / w);
+        px[i] = B / (w * w * (r + thr));
+    }
+    hyp_model_free(&h);
+}
+
+/* ------------------------------------------------------------------ */
+/* Hooks for the pins of the rules above (tests only).                  */
+/* ------------------------------------------------------------------ */
+/* Bound of one rule on FP32 operands a[0..3]: op 0 = a0 + a1, 1 = a0 * a1,
+ * 2 = fma(a0, a1, a2), 3 = a0 / a1, 4 = Kahan's a0 a3 - a1 a2, 5 = the
+ * cross product of the exact differences (a0 - a1, a2 - a3) and
+ * (a4 - a5, a6 - a7) (8 operands), 6 = the double-float product
+ * (a0 a1) a2 (TwoProduct, then a double-float times FP32 product) rounded
+ * once.  *v = exact value, returns the bound on |fl - v|. */
+double oracle_fp32_rule_bound(int op, const double *a, double *v)
+{
+    tape tt;
+    tape *t = &tt;
+    t->len = 0;
+    int x[8];
+    for (int k = 0; k < 8; ++k) x[k] = in(t, a[k]);
+    int r;
+    switch (op) {
+    case 0: r = add(t, x[0], x[1]); break;
+    case 1: r = mul(t, x[0], x[1]); break;
+    case 2: r = fma3(t, x[0], x[1], x[2]); break;
+    case 3: r = dv(t, x[0], x[1]); break;
+    case 4: r = det2(t, x[0], x[1], x[2], x[3]); break;
+    case 5: r = cross_x(t, xsub(t, x[0], x[1]), xsub(t, x[2], x[3]), xsub(t, x[4], x[5]), xsub(t, x[6], x[7])); break;
+    default: r = rn(t, dfmul(t, dfmul(t, x[0], x[1]), x[2])); break;
+    }
+    *v = t->n[r].v;
+    double adj[TAPE_MAX];
+    const double one = 1.0;
+    sweep(t, &r, &one, 1, adj);
+    return event_sum(t, adj);
+}
+
+/* Per point of one hypothesis: the exact E of the inlier test and the
+ * bound on |fl(e) - E| (the FP32 evaluation, solve included). */
+void oracle_score_bound_E(const double *s16, const float *corr, int64_t N, double thr, double *E, double *B)
+{
+    hyp_model h;
+    hyp_model_init(&h, s16);
+    for (int64_t i = 0; i < N; ++i) B[i] = test_bound(&h, thr, corr + 4 * i, &E[i]);
+    hyp_model_free(&h);
+}

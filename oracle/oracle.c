@@ -693,46 +693,30 @@ static int score_point(const double *H, const float *c, double thr, double *marg
     return r <= thr;
 }
 
-/* Ambiguity band of the RANSAC count parity.  An FP32 solver returns, at
- * best, the exact H of inputs perturbed by about one FP32 rounding (the
- * backward-stability reading of the solver gate, herr * 2^-24 relative per
- * coordinate).  The band of point i under hypothesis h is therefore
- * band_px + 2 * max_t |r_i(H_t) - r_i(H)| over BAND_TRIALS re-solves H_t of
- * the minimal set with every coordinate scaled by (1 +- herr 2^-24), signs
- * from a fixed hash of (h, t, coordinate).  A point whose exact residual is
- * closer to the threshold than its band may legitimately be counted either
- * way by an FP32 implementation. */
-#define BAND_TRIALS 6
-
-static double residual_of(const double *H, const float *c)
-{
-    const double x = c[0], y = c[1];
-    const double u = H[0] * x + H[1] * y + H[2];
-    const double v = H[3] * x + H[4] * y + H[5];
-    const double w = H[6] * x + H[7] * y + H[8];
-    if (w == 0) return INFINITY;
-    return hypot(c[2] - u / w, c[3] - v / w);
-}
-
-static uint32_t mix32(uint32_t x)
-{
-    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
-    return x;
-}
+/* Ambiguity band of the RANSAC count parity.  The stated tolerance is that
+ * counts are exact except for points within band_px of the threshold.  An
+ * FP32 implementation also meets points whose decision its own rounding can
+ * flip: fp32_bounds.c bounds, to first order, the rounding error of the
+ * library's FP32 evaluation of the test (its hypothesis solve included) at
+ * each point, and a point whose exact E = w^2 (r^2 - thr^2) lies within
+ * that bound is ambiguous too.  amb_in / amb_out count the ambiguous points
+ * that the exact test takes as inliers / outliers, so an FP32 count c must
+ * satisfy counts[h] - amb_in[h] <= c <= counts[h] + amb_out[h]. */
+void *oracle_fp32_test_model_new(const double *s16);
+int oracle_fp32_test_ambiguous(const void *model, double thr, const float *c);
+void oracle_fp32_test_model_free(void *model);
 
 /* Per-hypothesis inlier counts for one problem (N correspondences).
- * counts[h] = -1 for degenerate samples; band[h] (nullable) = number of
- * points whose exact residual lies within the ambiguity band of the
- * threshold (band_px alone when herr = 0, see the comment above
- * BAND_TRIALS). */
+ * counts[h] = -1 for degenerate samples; amb_in / amb_out (nullable, both or
+ * neither) as described above. */
 void oracle_score_problem(const float *corr, int64_t N, int32_t n_hyp, double thr, uint64_t seed,
-                          uint32_t prob, int32_t *counts, int32_t *band, double band_px, double herr)
+                          uint32_t prob, int32_t *counts, int32_t *amb_in, int32_t *amb_out, double band_px)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int32_t h = 0; h < n_hyp; ++h) {
         if (N < 4) {
             counts[h] = -1;
-            if (band) band[h] = 0;
+            if (amb_in) amb_in[h] = amb_out[h] = 0;
             continue;
         }
         int64_t idx[4];
@@ -747,50 +731,46 @@ void oracle_score_problem(const float *corr, int64_t N, int32_t n_hyp, double th
         }
         if (oracle_sample_degenerate(s)) {
             counts[h] = -1;
-            if (band) band[h] = 0;
+            if (amb_in) amb_in[h] = amb_out[h] = 0;
             continue;
         }
         double H[9];
         aca_one(s, H);
-        double Ht[BAND_TRIALS][9];
-        const int trials = (band && herr > 0) ? BAND_TRIALS : 0;
-        for (int t = 0; t < trials; ++t) {
-            double sp[16];
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t bit = mix32((uint32_t)h * 2654435761u ^ (uint32_t)(t * 16 + k) * 0x9E3779B9u ^ prob) & 1u;
-                sp[k] = s[k] * (1.0 + (bit ? 1.0 : -1.0) * herr * ldexp(1.0, -24));
-            }
-            aca_one(sp, Ht[t]);
-        }
-        int32_t cnt = 0, nb = 0;
+        void *model = amb_in ? oracle_fp32_test_model_new(s) : NULL;
+        int32_t cnt = 0, ni = 0, no = 0;
         for (int64_t i = 0; i < N; ++i) {
             double m;
-            cnt += score_point(H, corr + 4 * i, thr, &m);
-            if (band) {
-                double move = 0;
-                const double r0 = residual_of(H, corr + 4 * i);
-                for (int t = 0; t < trials; ++t) {
-                    const double d = fabs(residual_of(Ht[t], corr + 4 * i) - r0);
-                    move = d > move ? d : move;
+            const int inl = score_point(H, corr + 4 * i, thr, &m);
+            cnt += inl;
+            if (model) {
+                /* NaN margin (w = 0 or a non-finite point) counts as ambiguous */
+                const int amb = !(fabs(m) >= band_px) || oracle_fp32_test_ambiguous(model, thr, corr + 4 * i);
+                if (amb) {
+                    if (inl) ++ni;
+                    else ++no;
                 }
-                if (!(fabs(m) >= band_px + 2.0 * move)) ++nb;   /* NaN (w = 0 or inf - inf) counts as ambiguous */
             }
         }
         counts[h] = cnt;
-        if (band) band[h] = nb;
+        if (model) {
+            amb_in[h] = ni;
+            amb_out[h] = no;
+            oracle_fp32_test_model_free(model);
+        }
     }
 }
 
 /* Full RANSAC over P problems (CSR offsets in points, n_hyp[p] hypotheses
  * each).  Best = highest count, ties to the lowest hypothesis index;
  * best_H unit-Frobenius sign-fixed; best_hyp = -1 and best_count = 0 when
- * every sample is degenerate.  hyp_counts / band_counts (nullable) are laid
- * out problem after problem (prefix sums of n_hyp).  inlier_mask (nullable)
+ * every sample is degenerate.  hyp_counts (nullable) is laid
+ * out problem after problem (prefix sums of n_hyp); so are amb_in / amb_out
+ * (nullable, both or neither; see oracle_score_problem).  inlier_mask (nullable)
  * marks the best hypothesis's inliers. */
 void oracle_ransac(const float *corr, const int64_t *offsets, const int32_t *n_hyp, int32_t P, double thr,
                    uint64_t seed, uint32_t problem_base, double *best_H, int32_t *best_count,
-                   int32_t *best_hyp, int32_t *hyp_counts, int32_t *band_counts, double band_px,
-                   double herr, uint8_t *inlier_mask)
+                   int32_t *best_hyp, int32_t *hyp_counts, int32_t *amb_in, int32_t *amb_out, double band_px,
+                   uint8_t *inlier_mask)
 {
     int64_t hoff = 0;
     for (int32_t p = 0; p < P; ++p) {
@@ -798,8 +778,8 @@ void oracle_ransac(const float *corr, const int64_t *offsets, const int32_t *n_h
         const float *c = corr + 4 * offsets[p];
         const int32_t k = n_hyp[p];
         int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * (k > 0 ? k : 1));
-        int32_t *bnd = band_counts ? band_counts + hoff : NULL;
-        oracle_score_problem(c, N, k, thr, seed, problem_base + (uint32_t)p, cnt, bnd, band_px, herr);
+        oracle_score_problem(c, N, k, thr, seed, problem_base + (uint32_t)p, cnt, amb_in ? amb_in + hoff : NULL,
+                             amb_in ? amb_out + hoff : NULL, band_px);
         int32_t bh = -1, bc = -1;
         for (int32_t h = 0; h < k; ++h)
             if (cnt[h] > bc) {
@@ -878,13 +858,13 @@ int32_t oracle_adaptive_stop(const int32_t *cnt, int32_t k, int64_t N, double lo
 }
 
 /* RANSAC with the online stop: every problem scores its cap max_hyp[p]
- * hypotheses (hyp_counts / band_counts as in oracle_ransac, all of them),
+ * hypotheses (hyp_counts / amb_in / amb_out as in oracle_ransac, all of them),
  * n_eval[p] = the stop index, and the best is the argmax over the evaluated
  * hypotheses only (ties to the lowest index). */
 void oracle_ransac_adaptive(const float *corr, const int64_t *offsets, const int32_t *max_hyp, int32_t P, double thr,
                             uint64_t seed, uint32_t problem_base, double confidence, double *best_H,
                             int32_t *best_count, int32_t *best_hyp, int32_t *n_eval, int32_t *hyp_counts,
-                            int32_t *band_counts, double band_px, double herr, uint8_t *inlier_mask)
+                            int32_t *amb_in, int32_t *amb_out, double band_px, uint8_t *inlier_mask)
 {
     const double log_fail = log(1.0 - confidence);
     int64_t hoff = 0;
@@ -893,8 +873,8 @@ void oracle_ransac_adaptive(const float *corr, const int64_t *offsets, const int
         const float *c = corr + 4 * offsets[p];
         const int32_t k = max_hyp[p];
         int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * (k > 0 ? k : 1));
-        int32_t *bnd = band_counts ? band_counts + hoff : NULL;
-        oracle_score_problem(c, N, k, thr, seed, problem_base + (uint32_t)p, cnt, bnd, band_px, herr);
+        oracle_score_problem(c, N, k, thr, seed, problem_base + (uint32_t)p, cnt, amb_in ? amb_in + hoff : NULL,
+                             amb_in ? amb_out + hoff : NULL, band_px);
         const int32_t ne = N >= 4 && k > 0 ? oracle_adaptive_stop(cnt, k, N, log_fail) : 0;
         int32_t bh = -1, bc = -1;
         for (int32_t h = 0; h < ne; ++h)

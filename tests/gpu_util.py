@@ -3,30 +3,27 @@ import numpy as np
 import torch
 
 # FP32 gate on the homography, relative to |H|_F with both sides scaled to
-# unit Frobenius norm and the GPU sign aligned to the oracle's.
+# unit Frobenius norm and the GPU sign aligned to the oracle's: the stated
+# tolerance 1e-4, widened on a set only where the oracle's first-order bound
+# beta on the rounding error of the library's FP32 evaluation order
+# (oracle/fp32_bounds.c: every rounding event of that order, each bounded by
+# a published rule) exceeds it.  beta is derived from the arithmetic, not
+# calibrated; beta^2 allows for the neglected second-order terms.
 H_TOL = 1e-4
-# A set is well-conditioned for FP32 when perturbing its 16 input coordinates
-# by one FP32 rounding (relative 2^-24) moves the unit-Frobenius H by at most
-# H_TOL / KAPPA_C to first order (kappa * u <= 6.25e-6, kappa from the
-# oracle).  Well-conditioned sets must meet H_TOL; every other unflagged set
-# must meet max(H_TOL, KAPPA_C * kappa * u), a backward-stability bound: the
-# FP32 result is as close as FP32 rounding of the inputs alone permits.
-KAPPA_C = 16.0
-U32 = 2.0 ** -24
 
 
-def kappa_gate(err, kappa, label=""):
-    """Assert the FP32 gate above; returns a summary dict."""
-    import oracle  # noqa: F401
-    ku = np.asarray(kappa) * U32
-    well = KAPPA_C * ku <= H_TOL
-    bound = np.maximum(H_TOL, KAPPA_C * ku)
-    summary = dict(n=int(err.size), well_conditioned=int(well.sum()),
-                   max_err_well=float(err[well].max()) if well.any() else 0.0,
+def bound_gate(err, beta, label=""):
+    """Assert err <= max(H_TOL, beta + beta^2) per set; returns a summary."""
+    err = np.asarray(err, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    bound = np.maximum(H_TOL, beta + beta * beta)
+    within = beta <= H_TOL
+    summary = dict(n=int(err.size), bound_below_tol=int(within.sum()),
+                   max_err_bound_below_tol=float(err[within].max()) if within.any() else 0.0,
                    max_err_all=float(err.max()), n_above_1e4=int((err > H_TOL).sum()),
+                   max_err_over_beta=float(np.max(err / np.maximum(beta, 1e-300))),
                    worst_ratio=float(np.max(err / bound)))
     print(label, summary)
-    assert summary["max_err_well"] <= H_TOL, summary
     assert np.all(err <= bound), summary
     return summary
 

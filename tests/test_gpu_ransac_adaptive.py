@@ -17,7 +17,7 @@ import workloads
 from paper_2402_18008_gb300 import _lib, api
 from paper_2402_18008_gb300._lib import AcaError
 from tests.gpu_util import cuda
-from tests.test_gpu_ransac import BAND_PX, HERR, _count_gate, _sample_kappa_u
+from tests.test_gpu_ransac import BAND_PX, _count_gate
 
 pytestmark = pytest.mark.gpu
 CONF = 0.99
@@ -31,18 +31,19 @@ def _run(corr, offsets, caps, thr, seed, **kw):
     return {k: (None if v is None else v.cpu().numpy()) for k, v in r.__dict__.items()}
 
 
-def _check_problem(g, o, hoff, k, N, p, ku, label):
+def _check_problem(g, o, hoff, k, N, p, label):
     ne = int(g["n_evaluated"][p])
     gc = g["hyp_counts"][hoff:hoff + k]
     oc = o["hyp_counts"][hoff:hoff + k]
-    band = o["band_counts"][hoff:hoff + k]
-    lo = oracle.adaptive_stop(oc + band, N, CONF)
-    hi = oracle.adaptive_stop(np.where(oc < 0, oc, np.maximum(oc - band, 0)), N, CONF)
+    bi = o["band_in"][hoff:hoff + k]
+    bo = o["band_out"][hoff:hoff + k]
+    lo = oracle.adaptive_stop(np.where(oc < 0, oc, oc + bo), N, CONF)
+    hi = oracle.adaptive_stop(np.where(oc < 0, oc, np.maximum(oc - bi, 0)), N, CONF)
     assert lo <= ne <= hi, (label, p, lo, ne, hi, int(o["n_eval"][p]))
     assert np.all(gc[ne:] == -2)
     m = min(ne, int(o["n_eval"][p]))
-    _count_gate(gc[:m], oc[:m], band[:m], ku[hoff:hoff + m], f"{label} p={p}")
-    if not band[:max(ne, int(o["n_eval"][p]))].any():
+    _count_gate(gc[:m], oc[:m], bi[:m], bo[:m], f"{label} p={p}")
+    if not (bi + bo)[:max(ne, int(o["n_eval"][p]))].any():
         assert ne == o["n_eval"][p] and g["best_hyp"][p] == o["best_hyp"][p]
     # the best is the argmax of the evaluated counts, ties to the lowest index
     ev = gc[:ne]
@@ -57,9 +58,8 @@ def test_adaptive_one_pair_matches_the_sequential_loop():
     rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=0)
     thr, seed, cap = 3.0, 2024, 4096
     g = _run(rp.corr, [0, 2000], [cap], thr, seed)
-    o = oracle.ransac_adaptive(rp.corr, [0, 2000], [cap], thr, seed, CONF, band_px=BAND_PX, herr=HERR)
-    ku = _sample_kappa_u(rp.corr, [0, 2000], [cap], seed)
-    ne = _check_problem(g, o, 0, cap, 2000, 0, ku, "one pair")
+    o = oracle.ransac_adaptive(rp.corr, [0, 2000], [cap], thr, seed, CONF, band_px=BAND_PX)
+    ne = _check_problem(g, o, 0, cap, 2000, 0, "one pair")
     print(f"one pair: stopped after {ne} of {cap} hypotheses (oracle {int(o['n_eval'][0])})")
     assert ne < cap
 
@@ -68,12 +68,11 @@ def test_adaptive_batched_uneven_matches_the_oracle():
     rb = workloads.ransac_batch(P=24, seed=6, n_max=3000)
     caps = np.full(24, 2048, np.int32)
     g = _run(rb.corr, rb.offsets, caps, 3.0, 99)
-    o = oracle.ransac_adaptive(rb.corr, rb.offsets, caps, 3.0, 99, CONF, band_px=BAND_PX, herr=HERR)
-    ku = _sample_kappa_u(rb.corr, rb.offsets, caps, 99)
+    o = oracle.ransac_adaptive(rb.corr, rb.offsets, caps, 3.0, 99, CONF, band_px=BAND_PX)
     nes = []
     for p in range(24):
         N = int(rb.offsets[p + 1] - rb.offsets[p])
-        nes.append(_check_problem(g, o, 2048 * p, 2048, N, p, ku, "batched 24"))
+        nes.append(_check_problem(g, o, 2048 * p, 2048, N, p, "batched 24"))
     print("batched 24: evaluated", nes)
 
 
@@ -118,7 +117,7 @@ def test_adaptive_edge_cases_and_graph_replay():
     offsets = np.array([0, 3, 303, 303, 803], np.int64)         # N = 3, 300, 0, 500
     caps = np.array([64, 300, 10, 2000], np.int32)
     g = _run(corr, offsets, caps, 3.0, 3)
-    o = oracle.ransac_adaptive(corr, offsets, caps, 3.0, 3, CONF, band_px=BAND_PX, herr=HERR)
+    o = oracle.ransac_adaptive(corr, offsets, caps, 3.0, 3, CONF, band_px=BAND_PX)
     assert list(g["n_evaluated"][:3]) == [0, 300, 0]
     assert g["best_hyp"][0] == -1 and g["best_hyp"][2] == -1
     assert np.all(g["hyp_counts"][:64] == -1) and np.all(g["hyp_counts"][364:374] == -1)
@@ -163,15 +162,10 @@ def test_adaptive_full_size_512_pairs_sampled_against_the_oracle():
     for p in np.random.default_rng(3).choice(512, 8, replace=False):
         a, b = int(rb.offsets[p]), int(rb.offsets[p + 1])
         o = oracle.ransac_adaptive(rb.corr[a:b], [0, b - a], [16384], 3.0, 0, CONF, problem_base=int(p),
-                                   band_px=BAND_PX, herr=HERR)
-        gp = {k: (v[p:p + 1] if k in ("n_evaluated", "best_hyp", "best_count") else v) for k, v in g.items()}
+                                   band_px=BAND_PX)
+        gp = dict(g)
+        gp["n_evaluated"] = g["n_evaluated"][p:p + 1]
+        gp["best_hyp"] = g["best_hyp"][p:p + 1]
+        gp["best_count"] = g["best_count"][p:p + 1]
         gp["hyp_counts"] = g["hyp_counts"][16384 * p:16384 * (p + 1)]
-        n = int(ne[p])
-        lo = oracle.adaptive_stop(o["hyp_counts"] + o["band_counts"], b - a, CONF)
-        hi = oracle.adaptive_stop(np.where(o["hyp_counts"] < 0, o["hyp_counts"],
-                                           np.maximum(o["hyp_counts"] - o["band_counts"], 0)), b - a, CONF)
-        assert lo <= n <= hi, (p, lo, n, hi)
-        m = min(n, int(o["n_eval"][0]))
-        d = np.abs(gp["hyp_counts"][:m] - o["hyp_counts"][:m])
-        assert np.all(d <= o["band_counts"][:m]), p
-        assert np.all(gp["hyp_counts"][n:] == -2)
+        _check_problem(gp, o, 0, 16384, b - a, 0, f"512 pairs, pair {p}")

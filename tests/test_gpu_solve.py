@@ -9,7 +9,7 @@ import torch
 import oracle
 import workloads
 from paper_2402_18008_gb300 import _lib, api
-from tests.gpu_util import H_TOL, cuda, kappa_gate, planes_to_rows, unit_aligned_err
+from tests.gpu_util import H_TOL, bound_gate, cuda, planes_to_rows, unit_aligned_err
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def test_aca_ragged_sizes_and_untouched_tail(n, ld):
     ms = workloads.minimal_sets(n, seed=5)
     H, _ = _solve(ms.pts, n, ld)
     err = unit_aligned_err(planes_to_rows(H, n), oracle.aca(ms.pts))
-    kappa_gate(err, oracle.aca_condition(ms.pts), f"ragged n={n} ld={ld}")
+    bound_gate(err, oracle.aca_fp32_bound(ms.pts), f"ragged n={n} ld={ld}")
     if ld > n:
         assert torch.all(H[:, n:] == 12345.0)
 
@@ -65,14 +65,14 @@ def test_full_size_workload_sampled_against_oracle():
     err = unit_aligned_err(H[:, idx].cpu().numpy().T, oracle.aca(sub))
     f = fl.cpu().numpy()[idx]
     ok = (f & 7) == 0
-    kap = oracle.aca_condition(sub)
-    kappa_gate(err[ok], kap[ok], "full size 2^26 (sample 2^16)")
+    beta = oracle.aca_fp32_bound(sub)
+    bound_gate(err[ok], beta[ok], "full size 2^26 (sample 2^16)")
     print(f"flagged in sample: {int((~ok).sum())}, their max err {err[~ok].max():.3e}")
     # SKS on the same sets (sks_solve row of the benchmark)
     _lib.sks_solve(pts, H, None, n=n)
     torch.cuda.synchronize()
     err_s = unit_aligned_err(H[:, idx].cpu().numpy().T, oracle.sks(sub))
-    kappa_gate(err_s[ok], kap[ok], "sks full size 2^26 (sample 2^16)")
+    bound_gate(err_s[ok], oracle.sks_fp32_bound(sub)[ok], "sks full size 2^26 (sample 2^16)")
 
 
 @pytest.mark.parametrize("solver", ["aca", "sks"])
@@ -149,7 +149,7 @@ def test_sks_config0_parity():
     err = unit_aligned_err(planes_to_rows(H, 4096), oracle.sks(ms.pts))
     print(f"sks config0: max {err.max():.3e} median {np.median(err):.3e} >1e-4: {(err > 1e-4).sum()}")
     assert np.median(err) < 1e-6
-    kappa_gate(err, oracle.aca_condition(ms.pts), "sks config0")
+    bound_gate(err, oracle.sks_fp32_bound(ms.pts), "sks config0")
 
 
 @pytest.mark.parametrize("n,ld", [(3, 3), (5, 8), (1023, 1024), (1023, 1023)])
@@ -157,7 +157,7 @@ def test_sks_ragged_sizes_and_untouched_tail(n, ld):
     ms = workloads.minimal_sets(n, seed=5)
     H, _ = _solve(ms.pts, n, ld, solver="sks")
     err = unit_aligned_err(planes_to_rows(H, n), oracle.sks(ms.pts))
-    kappa_gate(err, oracle.aca_condition(ms.pts), f"sks ragged n={n} ld={ld}")
+    bound_gate(err, oracle.sks_fp32_bound(ms.pts), f"sks ragged n={n} ld={ld}")
     if ld > n:
         assert torch.all(H[:, n:] == 12345.0)
 
@@ -276,7 +276,7 @@ def test_solve_on_pinned_host_buffers_matches_device_buffers(n):
 def test_all_24_correspondence_orders_of_a_rectangle_source(solver):
     # a rectangle source in every one of the 24 orders of its corners (the
     # orders for which a pivot-free elimination divides by zero included):
-    # the same homography each time, within the conditioning gate
+    # the same homography each time, within the FP32 bound gate
     import itertools
     rb = workloads.rect_batch(64, seed=21)
     x0, y0, w, r = rb.rect
@@ -292,9 +292,11 @@ def test_all_24_correspondence_orders_of_a_rectangle_source(solver):
     torch.cuda.synchronize()
     g = planes_to_rows(H, S.shape[1])
     ref = oracle.aca(S)
-    kappa_gate(unit_aligned_err(g, ref), oracle.aca_condition(S), f"{solver} 24 orders")
+    beta = (oracle.aca_fp32_bound if solver == "aca" else oracle.sks_fp32_bound)(S)
+    bound_gate(unit_aligned_err(g, ref), beta, f"{solver} 24 orders")
+    # every order against the first order's H (the same map up to scale)
     per = unit_aligned_err(g.reshape(24, 64, 9).reshape(-1, 9), np.tile(ref[:64], (24, 1)))
-    assert per.max() < 2e-4
+    bound_gate(per, beta, f"{solver} 24 orders against order 0")
 
 
 def test_solve_beyond_32_bit_offsets():
@@ -321,6 +323,6 @@ def test_solve_beyond_32_bit_offsets():
     idx = np.random.default_rng(4).choice(m, 4096, replace=False)
     g = first[:, torch.from_numpy(idx).cuda()].cpu().numpy().T.astype(np.float64)
     sub = ms.pts[:, idx]
-    kappa_gate(unit_aligned_err(g, oracle.aca(sub)), oracle.aca_condition(sub), "2^30 + 3 sets")
+    bound_gate(unit_aligned_err(g, oracle.aca(sub)), oracle.aca_fp32_bound(sub), "2^30 + 3 sets")
     del pts, H
     torch.cuda.empty_cache()

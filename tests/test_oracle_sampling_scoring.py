@@ -114,7 +114,7 @@ def test_adaptive_count_reproduces_the_papers_sample_numbers():
 
 def test_noise_free_inlier_hypotheses_count_all_inliers():
     rp = workloads.ransac_problem(300, 0.6, 0.0, seed=5)
-    cnt, band = oracle.score_problem(rp.corr, 400, 1.0, seed=11)
+    cnt, _, _ = oracle.score_problem(rp.corr, 400, 1.0, seed=11)
     n_in = int(rp.is_inlier.sum())
     for h in range(400):
         idx = oracle.sample4(11, 0, h, 300)
@@ -155,36 +155,50 @@ def test_argmax_takes_the_lowest_index_among_ties():
 
 def test_scoring_matches_direct_residuals_of_oracle_hypotheses():
     rp = workloads.ransac_problem(120, 0.5, 1.0, seed=7)
-    cnt, band = oracle.score_problem(rp.corr, 64, 3.0, seed=2, band_px=1e-3)
+    cnt, b_in, b_out = oracle.score_problem(rp.corr, 64, 3.0, seed=2, band_px=1e-3)
     c64 = rp.corr.astype(np.float64)
     for h in range(64):
         idx = oracle.sample4(2, 0, h, 120)
         s = np.concatenate([c64[idx, :2].ravel(), c64[idx, 2:].ravel()])
         if oracle.sample_degenerate(s):
-            assert cnt[h] == -1
+            assert cnt[h] == -1 and b_in[h] == 0 and b_out[h] == 0
             continue
         H = oracle.aca(s.reshape(16, 1)).reshape(3, 3)
         X = np.stack([c64[:, 0], c64[:, 1], np.ones(120)])
         U = H @ X
         ok = U[2] != 0
         r = np.hypot(c64[:, 2] - U[0] / U[2], c64[:, 3] - U[1] / U[2])
-        assert cnt[h] == int(np.sum(ok & (r <= 3.0)))
-        assert band[h] == int(np.sum(ok & (np.abs(r - 3.0) < 1e-3)))
+        inl = ok & (r <= 3.0)
+        assert cnt[h] == int(np.sum(inl))
+        # the band is per point: the fixed band, widened by the FP32 test's
+        # derived bound; split by the exact decision
+        amb = oracle.score_band(s, rp.corr, 3.0, band_px=1e-3).astype(bool)
+        assert np.all(amb[ok & (np.abs(r - 3.0) < 1e-3)])
+        assert b_in[h] == int(np.sum(amb & inl)) and b_out[h] == int(np.sum(amb & ~inl))
 
 
-def test_ambiguity_band_contains_the_fixed_band_and_grows_with_the_error_model():
+def test_ambiguity_band_is_the_fixed_band_united_with_the_derived_fp32_band():
     rp = workloads.ransac_problem(400, 0.6, 1.0, seed=8)
-    c0, b0 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-3)
-    c1, b1 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-3, herr=16)
-    c2, b2 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-3, herr=4096)
+    c0, i0, o0 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=0.0)      # derived band alone
+    c1, i1, o1 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-3)
+    c2, i2, o2 = oracle.score_problem(rp.corr, 128, 3.0, seed=4, band_px=1e-1)
     assert np.array_equal(c0, c1) and np.array_equal(c1, c2)
-    assert np.all(b0 <= b1) and np.all(b1 <= b2)
-    assert b2.sum() > b0.sum()
-    # a noise-free problem: residuals of all-inlier hypotheses are ~0, far from
-    # the threshold, except under an ill-conditioned minimal set
+    assert np.all(i0 <= i1) and np.all(i1 <= i2) and np.all(o0 <= o1) and np.all(o1 <= o2)
+    assert (i2 + o2).sum() > (i0 + o0).sum()
+    # per point, the derived band is exactly where |E| <= the FP32 bound
+    for h in range(0, 128, 16):
+        idx = oracle.sample4(4, 0, h, 400)
+        s = np.concatenate([rp.corr[idx, :2].astype(np.float64).ravel(), rp.corr[idx, 2:].astype(np.float64).ravel()])
+        if oracle.sample_degenerate(s):
+            continue
+        E, B = oracle.score_bound_E(s, rp.corr, 3.0)
+        amb = oracle.score_band(s, rp.corr, 3.0, band_px=0.0).astype(bool)
+        assert np.array_equal(amb, ~(np.abs(E) > B))
+    # a noise-free problem: residuals of all-inlier hypotheses are ~0, far
+    # from the threshold, so nothing is ambiguous for most of them
     rq = workloads.ransac_problem(300, 1.0, 0.0, seed=9)
-    c, b = oracle.score_problem(rq.corr, 64, 3.0, seed=1, band_px=1e-3, herr=16)
-    assert np.mean(b[c == 300] == 0) > 0.9
+    c, bi, bo = oracle.score_problem(rq.corr, 64, 3.0, seed=1, band_px=1e-4)
+    assert np.mean((bi + bo)[c == 300] == 0) > 0.9
 
 
 def test_a_sample_with_a_non_finite_coordinate_is_degenerate():
