@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-log2", type=int, default=N_LOG2)
     ap.add_argument("--no-rows", action="store_true", help="headline only")
-    ap.add_argument("--rows", default="sks,affine,ransac1,ransac512,adaptive,refit,diff,latency",
-                    help="comma list of extra rows: sks, affine, ransac1, ransac512, adaptive, refit, diff, latency")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--rows", default="config0,sks,affine,ransac1,ransac512,adaptive,refit,diff,latency",
+                    help="comma list of extra rows: config0, sks, affine, ransac1, ransac512, adaptive, refit, diff, "
+                         "latency")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle timing of the headline")
+    ap.add_argument("--row-cpu-seconds", type=float, default=3.0, help="oracle timing of each extra row")
     ap.add_argument("--ransac-tuning", default="",
                     help="block_warps,hyps_per_thread,tile_points for the RANSAC rows (skips the autotuner)")
     ap.add_argument("--no-plain", action="store_true", help="skip the 512 per-problem RANSAC launches")
@@ -170,6 +172,35 @@ def sync_all(torch, dist_on):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
+
+
+def link_bandwidth(torch, dev, stream):
+    """Plain cudaMemcpyAsync bandwidth between page-locked host memory and the
+    device (GB/s): H2D alone, D2H alone, and both at once on two streams."""
+    nb = 1 << 30
+    h_in = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(nb, dtype=torch.uint8, device=dev)
+    d_out = torch.empty(nb, dtype=torch.uint8, device=dev)
+    s2 = torch.cuda.Stream(device=dev)
+    h2d = lambda: d_in.copy_(h_in, non_blocking=True)
+    d2h = lambda: h_out.copy_(d_out, non_blocking=True)
+
+    def both():
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            d2h()
+        h2d()
+        stream.wait_stream(s2)
+    for f in (h2d, d2h, both):
+        f()
+    torch.cuda.synchronize()
+    t_in = time_region(torch, h2d, 5, stream)
+    t_out = time_region(torch, d2h, 5, stream)
+    t_both = time_region(torch, both, 5, stream)
+    del h_in, h_out, d_in, d_out
+    return {"h2d_gbs": nb / (t_in * 1e-3) / 1e9, "d2h_gbs": nb / (t_out * 1e-3) / 1e9,
+            "h2d_gbs_duplex": nb / (t_both * 1e-3) / 1e9, "d2h_gbs_duplex": nb / (t_both * 1e-3) / 1e9}
 
 
 def time_region(torch, fn, steps, stream):
@@ -309,7 +340,8 @@ def main():
         if rank == 0:
             res["err"] = error_stats(H.cpu().numpy(), flags.cpu().numpy(), ms.pts, n, np.random.default_rng(1))
         if rows_on:
-            res.update(run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev))
+            ctx = {"peaks": peaks, "sms": sms, "pts_np": ms.pts, "cpu_s": args.row_cpu_seconds}
+            res.update(run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev, ctx))
     clk = clocks.summary()
     if rank != 0:
         if dist_on:
@@ -332,11 +364,20 @@ def main():
         pts.copy_(pts_h, non_blocking=True)
         _lib.aca_solve(pts, H, None, n=n)
         H_h.copy_(H, non_blocking=True)
-    for f in (e2e_step, staged_step):
+    pinned = api.PinnedSolver(dev)
+    pipelined_step = lambda: pinned(pts_h, H_h, n)
+    for f in (e2e_step, staged_step, pipelined_step):
         f()
     torch.cuda.synchronize()
-    e2e_ms = time_region(torch, e2e_step, e2e_steps, stream)
+    zero_copy_ms = time_region(torch, e2e_step, e2e_steps, stream)
     staged_ms = time_region(torch, staged_step, e2e_steps, stream)
+    pipelined_ms = time_region(torch, pipelined_step, e2e_steps, stream)
+    e2e_ms = min(zero_copy_ms, pipelined_ms)
+    e2e_path = ("aca_solve on pinned host buffers (zero-copy over the host link)" if zero_copy_ms <= pipelined_ms
+                else "api.PinnedSolver: chunked H2D -> solve -> D2H on 3 streams")
+    link = link_bandwidth(torch, dev, stream)
+    in_b, out_b = 64 * n, 36 * n
+    link_ms = max(in_b / link["h2d_gbs_duplex"], out_b / link["d2h_gbs_duplex"]) / 1e6
 
     cpu = cpu_baseline_aca(ms.pts, args.cpu_seconds)
     value = job_throughput(n, world, ms_step)
@@ -354,10 +395,14 @@ def main():
                      "peak_source": peaks["source"], "kernel": "solve_ring_kernel<ACA, NONE, no flags>",
                      "algorithmic_bytes_per_launch": BYTES_PER_SET * n},
         "cpu_baseline": cpu,
-        "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "H/s", "h2d_bytes_per_step": 64 * n,
-                "d2h_bytes_per_step": 36 * n, "ms_per_step": e2e_ms,
-                "path": "aca_solve on pinned host buffers (zero-copy over the host link)",
-                "staged_copies_ms_per_step": staged_ms},
+        "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "H/s", "h2d_bytes_per_step": in_b,
+                "d2h_bytes_per_step": out_b, "ms_per_step": e2e_ms, "path": e2e_path,
+                "zero_copy_ms_per_step": zero_copy_ms, "pipelined_3_streams_ms_per_step": pipelined_ms,
+                "serial_staged_copies_ms_per_step": staged_ms,
+                "roofline": {"bound": "host link", "link": link, "link_bound_ms": link_ms,
+                             "frac": link_ms / e2e_ms,
+                             "note": "bound = max(in bytes / H2D rate, out bytes / D2H rate), both directions "
+                                     "measured at once with plain cudaMemcpyAsync copies of 1 GiB pinned buffers"}},
         "gpu_launches": args.steps,
         "clocks": clk,
         "max_err_vs_fp64": res.get("err"),
@@ -374,27 +419,88 @@ def fp32_peak_tflops(sms, mhz):
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev):
+def row_counter(row):
+    """The ncu counter behind a row's roofline, from the committed capture
+    (profiles/row_counters.json); marked stale when the kernel's sources
+    changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "row_counters.json")))[row]
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        out = {k: v for k, v in rec.items() if k not in ("source_files", "source_sha256")}
+        if h.hexdigest() != rec["source_sha256"]:
+            out["stale"] = True
+        return out
+    except Exception:
+        return None
+
+
+def roofline_hbm(row, bytes_per_launch, ms, ctx, kernel, note=None):
+    achieved = bytes_per_launch / (ms * 1e-3) / 1e9
+    peak = ctx["peaks"]["hbm_gbs"]
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+         "peak_source": ctx["peaks"]["source"], "kernel": kernel, "algorithmic_bytes_per_launch": bytes_per_launch,
+         "counter": row_counter(row)}
+    if note:
+        r["note"] = note
+    return r
+
+
+def roofline_alu(row, flops, ms, ctx, kernel, note=None):
+    """FP32-pipe bound: peak = SMs x 128 FP32 lanes x 2 (FMA) x max SM clock."""
+    peak = fp32_peak_tflops(ctx["sms"], ctx["peaks"]["sm_max_mhz"])
+    achieved = flops / (ms * 1e-3) / 1e12
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+         "peak_source": f"derived: {ctx['sms']} SMs x 128 FP32 lanes x 2 x {ctx['peaks']['sm_max_mhz']:.0f} MHz",
+         "kernel": kernel, "algorithmic_flops_per_launch": flops, "flops_per_test": FLOPS_PER_TEST,
+         "counter": row_counter(row)}
+    if note:
+        r["note"] = note
+    return r
+
+
+def cpu_rate(run_once, units_per_call, seconds, unit, sample):
+    """The oracle as it stands, timed on the host cores: units per second over
+    repeated calls totalling about `seconds`."""
+    import oracle
+    run_once()                     # warm (page-in, thread pool)
+    done, k, t0 = 0.0, 0, time.perf_counter()
+    while True:
+        run_once()
+        done += units_per_call
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": unit, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{sample}; {k} calls in {el:.1f} s"}
+
+
+def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev, ctx):
     out = {}
     reps = max(20, args.steps // 4)
+    if "config0" in args.row_set:
+        out.update(row_config0(torch, _lib, stream, dev, ctx))
     if "sks" in args.row_set:
-        out.update(row_sks(torch, _lib, pts, H, flags, n, reps, stream))
+        out.update(row_sks(torch, _lib, pts, H, flags, n, reps, stream, ctx))
     fixed = None
     if args.ransac_tuning:
         w, h, t = (int(x) for x in args.ransac_tuning.split(","))
         fixed = dict(block_warps=w, hyps_per_thread=h, tile_points=t)
     if "affine" in args.row_set:
-        out.update(row_affine(torch, _lib, pts, n, reps, stream))
+        out.update(row_affine(torch, _lib, pts, n, reps, stream, ctx))
     if rp is not None:
-        out.update(row_ransac1(torch, api, rp, stream, dev, fixed))
+        out.update(row_ransac1(torch, api, rp, stream, dev, ctx, fixed))
     if rb is not None and "ransac512" in args.row_set:
-        out.update(row_ransac512(torch, api, rb, stream, dev, fixed, not args.no_plain))
+        out.update(row_ransac512(torch, api, rb, stream, dev, ctx, fixed, not args.no_plain))
     if rb is not None and "adaptive" in args.row_set:
-        out.update(row_adaptive(torch, api, rb, stream, dev, fixed))
+        out.update(row_adaptive(torch, api, rb, stream, dev, ctx, fixed))
     if rb is not None and "refit" in args.row_set:
-        out.update(row_refit(torch, _lib, api, rb, stream, dev, fixed))
+        out.update(row_refit(torch, _lib, api, rb, stream, dev, ctx, fixed))
     if rect is not None:
-        out.update(row_diff(torch, _lib, rect, stream, dev))
+        out.update(row_diff(torch, _lib, rect, stream, dev, ctx))
     if "latency" in args.row_set:
         out.update(row_latency(torch, _lib, pts, H, n, stream))
     return out
@@ -439,40 +545,111 @@ def row_latency(torch, _lib, pts, H, n_total, stream):
     return {"aca_latency_sweep": res}
 
 
-def row_sks(torch, _lib, pts, H, flags, n, reps, stream):
+def row_sks(torch, _lib, pts, H, flags, n, reps, stream, ctx):
+    import oracle
     out = {}
+    chunk = min(n, 1 << 20)
+    aos = oracle.sets_aos(ctx["pts_np"][:, :chunk])
+    buf = np.empty((chunk, 9))
     # SKS on the same sets
     sks = lambda: _lib.sks_solve(pts, H, None, n=n)
     for _ in range(3):
         sks()
     t = time_region(torch, sks, reps, stream)
     out["sks_solve"] = {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
-                        "achieved_gbs": BYTES_PER_SET * n / (t * 1e-3) / 1e9}
+                        "roofline": roofline_hbm("sks_solve", BYTES_PER_SET * n, t, ctx, "solve_vec4_kernel<SKS>"),
+                        "cpu_baseline": cpu_rate(lambda: oracle.lib().oracle_sks(aos.ctypes.data_as(oracle._d),
+                                                                                   buf.ctypes.data_as(oracle._d), chunk),
+                                                 chunk, ctx["cpu_s"], "H/s",
+                                                 f"FP64 SKS oracle (Eq. 4-14) over the first {chunk} of the sets")}
     fl = lambda: _lib.aca_solve(pts, H, flags, n=n)
     for _ in range(3):
         fl()
     t = time_region(torch, fl, reps, stream)
-    out["aca_solve_with_flags"] = {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
-                                   "achieved_gbs": (BYTES_PER_SET + 1) * n / (t * 1e-3) / 1e9}
+    out["aca_solve_with_flags"] = {
+        "value": n / (t * 1e-3), "unit": "H/s", "ms": t,
+        "roofline": roofline_hbm("aca_solve_with_flags", (BYTES_PER_SET + 1) * n, t, ctx,
+                                 "solve_ring_kernel<ACA, NONE, flags>"),
+        "cpu_baseline": cpu_rate(lambda: oracle.lib().oracle_aca(aos.ctypes.data_as(oracle._d),
+                                                                buf.ctypes.data_as(oracle._d), chunk),
+                                 chunk, ctx["cpu_s"], "H/s",
+                                 f"FP64 ACA oracle (the oracle has no flag computation) over the first {chunk} sets")}
     return out
 
 
-def row_affine(torch, _lib, pts, n, reps, stream):
+def row_affine(torch, _lib, pts, n, reps, stream, ctx):
     """Three-point affine solve (Eq. 38) on the M, N, P points of the same
     sets: 12 float planes in, 9 out (84 B per set)."""
+    import oracle
     p12 = torch.cat([pts[0:6], pts[8:14]], dim=0).contiguous()
     A = torch.empty((9, n), dtype=torch.float32, device=pts.device)
     f = lambda: _lib.aca_affine_solve(p12, A, n=n)
     for _ in range(3):
         f()
     t = time_region(torch, f, reps, stream)
-    out = {"aca_affine_solve": {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
-                                "achieved_gbs": 84 * n / (t * 1e-3) / 1e9, "bytes_per_set": 84}}
+    chunk = min(n, 1 << 20)
+    p12h = np.concatenate([ctx["pts_np"][0:6, :chunk], ctx["pts_np"][8:14, :chunk]], axis=0)
+    aos = np.ascontiguousarray(p12h.T.astype(np.float64))
+    buf = np.empty((chunk, 9))
+    out = {"aca_affine_solve": {
+        "value": n / (t * 1e-3), "unit": "H/s", "ms": t, "bytes_per_set": 84,
+        "roofline": roofline_hbm("aca_affine_solve", 84 * n, t, ctx, "affine_ring_kernel"),
+        "cpu_baseline": cpu_rate(lambda: oracle.lib().oracle_aca_affine(aos.ctypes.data_as(oracle._d),
+                                                                       buf.ctypes.data_as(oracle._d), chunk),
+                                 chunk, ctx["cpu_s"], "H/s", f"FP64 affine oracle (Eq. 38) over the first {chunk} sets")}}
     del p12, A
     return out
 
 
-def row_ransac1(torch, api, rp, stream, dev, fixed=None):
+def row_config0(torch, _lib, stream, dev, ctx):
+    """Config 0: 4096 minimal sets, the parity configuration.  Device time per
+    aca_solve from graph replays, the largest error against the FP64 oracle,
+    and the oracle's ACA (O1) and independent DLT (O2) on one host thread and
+    on all host cores."""
+    import oracle
+    ms0 = workloads.minimal_sets(4096, seed=0)
+    pts0 = torch.from_numpy(ms0.pts).to(dev)
+    H0 = torch.empty((9, 4096), dtype=torch.float32, device=dev)
+    f = lambda: _lib.aca_solve(pts0, H0, None, n=4096)
+    for _ in range(5):
+        f()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(100):
+                _lib.aca_solve(pts0, H0, None, n=4096, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    t = time_region(torch, g.replay, 10, stream) / 100
+    a = H0.cpu().numpy().T.astype(np.float64)
+    ref = oracle.aca(ms0.pts)
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    b = ref / np.linalg.norm(ref, axis=1, keepdims=True)
+    a *= np.sign(np.sum(a * b, axis=1, keepdims=True))
+    err = np.abs(a - b).max(axis=1)
+    aos = oracle.sets_aos(ms0.pts)
+    buf = np.empty((4096, 9))
+    cores = oracle.num_threads()
+    cpu = {}
+    for name, fn in (("aca_O1", "oracle_aca"), ("dlt_O2", "oracle_dlt")):
+        for thr in (1, cores):
+            oracle.set_num_threads(thr)
+            run = lambda: getattr(oracle.lib(), fn)(aos.ctypes.data_as(oracle._d), buf.ctypes.data_as(oracle._d), 4096)
+            cpu[f"{name}_{thr}_threads"] = cpu_rate(run, 4096, min(2.0, ctx["cpu_s"]), "H/s",
+                                                    f"FP64 {fn} over the 4096 config-0 sets, {thr} thread(s)")
+            cpu[f"{name}_{thr}_threads"]["cores"] = thr
+    oracle.set_num_threads(cores)
+    return {"aca_config0_4096": {
+        "value": 4096 / (t * 1e-3), "unit": "H/s", "us_per_call_device": t * 1e3,
+        "max_err_vs_fp64": float(err.max()), "median_err_vs_fp64": float(np.median(err)),
+        "roofline": roofline_hbm("aca_config0_4096", BYTES_PER_SET * 4096, t, ctx, "solve_scalar_kernel<ACA>",
+                                 note="410 KB per call: launch/latency-bound, not HBM-bound"),
+        "cpu_baseline": cpu[f"aca_O1_{cores}_threads"], "cpu_oracles": cpu}}
+
+
+def row_ransac1(torch, api, rp, stream, dev, ctx, fixed=None):
     out = {}
     # fused RANSAC, one pair (config 2), graph-replayed
     from paper_2402_18008_gb300 import autotune
@@ -486,14 +663,24 @@ def row_ransac1(torch, api, rp, stream, dev, fixed=None):
         plan2.replay()
     t = time_region(torch, plan2.replay, 200, stream)
     tests = 4096 * 2000
-    out["ransac_fused_one_pair"] = {"value": tests / (t * 1e-3), "unit": "hyp*pts/s", "ms_per_ransac": t,
-                                    "tflops_fp32": tests * FLOPS_PER_TEST / (t * 1e-3) / 1e12,
-                                    "tuning": best2,
-                                    "config": "N=2000, 60% inliers, 4096 hypotheses, thr 3 px, graph replay"}
+    import oracle
+    cnt = np.empty(4096, np.int32)
+    c = np.ascontiguousarray(rp.corr, np.float32)
+    run = lambda: oracle.lib().oracle_score_problem(c.ctypes.data_as(oracle._f), 2000, 4096, RANSAC_THR, SEED, 0,
+                                                    cnt.ctypes.data_as(oracle._i32), None, None, 0.0)
+    out["ransac_fused_one_pair"] = {
+        "value": tests / (t * 1e-3), "unit": "hyp*pts/s", "ms_per_ransac": t,
+        "tflops_fp32": tests * FLOPS_PER_TEST / (t * 1e-3) / 1e12, "tuning": best2,
+        "roofline": roofline_alu("ransac_fused_one_pair", tests * FLOPS_PER_TEST, t, ctx, "ransac_fused_kernel",
+                                 note="whole RANSAC per graph replay (one launch): sampling, solve, scoring, argmax, "
+                                      "re-solve, outputs"),
+        "cpu_baseline": cpu_rate(run, tests, ctx["cpu_s"], "hyp*pts/s",
+                                 "brute-force FP64 scoring oracle (O5) on the same pair, 4096 hypotheses"),
+        "config": "N=2000, 60% inliers, 4096 hypotheses, thr 3 px, graph replay"}
     return out
 
 
-def row_ransac512(torch, api, rb, stream, dev, fixed=None, plain=True):
+def row_ransac512(torch, api, rb, stream, dev, ctx, fixed=None, plain=True):
     out = {}
     # batched uneven RANSAC (config 3) vs 512 separate per-problem launches
     tot = int(rb.n_hyp.sum())
@@ -513,7 +700,9 @@ def row_ransac512(torch, api, rb, stream, dev, fixed=None, plain=True):
            "tflops_fp32": tests3 * FLOPS_PER_TEST / (t3 * 1e-3) / 1e12, "tests": tests3, "hypotheses": tot,
            "points": int(rb.offsets[-1]), "tuning": best3,
            "config": "512 pairs, N log-uniform [200,8000], eps U[0.1,0.9], adaptive hypotheses (99%, cap 16384), "
-                     "one graph replay"}
+                     "one graph replay",
+           "roofline": roofline_alu("ransac_batched_512", tests3 * FLOPS_PER_TEST, t3, ctx, "ransac_score_kernel"),
+           "cpu_baseline": cpu_ransac_pairs(rb, ctx["cpu_s"])}
     if not plain:
         out["ransac_batched_512"] = res
         return out
@@ -538,7 +727,35 @@ def row_ransac512(torch, api, rb, stream, dev, fixed=None, plain=True):
 ADAPTIVE_CAP = 16384
 
 
-def row_adaptive(torch, api, rb, stream, dev, fixed=None):
+def cpu_ransac_pairs(rb, seconds, cap=None):
+    """The brute-force FP64 RANSAC oracle (O5) over the batch's pairs in
+    order, as many as fit in about `seconds`: hypothesis x point tests per
+    second (with `cap`, the adaptive oracle, which scores every one of the
+    cap hypotheses and then finds the sequential stop)."""
+    import oracle
+    done, k, t0 = 0.0, 0, time.perf_counter()
+    P = len(rb.n_hyp)
+    while k < P:
+        a, b = int(rb.offsets[k]), int(rb.offsets[k + 1])
+        if cap is None:
+            oracle.ransac(rb.corr[a:b], [0, b - a], rb.n_hyp[k:k + 1], RANSAC_THR, SEED, problem_base=k,
+                          want_counts=False)
+            done += float(rb.n_hyp[k]) * (b - a)
+        else:
+            oracle.ransac_adaptive(rb.corr[a:b], [0, b - a], [cap], RANSAC_THR, SEED, 0.99, problem_base=k,
+                                   want_band=False)
+            done += float(cap) * (b - a)
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    what = "adaptive FP64 RANSAC oracle (scores all cap hypotheses, then the sequential stop)" if cap else \
+        "brute-force FP64 RANSAC oracle (O5)"
+    return {"value": done / el, "unit": "hyp*pts/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{what} over the first {k} of the {P} pairs ({el:.1f} s)"}
+
+
+def row_adaptive(torch, api, rb, stream, dev, ctx, fixed=None):
     """Batched RANSAC with the online adaptive stop (99% confidence) over the
     512 pairs with the same cap for every pair (no knowledge of the inlier
     ratio), against fixed counts: the cap for every pair, and counts computed
@@ -572,10 +789,14 @@ def row_adaptive(torch, api, rb, stream, dev, fixed=None):
                median_evaluated=float(np.median(ne)), max_evaluated=int(ne.max()),
                hypotheses_fixed_from_true_ratio=int(rb.n_hyp.sum()),
                value=res["ms_adaptive"], speedup_vs_fixed_cap=res["ms_fixed_cap"] / res["ms_adaptive"])
+    res["roofline"] = roofline_alu("ransac_adaptive_512", res["tests_evaluated"] * FLOPS_PER_TEST, res["ms_adaptive"],
+                                   ctx, "ransac_score_kernel<adaptive>",
+                                   note="useful work: the tests of the hypotheses the sequential loop evaluates")
+    res["cpu_baseline"] = cpu_ransac_pairs(rb, ctx["cpu_s"], cap=ADAPTIVE_CAP)
     return {"ransac_adaptive_512": res}
 
 
-def row_refit(torch, _lib, api, rb, stream, dev, fixed=None):
+def row_refit(torch, _lib, api, rb, stream, dev, ctx, fixed=None):
     """Refit on all inliers (aca_refit) over the 512 pairs of the batched
     RANSAC workload: with the generated inlier masks alone (DLT only and DLT
     + 10 LM steps), and appended to the batched RANSAC in one CUDA graph."""
@@ -622,10 +843,28 @@ def row_refit(torch, _lib, api, rb, stream, dev, fixed=None):
                refit_share_of_pipeline=1.0 - times["ransac_only"] / times["ransac_plus_refit"],
                ms_adaptive_ransac_plus_refit=times["adaptive_plus_refit"], tuning_adaptive=best_a,
                us_per_pair_adaptive_ransac_plus_refit=times["adaptive_plus_refit"] * 1e3 / P)
+    # compulsory traffic: every correspondence (16 B) and mask byte read once,
+    # 9 floats + 2 ints written per pair
+    npts = int(rb.offsets[-1])
+    res["roofline"] = roofline_hbm("refit_512", 17 * npts + 44 * P, res["ms_lm10"], ctx, "refit_kernel",
+                                   note="latency-bound: per-problem passes and serial solves, not HBM traffic")
+    import oracle
+    done, k, t0 = 0.0, 0, time.perf_counter()
+    while k < P:
+        a, b = int(rb.offsets[k]), int(rb.offsets[k + 1])
+        oracle.refit(rb.corr[a:b], [0, b - a], rb.is_inlier[a:b], 10)
+        done += float(rb.is_inlier[a:b].sum())
+        k += 1
+        if time.perf_counter() - t0 >= ctx["cpu_s"]:
+            break
+    el = time.perf_counter() - t0
+    res["cpu_baseline"] = {"value": done / el, "unit": "used points/s", "cores": 1, "kind": "oracle",
+                           "sample": f"float64 refit oracle (normalised DLT + 10 LM steps, numpy, one thread) over "
+                                     f"the first {k} of the {P} pairs ({el:.1f} s)"}
     return {"refit_512": res}
 
 
-def row_diff(torch, _lib, rect, stream, dev):
+def row_diff(torch, _lib, rect, stream, dev, ctx):
     out = {}
     # differentiable rectangle ACA (config 4): forward + backward vs plain solve
     B = rect.tgt.shape[1]
@@ -676,11 +915,30 @@ def row_diff(torch, _lib, rect, stream, dev):
     g.replay()
     torch.cuda.synchronize()
     tdev = time_region(torch, g.replay, 10, stream) / 50
-    out["diff_aca_rect_65536"] = {"value": B / (tfb * 1e-3), "unit": "sets/s (fwd+bwd, eager calls)",
-                                  "ms_fwd_bwd": tfb, "ms_fwd_bwd_device": tdev,
-                                  "sets_per_s_device": B / (tdev * 1e-3),
-                                  "ms_plain_aca_solve": tpl, "ratio_vs_plain": tfb / tpl,
-                                  "ms_torch_ops_autograd_fwd_bwd": ttt, "speedup_vs_torch_ops": ttt / tfb}
+    import oracle
+    tg = np.ascontiguousarray(rect.tgt.T.astype(np.float64))
+    x0, y0, w, r = (float(v) for v in rect.rect)
+    Hbuf = np.empty((B, 9))
+    Jbuf = np.empty((B, 9, 8))
+    gHh = gH.cpu().numpy().T.astype(np.float64)
+
+    def cpu_fwd_bwd():
+        oracle.lib().oracle_aca_rect(tg.ctypes.data_as(oracle._d), x0, y0, w, r, Hbuf.ctypes.data_as(oracle._d), B)
+        oracle.lib().oracle_aca_rect_jacobian(tg.ctypes.data_as(oracle._d), x0, y0, w, r,
+                                              Jbuf.ctypes.data_as(oracle._d), B)
+        np.einsum("nik,ni->nk", Jbuf, gHh)
+    out["diff_aca_rect_65536"] = {
+        "value": B / (tfb * 1e-3), "unit": "sets/s (fwd+bwd, eager calls)",
+        "ms_fwd_bwd": tfb, "ms_fwd_bwd_device": tdev, "sets_per_s_device": B / (tdev * 1e-3),
+        "ms_plain_aca_solve": tpl, "ratio_vs_plain": tfb / tpl,
+        "ms_torch_ops_autograd_fwd_bwd": ttt, "speedup_vs_torch_ops": ttt / tfb,
+        # forward 32 B in + 36 out, backward 32 + 36 in + 32 out, per set
+        "roofline": roofline_hbm("diff_aca_rect_65536", 168 * B, tdev, ctx,
+                                 "rect_vec4_kernel + rect_backward_vec4_kernel",
+                                 note="11 MB per forward + backward: latency-bound at this batch"),
+        "cpu_baseline": cpu_rate(cpu_fwd_bwd, B, ctx["cpu_s"], "sets/s",
+                                 "FP64 Eq. 42 forward + analytic Jacobian oracle and its product with dL/dH, "
+                                 f"{B} sets")}
     return out
 
 

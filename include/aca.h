@@ -155,15 +155,24 @@ aca_status aca_rect_backward(const float *tgt, float x0, float y0, float w, floa
  *             problem after problem; -1 for a degenerate sample.
  *   inlier_mask[total] uint8 or NULL: 1 for the inliers of the best hypothesis.
  *   workspace device memory of at least ransac_aca_workspace_size(P, sum n_hyp)
- *             bytes, 256-byte aligned; its contents need not be initialised.
+ *             bytes, 256-byte aligned.  With P <= 8 its first 256 bytes must
+ *             be zero before the first call on it (e.g. cudaMemset once at
+ *             allocation); every call leaves them zero.  Otherwise its
+ *             contents need not be initialised.
  *
- * Work decomposition: the (problem, block of 32*hyps_per_thread hypotheses,
- * slice of tile_points correspondences) items of all problems are pulled by
- * a persistent grid from one atomic counter; every item samples and solves
- * its hypotheses in registers (Philox + ACA), stages its correspondence
- * slice in shared memory and scores every hypothesis against it; per-slice
- * counts are summed with one atomic add per hypothesis; a last kernel takes
- * the argmax per problem, re-solves the winner and writes the outputs.
+ * Work decomposition, P > 8: the (problem, block of 32*hyps_per_thread
+ * hypotheses, slice of tile_points correspondences) items of all problems
+ * are pulled by a persistent grid from one atomic counter; every item
+ * samples and solves its hypotheses in registers (Philox + ACA), stages its
+ * correspondence slice in shared memory and scores every hypothesis against
+ * it; per-slice counts are summed with one atomic add per hypothesis; a last
+ * kernel takes the argmax per problem, re-solves the winner and writes the
+ * outputs.  P <= 8 (e.g. one image pair): everything in one launch; the
+ * items (problem, block of hypotheses, one of 4 point ranges) are striped
+ * over the resident blocks, each writes its partial counts to the slot of
+ * its point range (and its hypotheses' H), and the last block to finish
+ * sums them, takes the argmax and writes the outputs from the winner's
+ * stored H.  Both give the same results bit for bit.
  *
  * Sampling: hypothesis h of problem p draws Philox4x32-10 (Salmon et al.,
  * SC'11) with counter (h, problem_base + p, 0, 0) and key (seed low 32 bits,
@@ -188,12 +197,14 @@ typedef struct {
     int32_t block_warps;     /* warps per block, 0 = default (8); 1..16 */
     int32_t hyps_per_thread; /* hypotheses per thread, 0 = default (2); 1, 2 or 4 */
     int32_t grid_blocks;     /* resident blocks of the persistent kernel, 0 = SMs x occupancy */
-    int32_t tile_points;     /* correspondences per work item (staged in shared memory),
+    int32_t tile_points;     /* correspondences per work item (P > 8) or per shared-memory
+                                tile of a point range (P <= 8), staged in shared memory;
                                 0 = default (1024); a multiple of 32, 32..8192 */
 } aca_ransac_params;
 
 /* Workspace bytes ransac_aca needs for P problems with total_hyps =
  * sum of n_hyp hypotheses (per-problem offsets plus one int32 count per
+ * hypothesis; with P <= 8, four partial counts and the 9 entries of H per
  * hypothesis).  If the device-side sum of n_hyp exceeds what the workspace
  * holds, nothing is scored and every best_hyp is -2. */
 size_t ransac_aca_workspace_size(int32_t P, int64_t total_hyps);

@@ -66,6 +66,8 @@ def lib():
         if _lib is None:
             L = ctypes.CDLL(build())
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_set_num_threads.argtypes = [ctypes.c_int]
+            L.oracle_set_num_threads.restype = None
             for name in ("oracle_aca", "oracle_aca_divform", "oracle_sks", "oracle_aca_jacobian",
                          "oracle_aca_jacobian_src", "oracle_aca_condition"):
                 getattr(L, name).argtypes = [_d, _d, ctypes.c_int64]
@@ -115,6 +117,11 @@ def _ptr(a, t):
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on."""
+    lib().oracle_set_num_threads(int(n))
 
 
 def sets_aos(pts16: np.ndarray, n: int | None = None) -> np.ndarray:
@@ -296,10 +303,12 @@ def adaptive_stop(counts, N: int, confidence: float = 0.99) -> int:
 
 
 def ransac_adaptive(corr, offsets, max_hyp, thr: float, seed: int, confidence: float = 0.99,
-                    problem_base: int = 0, band_px: float = 1e-4, want_mask: bool = False) -> dict:
+                    problem_base: int = 0, band_px: float = 1e-4, want_mask: bool = False,
+                    want_band: bool = True) -> dict:
     """RANSAC with the online stop (oracle_ransac_adaptive): counts and
-    ambiguous points (band_in / band_out, as in ransac) of all max_hyp
-    hypotheses, n_eval, and the best over the evaluated ones."""
+    ambiguous points (band_in / band_out, as in ransac; None without
+    want_band) of all max_hyp hypotheses, n_eval, and the best over the
+    evaluated ones."""
     c = np.ascontiguousarray(corr, dtype=np.float32)
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     k = np.ascontiguousarray(max_hyp, dtype=np.int32)
@@ -310,15 +319,15 @@ def ransac_adaptive(corr, offsets, max_hyp, thr: float, seed: int, confidence: f
     best_hyp = np.empty(P, dtype=np.int32)
     n_eval = np.empty(P, dtype=np.int32)
     counts = np.empty(tot, dtype=np.int32)
-    ai = np.empty(tot, dtype=np.int32)
-    ao = np.empty(tot, dtype=np.int32)
+    ai = np.empty(tot, dtype=np.int32) if want_band else None
+    ao = np.empty(tot, dtype=np.int32) if want_band else None
     mask = np.empty(c.shape[0], dtype=np.uint8) if want_mask else None
     lib().oracle_ransac_adaptive(_ptr(c, _f), _ptr(off, _i64), _ptr(k, _i32), P, thr, seed, problem_base,
                                  confidence, _ptr(best_H, _d), _ptr(best_count, _i32), _ptr(best_hyp, _i32),
                                  _ptr(n_eval, _i32), _ptr(counts, _i32), _ptr(ai, _i32), _ptr(ao, _i32), band_px,
                                  _ptr(mask, _u8))
     return dict(best_H=best_H, best_count=best_count, best_hyp=best_hyp, n_eval=n_eval, hyp_counts=counts,
-                band_in=ai, band_out=ao, band_counts=ai + ao, inlier_mask=mask)
+                band_in=ai, band_out=ao, band_counts=None if ai is None else ai + ao, inlier_mask=mask)
 
 
 from .inlier_refit import hartley_normalization, refit, refit_dlt, refit_lm, refit_tolerance, reprojection_cost  # noqa: E402,F401

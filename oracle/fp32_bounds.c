@@ -43,7 +43,8 @@
  * Eq. 28-29 and the local-frame product of Eq. 24 in double-float rounded
  * once per entry, the translation back in FP32; SKS (Eq. 4-14) with exact
  * differences, the similarity images P3, Q3 as compensated dot and cross
- * products, the cleared-denominator form of Eq. 11-13, the composition of
+ * products, each side scaled by a power of two, the division-free form of
+ * Eq. 11-13 over their common denominator, the composition of
  * Eq. 14 in double-float rounded once per entry and the translation back in
  * FP32; the inlier test in its threshold-folded form.  A bound that fails
  * to cover the library's FP32 result therefore means that either the
@@ -118,6 +119,14 @@ static int xscale(tape *t, int a, double c)
     const int k = push(t, c * V(a), fabs(c * V(a)), 0.0);
     dep(t, k, a, c);
     return k;
+}
+/* 2^-e with 2^e <= |x| < 2^(e+1) (1 for 0 or non-finite x) */
+static double pow2_inv(float x)
+{
+    if (!(x != 0) || !isfinite(x)) return 1.0;
+    int e;
+    frexpf(x, &e);
+    return ldexp(1.0, 1 - e);
 }
 /* the value of a, rounded once to FP32 */
 static int rn(tape *t, int a)
@@ -343,18 +352,23 @@ static void sks_chain(tape *t, const double *s, int H[9])
     sks_side_t a, b;
     sks_side(t, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], &a);
     sks_side(t, x[8], x[9], x[10], x[11], x[12], x[13], x[14], x[15], &b);
+    /* each side's P3, Q3, f_S, cross(ON, QP) scaled by the power of two
+     * that brings f_S (as rounded to FP32) into [1, 2) (exact) */
+    const double ka = pow2_inv((float)V(a.fS)), kb = pow2_inv((float)V(b.fS));
+    const int aP3x = xscale(t, a.P3x, ka), aP3y = xscale(t, a.P3y, ka), aQ3x = xscale(t, a.Q3x, ka);
+    const int aQ3y = xscale(t, a.Q3y, ka), afS = xscale(t, a.fS, ka), acQP = xscale(t, a.cQP, ka);
+    const int bP3x = xscale(t, b.P3x, kb), bP3y = xscale(t, b.P3y, kb), bQ3x = xscale(t, b.Q3x, kb);
+    const int bQ3y = xscale(t, b.Q3y, kb), bfS = xscale(t, b.fS, kb), bcQP = xscale(t, b.cQP, kb);
     /* Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11) */
-    const int n7x = det2(t, a.Q3x, a.P3x, a.Q3y, a.P3y), n7y = mul(t, a.fS, a.cQP), d7 = mul(t, a.Q3y, a.P3y);
-    const int n8x = det2(t, b.Q3x, b.P3x, b.Q3y, b.P3y), n8y = mul(t, b.fS, b.cQP), d8 = mul(t, b.Q3y, b.P3y);
-    /* Eq. 11 */
-    const int den = mul(t, d8, mul(t, sub(t, n7x, n7y), add(t, n7x, n7y)));
-    const int aK = dv(t, mul(t, d7, det2(t, n8x, n8y, n7y, n7x)), den);
-    const int bK = dv(t, mul(t, d7, det2(t, n8y, n8x, n7y, n7x)), den);
-    /* Eq. 13 */
-    const int P5x = dv(t, a.P3x, a.P3y), P5y = dv(t, a.fS, a.P3y);
-    const int P6x = dv(t, b.P3x, b.P3y), P6y = dv(t, b.fS, b.P3y);
-    const int uK = sub(t, P6x, fma3(t, aK, P5x, mul(t, bK, P5y)));
-    const int vK = sub(t, P6y, fma3(t, bK, P5x, mul(t, aK, P5y)));
+    const int n7x = det2(t, aQ3x, aP3x, aQ3y, aP3y), n7y = mul(t, afS, acQP);
+    const int n8x = det2(t, bQ3x, bP3x, bQ3y, bP3y), n8y = mul(t, bfS, bcQP);
+    /* Eq. 11 and Eq. 13 over the common denominator Q4.y P4.y m */
+    const int A = det2(t, n8x, n8y, n7y, n7x), B = det2(t, n8y, n8x, n7y, n7x);
+    const int m = mul(t, sub(t, n7x, n7y), add(t, n7x, n7y));
+    const int q = mul(t, aQ3y, aP3y), bm = mul(t, bQ3y, m);
+    const int aK = mul(t, q, A), bK = mul(t, q, B), dK = mul(t, bP3y, bm);
+    const int uK = fma3(t, bP3x, bm, neg(t, mul(t, aQ3y, fma3(t, A, aP3x, mul(t, B, afS)))));
+    const int vK = fma3(t, bfS, bm, neg(t, mul(t, aQ3y, fma3(t, B, aP3x, mul(t, A, afS)))));
     /* Eq. 14 in the M frames, double-float; ON rounded once where used */
     const int o1x = rn(t, a.onx), o1y = rn(t, a.ony), o2x = rn(t, b.onx), o2y = rn(t, b.ony);
     const int A00 = dfsub(t, dfmul(t, aK, o1x), dfmul(t, uK, o1y));
@@ -363,11 +377,12 @@ static void sks_chain(tape *t, const double *s, int H[9])
     const int A20 = dfsub(t, dfmul(t, bK, o1x), dfmul(t, vK, o1y));
     const int A21 = dfadd(t, dfmul(t, bK, o1y), dfmul(t, vK, o1x));
     const int A22 = dfmul(t, aK, a.fS);
-    const int L00 = dfadd(t, dfmul(t, A00, o2x), dfmul(t, o2y, o1y));
-    const int L01 = dfsub(t, dfmul(t, A01, o2x), dfmul(t, o2y, o1x));
+    const int D1x = dfmul(t, dK, o1x), D1y = dfmul(t, dK, o1y);
+    const int L00 = dfadd(t, dfmul(t, A00, o2x), dfmul(t, D1y, o2y));
+    const int L01 = dfsub(t, dfmul(t, A01, o2x), dfmul(t, D1x, o2y));
     const int L02 = dfmul(t, A02, o2x);
-    const int L10 = dfsub(t, dfmul(t, A00, o2y), dfmul(t, o2x, o1y));
-    const int L11 = dfadd(t, dfmul(t, A01, o2y), dfmul(t, o2x, o1x));
+    const int L10 = dfsub(t, dfmul(t, A00, o2y), dfmul(t, D1y, o2x));
+    const int L11 = dfadd(t, dfmul(t, A01, o2y), dfmul(t, D1x, o2x));
     const int L12 = dfmul(t, A02, o2y);
     const int G02 = dfsub(t, dfsub(t, L02, dfmul(t, L00, o1x)), dfmul(t, L01, o1y));
     const int G12 = dfsub(t, dfsub(t, L12, dfmul(t, L10, o1x)), dfmul(t, L11, o1y));

@@ -32,6 +32,16 @@ int oracle_num_threads(void)
 #endif
 }
 
+/* Threads of the following parallel loops (timing on one core or all). */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* 3x3 helpers                                                          */
 /* ------------------------------------------------------------------ */

@@ -33,6 +33,43 @@ def solve(pts: torch.Tensor, norm: int = ACA_NORM_NONE, solver: str = "aca", wit
     return (H, fl) if with_flags else H
 
 
+class PinnedSolver:
+    """ACA on page-locked host planes through device staging buffers: the
+    sets are copied to the device chunk by chunk (one cudaMemcpyAsync per
+    plane segment), solved there, and the homographies copied back, with
+    `streams` chunks in flight on streams of their own so that the two copy
+    directions and the solves overlap.  The alternative to calling
+    aca_solve on the host buffers directly (zero-copy: the kernel itself
+    reads and writes over the host link).  Staging buffers are allocated
+    once, here: streams x 25 planes x chunk floats."""
+
+    def __init__(self, device, chunk: int = 1 << 22, streams: int = 3):
+        self.chunk = int(chunk)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
+        self.pts = [torch.empty((16, self.chunk), dtype=torch.float32, device=device) for _ in range(streams)]
+        self.H = [torch.empty((9, self.chunk), dtype=torch.float32, device=device) for _ in range(streams)]
+
+    def __call__(self, pts_h: torch.Tensor, H_h: torch.Tensor, n: int | None = None):
+        if not (pts_h.is_pinned() and H_h.is_pinned()):
+            raise ValueError("pts_h and H_h must be page-locked host tensors")
+        n = pts_h.shape[1] if n is None else int(n)
+        cur = torch.cuda.current_stream()
+        for s in self.streams:
+            s.wait_stream(cur)
+        for j, a in enumerate(range(0, n, self.chunk)):
+            c = min(self.chunk, n - a)
+            k = j % len(self.streams)
+            s, dp, dh = self.streams[k], self.pts[k], self.H[k]
+            with torch.cuda.stream(s):
+                for r in range(16):
+                    dp[r, :c].copy_(pts_h[r, a:a + c], non_blocking=True)
+                _lib.aca_solve(dp, dh, None, n=c, stream=s)
+                for r in range(9):
+                    H_h[r, a:a + c].copy_(dh[r, :c], non_blocking=True)
+        for s in self.streams:
+            cur.wait_stream(s)
+
+
 def rect_solve(tgt: torch.Tensor, rect, out: torch.Tensor | None = None):
     """Rectangle-source ACA (Eq. 42).  tgt: (8, ld) float32; rect = (x0, y0, w, r)."""
     _require_cuda(tgt, "tgt")
@@ -111,7 +148,9 @@ class RansacPlan:
                                    tile_points=int(tile_points))
         ws = (_lib.ransac_aca_adaptive_workspace_size(self.P, int(total_hyps)) if confidence is not None
               else _lib.ransac_aca_workspace_size(self.P, int(total_hyps)))
-        self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+        # zeroed: the one-launch path of small batches needs its done counter
+        # at zero before the first call (every call leaves it zero)
+        self.workspace = torch.zeros(max(ws, 256), dtype=torch.uint8, device=dev)
         self.best_H = torch.empty((self.P, 9), dtype=torch.float32, device=dev)
         self.best_count = torch.empty(self.P, dtype=torch.int32, device=dev)
         self.best_hyp = torch.empty(self.P, dtype=torch.int32, device=dev)

@@ -188,6 +188,17 @@ ACA_HD float fmax3_(float a, float b, float c)
     return m > c ? m : c;
 }
 
+// pow2_inv_scale lane by lane (one set, or each set of a packed pair).
+ACA_HD float vpow2_inv_scale(float x) { return pow2_inv_scale(x); }
+#if defined(__CUDACC__)
+__device__ __forceinline__ P2 vpow2_inv_scale(P2 x)
+{
+    float a, b;
+    vunpack(x, a, b);
+    return vpack(pow2_inv_scale(a), pow2_inv_scale(b));
+}
+#endif
+
 // Largest |entry| of H.
 ACA_HD float max_abs9(const float H[9])
 {
@@ -282,13 +293,24 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 //   P5 = (P3.x, f_S1) / P3.y, Q7 = (Q3.x, f_S1) / Q3.y - P5 (Eq. 10-11) with
 //     Q7.x = (Q3.x P3.y - P3.x Q3.y) / (Q3.y P3.y),
 //     Q7.y = f_S1 (P3.y - Q3.y) / (Q3.y P3.y), P3.y - Q3.y = ON x Q1P1;
-//   a_K, b_K of Eq. 11 with the common denominators cancelled:
-//     a_K = d7 (n8x n7x - n8y n7y) / (d8 (n7x^2 - n7y^2)),
-//     b_K = d7 (n8y n7x - n8x n7y) / (d8 (n7x^2 - n7y^2)),
-//     where Q7 = (n7x, n7y) / d7 and Q8 = (n8x, n8y) / d8;
-//   u_K, v_K of Eq. 13; H = H_S2^-1 H_K H_S1 (Eq. 14) composed in the M
-//   frames in double-float, rounded once per entry, then translated back in
-//   FP32.
+//   a_K, b_K of Eq. 11 and u_K, v_K of Eq. 13 over their common
+//   denominator: with Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (d7 =
+//   Q3.y P3.y, d8 likewise), A = n8x n7x - n8y n7y, B = n8y n7x - n8x n7y,
+//   m = n7x^2 - n7y^2, and P5, P6 the dehomogenised P3, P4, the kernel
+//   H_K = [[a_K, u_K, b_K], [0, 1, 0], [b_K, v_K, a_K]] times
+//   D = Q4.y P4.y m is
+//     K = [[a3, u3, b3], [0, D, 0], [b3, v3, a3]],
+//     a3 = Q3.y P3.y A,  b3 = Q3.y P3.y B,
+//     u3 = P4.x Q4.y m - Q3.y (A P3.x + B f_S1),
+//     v3 = f_S2 Q4.y m - Q3.y (B P3.x + A f_S1),
+//   the same H up to scale without a single division.  m, the determinant
+//   of Eq. 11, vanishes where the SKS parameterisation (not the map) is
+//   singular; dividing by it there amplified the rounding of P3, Q3, while
+//   in K it only enters as a term.  The quantities of each side are first
+//   scaled by one power of two (exact) so that f_S lies in [1, 2): H_K is
+//   invariant under it and the products stay far from overflow;
+//   H = H_S2^-1 K H_S1 (Eq. 14) composed in the M frames in double-float,
+//   rounded once per entry, then translated back in FP32.
 // Differences are exact (TwoSum) and dot / cross products of them carry
 // their remainders.
 // ---------------------------------------------------------------------------
@@ -324,35 +346,41 @@ ACA_HD void sks_solve(const SetT<V> &s, V H[9])
     SksSide<V> a, b;
     sks_side(s.M1x, s.M1y, s.N1x, s.N1y, s.P1x, s.P1y, s.Q1x, s.Q1y, a);
     sks_side(s.M2x, s.M2y, s.N2x, s.N2y, s.P2x, s.P2y, s.Q2x, s.Q2y, b);
+    // each side's P3, Q3, f_S, cross(ON, QP) scaled by one power of two
+    // (H_K is invariant); the unscaled f_S1 stays for H_S1 below
+    const V ka = vpow2_inv_scale(a.fS), kb = vpow2_inv_scale(b.fS);
+    const V aP3x = vmul(a.P3x, ka), aP3y = vmul(a.P3y, ka), aQ3x = vmul(a.Q3x, ka), aQ3y = vmul(a.Q3y, ka);
+    const V afS = vmul(a.fS, ka), acQP = vmul(a.cQP, ka);
+    const V bP3x = vmul(b.P3x, kb), bP3y = vmul(b.P3y, kb), bQ3x = vmul(b.Q3x, kb), bQ3y = vmul(b.Q3y, kb);
+    const V bfS = vmul(b.fS, kb), bcQP = vmul(b.cQP, kb);
     // Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11)
-    const V n7x = det2(a.Q3x, a.P3x, a.Q3y, a.P3y), n7y = vmul(a.fS, a.cQP), d7 = vmul(a.Q3y, a.P3y);
-    const V n8x = det2(b.Q3x, b.P3x, b.Q3y, b.P3y), n8y = vmul(b.fS, b.cQP), d8 = vmul(b.Q3y, b.P3y);
-    // Eq. 11 solved for a_K = a_G, b_K = b_G
-    const V den = vmul(d8, vmul(vsub(n7x, n7y), vadd(n7x, n7y)));
-    const V aK = vdiv(vmul(d7, det2(n8x, n8y, n7y, n7x)), den);
-    const V bK = vdiv(vmul(d7, det2(n8y, n8x, n7y, n7x)), den);
-    // Eq. 13 with P5 = (P3.x, f_S1) / P3.y, P6 = (P4.x, f_S2) / P4.y
-    const V P5x = vdiv(a.P3x, a.P3y), P5y = vdiv(a.fS, a.P3y);
-    const V P6x = vdiv(b.P3x, b.P3y), P6y = vdiv(b.fS, b.P3y);
-    const V uK = vsub(P6x, vfma(aK, P5x, vmul(bK, P5y)));
-    const V vK = vsub(P6y, vfma(bK, P5x, vmul(aK, P5y)));
+    const V n7x = det2(aQ3x, aP3x, aQ3y, aP3y), n7y = vmul(afS, acQP);
+    const V n8x = det2(bQ3x, bP3x, bQ3y, bP3y), n8y = vmul(bfS, bcQP);
+    // Eq. 11 and Eq. 13 over the common denominator Q4.y P4.y m
+    const V A = det2(n8x, n8y, n7y, n7x), B = det2(n8y, n8x, n7y, n7x);
+    const V m = vmul(vsub(n7x, n7y), vadd(n7x, n7y));
+    const V q = vmul(aQ3y, aP3y), bm = vmul(bQ3y, m);
+    const V aK = vmul(q, A), bK = vmul(q, B), dK = vmul(bP3y, bm);
+    const V uK = vfma(bP3x, bm, vneg(vmul(aQ3y, vfma(A, aP3x, vmul(B, afS)))));
+    const V vK = vfma(bfS, bm, vneg(vmul(aQ3y, vfma(B, aP3x, vmul(A, afS)))));
     // Eq. 14 in the M frames: H = T(M2) L T(-M1) with
     // L = T(ON2) R2^-1 K R1 T(-ON1), R1 = [[ONx, ONy, 0], [-ONy, ONx, 0], [0, 0, fS1]],
-    // R2^-1 = [[ONx, -ONy, 0], [ONy, ONx, 0], [0, 0, 1]], K = [[aK, uK, bK], [0, 1, 0], [bK, vK, aK]].
+    // R2^-1 = [[ONx, -ONy, 0], [ONy, ONx, 0], [0, 0, 1]], K = [[aK, uK, bK], [0, dK, 0], [bK, vK, aK]].
     const V o1x = a.onx.h, o1y = a.ony.h, o2x = b.onx.h, o2y = b.ony.h;
-    // K R1 (rows), in double-float
+    // K R1 (rows), in double-float; row 1 of K R1 is dK (-o1y, o1x, 0)
     const DF A00 = df_sub(df_prod(aK, o1x), df_prod(uK, o1y));
     const DF A01 = df_add(df_prod(aK, o1y), df_prod(uK, o1x));
     const DF A02 = df_prod(bK, a.fS);
     const DF A20 = df_sub(df_prod(bK, o1x), df_prod(vK, o1y));
     const DF A21 = df_add(df_prod(bK, o1y), df_prod(vK, o1x));
     const DF A22 = df_prod(aK, a.fS);
-    // R2^-1 (K R1): row 1 of K R1 is (-o1y, o1x, 0)
-    const DF L00 = df_add(df_mul(A00, o2x), df_prod(o2y, o1y));
-    const DF L01 = df_sub(df_mul(A01, o2x), df_prod(o2y, o1x));
+    const DF D1x = df_prod(dK, o1x), D1y = df_prod(dK, o1y);
+    // R2^-1 (K R1)
+    const DF L00 = df_add(df_mul(A00, o2x), df_mul(D1y, o2y));
+    const DF L01 = df_sub(df_mul(A01, o2x), df_mul(D1x, o2y));
     const DF L02 = df_mul(A02, o2x);
-    const DF L10 = df_sub(df_mul(A00, o2y), df_prod(o2x, o1y));
-    const DF L11 = df_add(df_mul(A01, o2y), df_prod(o2x, o1x));
+    const DF L10 = df_sub(df_mul(A00, o2y), df_mul(D1y, o2x));
+    const DF L11 = df_add(df_mul(A01, o2y), df_mul(D1x, o2x));
     const DF L12 = df_mul(A02, o2y);
     // fold T(-ON1) on the right (column 3 -= ON1.x col 1 + ON1.y col 2) and
     // T(ON2) on the left (rows 1, 2 += ON2 * row 3); ON1, ON2 as value + remainder

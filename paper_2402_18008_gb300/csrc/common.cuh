@@ -24,6 +24,11 @@ inline aca_status check_launch(const char *what)
 // SM count of the current device (queried once per device and cached).
 int sm_count();
 
+// 32-bit words per hypothesis that a ransac_aca workspace holds for P
+// problems (on the one-launch path of small batches one count per point
+// slice plus the hypothesis's 9 entries of H, else one count).
+size_t ransac_count_slots(int32_t P);
+
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

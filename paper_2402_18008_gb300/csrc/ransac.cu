@@ -206,6 +206,9 @@ struct Workspace {
     int64_t *item_off;           // [P+1] prefix of the work items over `order` (fixed counts)
     unsigned long long *counter; // [1] work counter
     int32_t *flags;              // [1] 1 = counts capacity exceeded
+    unsigned *done;              // [1] blocks finished (one-launch path); zero between calls
+    unsigned long long *best;    // [kFusedMaxP] packed best (count, ~index) per problem (one-launch
+                                 // path, whole-range items); zero between calls
     int32_t *order;              // [P] scoring order of the problems (fixed counts): largest N first
     int32_t *counts;             // [capacity]
     int64_t capacity;
@@ -213,18 +216,29 @@ struct Workspace {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Every layout starts with the same 256-byte control block (work counter,
+// overflow flag, the one-launch path's done counter and per-problem best),
+// so that a workspace shared by calls of different sizes and kinds keeps the
+// one-launch path's state in one place, written by nothing but that path,
+// which leaves it zero.
+static void carve_control(char *b, Workspace &w)
+{
+    w.counter = reinterpret_cast<unsigned long long *>(b);
+    w.flags = reinterpret_cast<int32_t *>(b + 8);
+    w.done = reinterpret_cast<unsigned *>(b + 16);
+    w.best = reinterpret_cast<unsigned long long *>(b + 32);
+}
+
 static Workspace carve(void *base, int32_t P, size_t bytes)
 {
     Workspace w;
     char *b = static_cast<char *>(base);
-    size_t o = 0;
+    carve_control(b, w);
+    size_t o = 256;
     w.hyp_off = reinterpret_cast<int64_t *>(b + o);
     o += align256(sizeof(int64_t) * (size_t)(P + 1));
     w.item_off = reinterpret_cast<int64_t *>(b + o);
     o += align256(sizeof(int64_t) * (size_t)(P + 1));
-    w.counter = reinterpret_cast<unsigned long long *>(b + o);
-    w.flags = reinterpret_cast<int32_t *>(b + o + 8);
-    o += 256;
     w.order = reinterpret_cast<int32_t *>(b + o);
     o += align256(sizeof(int32_t) * (size_t)P);
     w.counts = reinterpret_cast<int32_t *>(b + o);
@@ -279,14 +293,12 @@ static void carve_adaptive(void *base, int32_t P, int64_t total, Workspace &w, A
     char *b = static_cast<char *>(base);
     size_t counts_at = 0;
     adaptive_bytes(P, total, &a.rb, &a.cb, &counts_at);
-    size_t o = 0;
+    carve_control(b, w);                                   // done: unused by the adaptive variant
+    size_t o = 256;
     w.hyp_off = reinterpret_cast<int64_t *>(b + o);
     o += align256(sizeof(int64_t) * (size_t)(P + 1));
     w.item_off = reinterpret_cast<int64_t *>(b + o);
     o += align256(sizeof(int64_t) * (size_t)(P + 1));
-    w.counter = reinterpret_cast<unsigned long long *>(b + o);
-    w.flags = reinterpret_cast<int32_t *>(b + o + 8);
-    o += 256;
     w.order = reinterpret_cast<int32_t *>(b + o);          // unused by the adaptive variant
     o += align256(sizeof(int32_t) * (size_t)P);
     a.chunk_off = reinterpret_cast<int64_t *>(b + o);
@@ -983,6 +995,300 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// Small batches (at most kFusedMaxP problems, e.g. one image pair): the whole
+// RANSAC in ONE launch.  The work is items (problem p, chunk of HB hypotheses,
+// slice s of S point ranges); block b takes items b, b + G, b + 2G, ...
+// (every block derives the item layout from offsets and n_hyp itself: no
+// set-up kernel, no work counter).  An item issues the loads of its first
+// tile of points, samples and solves its HB hypotheses meanwhile, walks its
+// point range tile by tile (T points staged in shared memory at a time) and
+// stores its partial counts with plain stores into the slot of its slice,
+// part[s][hyp], so that no count needs clearing and no atomic adds are made;
+// the slice-0 item also stores each hypothesis's H.  A block that has
+// finished all of its items fences and counts itself done; the last one sums
+// the slots of every hypothesis, takes each problem's argmax (ties to the
+// lowest index), writes the mask and the outputs from the winner's stored H
+// (the bits its scoring used), and sets the done counter back to zero for
+// the next call.  Nothing waits on
+// another block.  The counts, the argmax, H and the mask are those of the
+// multi-kernel path bit for bit: integer sums do not depend on the split.
+// ---------------------------------------------------------------------------
+constexpr int32_t kFusedMaxP = 8;
+constexpr int kFusedSlices = 4;
+
+// 32-bit words per hypothesis in the workspace: on the one-launch path one
+// count slot per slice plus the hypothesis's 9 entries of H, else one count.
+constexpr int kFusedWords = kFusedSlices + 9;
+size_t ransac_count_slots(int32_t P) { return P <= kFusedMaxP ? (size_t)kFusedWords : 1; }
+
+template <int HPT>
+__global__ void __launch_bounds__(512) ransac_fused_kernel(const float4 *__restrict__ corr,
+                                                           const int64_t *__restrict__ offsets,
+                                                           const int32_t *__restrict__ n_hyp, int32_t P, float thr,
+                                                           uint64_t seed, uint32_t prob_base, int T, Workspace ws,
+                                                           float *__restrict__ best_H, int32_t *__restrict__ best_count,
+                                                           int32_t *__restrict__ best_hyp,
+                                                           int32_t *__restrict__ hyp_counts, uint8_t *__restrict__ mask)
+{
+    constexpr int HB = 32 * HPT;
+    extern __shared__ float4 smem4[];
+    const int W = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4 *tile = smem4;                                                   // [T/2][2]: point pairs
+    float *Hs = reinterpret_cast<float *>(smem4 + T);                       // [HB][12]
+    int32_t *red = reinterpret_cast<int32_t *>(Hs + HB * 12);               // [W][HB]
+    __shared__ int64_t s_item0[kFusedMaxP + 1], s_hoff[kFusedMaxP + 1], s_off[kFusedMaxP + 1];
+    __shared__ int32_t s_overflow, s_last, s_best, s_S;
+    __shared__ int32_t s_cnt[16], s_idx[16];
+    __shared__ float sH[9];
+    const float rthr = target_scale(thr);
+    const float nanv = __int_as_float(0x7fc00000);
+
+    grid_launch_dependents();
+    grid_dependency_wait();
+    if (wid == 0) {
+        int64_t k = 0, chunks = 0;
+        if (lane < P) {
+            const int64_t N = offsets[lane + 1] - offsets[lane];
+            k = n_hyp[lane] > 0 ? n_hyp[lane] : 0;
+            if (N >= 4 && k > 0)
+                chunks = (k + HB - 1) / HB;
+            s_off[lane] = offsets[lane];
+        }
+        if (lane == 0) s_off[P] = offsets[P];
+        // whole point ranges per item when the hypothesis chunks alone fill
+        // half of the grid, else kFusedSlices point ranges per chunk (every
+        // block takes the same decision)
+        int64_t allc = chunks;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) allc += __shfl_xor_sync(0xffffffffu, allc, o);
+        const int S = 2 * allc >= (int64_t)gridDim.x ? 1 : kFusedSlices;
+        int64_t ik = k, ii = chunks * S;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t a = __shfl_up_sync(0xffffffffu, ik, o), b = __shfl_up_sync(0xffffffffu, ii, o);
+            if (lane >= o) { ik += a; ii += b; }
+        }
+        if (lane < P) { s_hoff[lane + 1] = ik; s_item0[lane + 1] = ii; }
+        if (lane == 0) { s_hoff[0] = 0; s_item0[0] = 0; s_S = S; }
+        const int64_t tot = __shfl_sync(0xffffffffu, ik, 31);
+        // the counts hold S slots of tot values each, then 9 floats per
+        // hypothesis (its H)
+        if (lane == 0) s_overflow = tot > ws.capacity / kFusedWords;
+    }
+    __syncthreads();
+    const int64_t total_items = s_overflow ? 0 : s_item0[P];
+    const int64_t total_h = s_hoff[P];
+    const int S = s_S;
+    int32_t *part = ws.counts;                                              // [S][total_h] (S > 1)
+    float *hst = reinterpret_cast<float *>(ws.counts + (int64_t)kFusedSlices * total_h);  // [total_h][9]
+
+    for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
+        int32_t p = 0;
+        while (s_item0[p + 1] <= item) ++p;
+        const int64_t r = item - s_item0[p];
+        const int32_t chunk = (int32_t)(r / S), slice = (int32_t)(r % S);
+        const int64_t base = s_off[p];
+        const uint32_t N = (uint32_t)(s_off[p + 1] - base);
+        const int64_t hbase = s_hoff[p];
+        const int32_t k = (int32_t)(s_hoff[p + 1] - hbase);
+        const int32_t h0 = chunk * HB, nh = min(HB, k - h0);
+        const int64_t L = (((int64_t)N + S - 1) / S + 1) & ~(int64_t)1;     // even slice length
+        const int64_t i0 = (int64_t)slice * L;
+        const int64_t ni = max((int64_t)0, min(L, (int64_t)N - i0));
+        const float4 *cp = corr + base;
+        auto stage = [&](int64_t t0, int nt) {
+            const int npairs = (nt + 1) >> 1;
+            for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+                const int64_t i = i0 + t0 + 2 * q;
+                const float4 a = cp[i];
+                const float4 b = (2 * q + 1 < nt) ? cp[i + 1] : make_float4(nanv, nanv, nanv, nanv);
+                tile[2 * q] = make_float4(a.x, b.x, a.y, b.y);
+                tile[2 * q + 1] = make_float4(F_MUL(a.z, rthr), F_MUL(b.z, rthr), F_MUL(a.w, rthr), F_MUL(b.w, rthr));
+            }
+        };
+        // the first tile's loads go out before the hypotheses are solved, so
+        // that their latencies overlap
+        if (ni > 0) stage(0, (int)min((int64_t)T, ni));
+
+        // hypotheses of this item -> shared memory (test form, see inlier);
+        // the slice-0 item also keeps each H for the final re-use
+        if ((int)threadIdx.x < HB) {
+            float H[9], G[9];
+            const int t = threadIdx.x;
+            bool valid = false;
+            if (t < nh)
+                valid = make_hypothesis(cp, N, seed, prob_base + (uint32_t)p, (uint32_t)(h0 + t), H);
+            if (!valid) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) H[i] = 0.0f;   // scores nothing (w == 0)
+            }
+            if (slice == 0 && t < nh) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) hst[(hbase + h0 + t) * 9 + i] = H[i];
+            }
+            to_test_form(G, H, thr);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Hs[t * 12 + i] = G[i];
+            Hs[t * 12 + 9] = valid ? 1.0f : 0.0f;
+        }
+        __syncthreads();          // first tile and Hs written
+        int cnt[HPT];
+        float2 g[HPT][9];
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) {
+            cnt[j] = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float v = Hs[(lane + 32 * j) * 12 + i];
+                g[j][i] = make_float2(v, v);
+            }
+        }
+        for (int64_t t0 = 0; t0 < ni; t0 += T) {
+            const int nt = (int)min((int64_t)T, ni - t0);
+            const int npairs = (nt + 1) >> 1;
+            if (t0 > 0) {
+                __syncthreads();  // the previous tile is consumed
+                stage(t0, nt);
+                __syncthreads();
+            }
+            int q = wid;
+            for (; q + W < npairs; q += 2 * W) {
+                const float4 p0 = tile[2 * q], q0 = tile[2 * q + 1];
+                const float4 p1 = tile[2 * (q + W)], q1 = tile[2 * (q + W) + 1];
+#pragma unroll
+                for (int j = 0; j < HPT; ++j)
+                    cnt[j] += inlier2(g[j], p0, q0) + inlier2(g[j], p1, q1);
+            }
+            for (; q < npairs; q += W) {
+                const float4 p0 = tile[2 * q], q0 = tile[2 * q + 1];
+#pragma unroll
+                for (int j = 0; j < HPT; ++j) cnt[j] += inlier2(g[j], p0, q0);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) red[wid * HB + lane + 32 * j] = cnt[j];
+        __syncthreads();
+        int32_t c = -1;
+        if ((int)threadIdx.x < nh) {
+            c = 0;
+            for (int w = 0; w < W; ++w) c += red[w * HB + threadIdx.x];
+            // a degenerate sample is marked in slot 0 (its counts are 0)
+            if (Hs[threadIdx.x * 12 + 9] == 0.0f) c = slice == 0 ? -1 : 0;
+            if (S > 1)
+                part[(int64_t)slice * total_h + hbase + h0 + threadIdx.x] = c;
+            else if (hyp_counts)
+                hyp_counts[hbase + h0 + threadIdx.x] = c;
+        }
+        if (S == 1 && (int)threadIdx.x < HB) {
+            // whole range: the counts are final; the chunk's best (highest
+            // count, then lowest index) joins the problem's packed maximum
+            int32_t bi = (int)threadIdx.x < nh ? h0 + (int32_t)threadIdx.x : 0x7fffffff;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int32_t c2 = __shfl_down_sync(0xffffffffu, c, o), i2 = __shfl_down_sync(0xffffffffu, bi, o);
+                if (c2 > c || (c2 == c && i2 < bi)) { c = c2; bi = i2; }
+            }
+            if (lane == 0 && c >= 0)
+                atomicMax(&ws.best[p], ((unsigned long long)(uint32_t)c << 32) | (unsigned long long)(0xffffffffu - (uint32_t)bi));
+        }
+        __syncthreads();          // Hs and red are rewritten by the next item
+    }
+
+    // the last block to finish takes the argmax of every problem
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ws.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    const bool overflow = s_overflow != 0;
+    for (int32_t p = 0; p < P; ++p) {
+        const int64_t base = s_off[p];
+        const int64_t N = s_off[p + 1] - base;
+        const int64_t hb = s_hoff[p];
+        const int32_t k = (int32_t)(s_hoff[p + 1] - hb);
+        int32_t bc = -1, bi = 0x7fffffff;
+        if (!overflow && N >= 4 && S == 1) {
+            // the packed maximum of the items (0: no valid hypothesis)
+            if (threadIdx.x == 0) {
+                const unsigned long long v = __ldcg(&ws.best[p]);
+                if (v) { bc = (int32_t)(v >> 32); bi = (int32_t)(0xffffffffu - (uint32_t)v); }
+            }
+        } else if (!overflow && N >= 4) {
+            // all slots of four hypotheses per thread in flight at once (one
+            // L2 round trip per 4 x blockDim hypotheses)
+            for (int32_t h0 = threadIdx.x; h0 < k; h0 += 4 * (int32_t)blockDim.x) {
+                constexpr int SL = kFusedSlices;
+                int32_t c[4][SL];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t h = h0 + u * (int32_t)blockDim.x;
+#pragma unroll
+                    for (int sl = 0; sl < SL; ++sl)
+                        c[u][sl] = h < k ? __ldcg(&part[(int64_t)sl * total_h + hb + h]) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t h = h0 + u * (int32_t)blockDim.x;
+                    if (h >= k) break;
+                    int32_t t = c[u][0];
+                    if (t >= 0) {
+#pragma unroll
+                        for (int sl = 1; sl < SL; ++sl) t += c[u][sl];
+                    }
+                    if (hyp_counts) hyp_counts[hb + h] = t;
+                    if (t > bc) { bc = t; bi = h; }
+                }
+            }
+        } else if (!overflow && hyp_counts) {
+            for (int32_t h = threadIdx.x; h < k; h += blockDim.x) hyp_counts[hb + h] = -1;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int32_t c = __shfl_down_sync(0xffffffffu, bc, o), i = __shfl_down_sync(0xffffffffu, bi, o);
+            if (c > bc || (c == bc && i < bi)) { bc = c; bi = i; }
+        }
+        if (lane == 0) { s_cnt[wid] = bc; s_idx[wid] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bc = s_cnt[0]; bi = s_idx[0];
+            for (int w = 1; w < W; ++w)
+                if (s_cnt[w] > bc || (s_cnt[w] == bc && s_idx[w] < bi)) { bc = s_cnt[w]; bi = s_idx[w]; }
+            if (overflow) { bi = -2; bc = 0; }
+            else if (bc < 0) { bi = -1; bc = 0; }
+            s_best = bi;
+            float H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if (bi >= 0) {        // the winner's H as its scoring item solved it
+#pragma unroll
+                for (int i = 0; i < 9; ++i) H[i] = __ldcg(&hst[(hb + bi) * 9 + i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) sH[i] = H[i];
+            best_hyp[p] = bi;
+            best_count[p] = bc;
+            normalize_frob(H);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) best_H[9 * p + i] = H[i];
+        }
+        __syncthreads();
+        if (mask) {
+            float H[9], G[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) H[i] = sH[i];
+            to_test_form(G, H, thr);
+            write_mask(G, corr + base, N, target_scale(thr), s_best >= 0, mask + base);
+        }
+        __syncthreads();          // s_cnt, sH are reused by the next problem
+    }
+    if (threadIdx.x < kFusedMaxP)
+        ws.best[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0)
+        *ws.done = 0u;
+}
+
 // Adaptive finish, one block of 512 threads per problem: inclusive prefix
 // maxima I of the counts, tile by tile (2048 hypotheses), until the stop is
 // certain within the scanned part; the stop index is the first i in 1..k with
@@ -1167,7 +1473,7 @@ extern "C" size_t ransac_aca_workspace_size(int32_t P, int64_t total_hyps)
 {
     if (P < 0 || total_hyps < 0)
         return 0;
-    return header_bytes(P) + align256(sizeof(int32_t) * (size_t)total_hyps);
+    return header_bytes(P) + align256(sizeof(int32_t) * (size_t)total_hyps * ransac_count_slots(P));
 }
 
 extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, const int32_t *n_hyp, int32_t P,
@@ -1203,12 +1509,36 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
     const int HB = 32 * HPT;
     const cudaStream_t st = as_stream(stream);
     const Workspace ws = carve(workspace, P, workspace_bytes);
+    const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
+    const int threads = 32 * W;
+    const float4 *c4 = reinterpret_cast<const float4 *>(corr);
+    aca_status s = ACA_OK;
+
+    if (P <= kFusedMaxP) {
+        // small batches: everything in one launch (ransac_fused_kernel)
+#define ACA_FUSED(HPTV)                                                                                       \
+    {                                                                                                          \
+        auto k = ransac_fused_kernel<HPTV>;                                                                    \
+        if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                                     (int)smem) != cudaSuccess)                                \
+            return set_error(ACA_ERR_CUDA, "ransac_aca: cannot reserve %zu bytes of shared memory", smem);    \
+        const int grid = params->grid_blocks > 0 ? params->grid_blocks : resident_grid(k, threads, smem, 1 << 30); \
+        launch_after_previous(k, dim3(grid), dim3(threads), smem, st, c4, offsets, n_hyp, P, params->threshold_px, \
+                              params->seed, params->problem_base, T, ws, best_H, best_count, best_hyp, hyp_counts, \
+                              inlier_mask);                                                                    \
+    }
+        if (HPT == 1) ACA_FUSED(1)
+        else if (HPT == 2) ACA_FUSED(2)
+        else ACA_FUSED(4)
+#undef ACA_FUSED
+        return check_launch("ransac_aca (one launch)");
+    }
 
     // counts of small workspaces are cleared by the prep kernel itself
     const bool zero_in_prep = ws.capacity <= 65536;
     const bool by_size = P >= 64;     // problems by size, largest first (ransac_prep_kernel)
     ransac_prep_kernel<<<1, 1024, 0, st>>>(offsets, n_hyp, P, HB, T, ws, zero_in_prep, by_size);
-    aca_status s = check_launch("ransac_aca (prep)");
+    s = check_launch("ransac_aca (prep)");
     if (s != ACA_OK) return s;
     if (!zero_in_prep) {
         const int threads = 256;
@@ -1216,9 +1546,6 @@ extern "C" aca_status ransac_aca(const float *corr, const int64_t *offsets, cons
         launch_after_previous(zero_counts_kernel, dim3(grid), dim3(threads), 0, st, ws, P);
         if ((s = check_launch("ransac_aca (zero)")) != ACA_OK) return s;
     }
-    const size_t smem = (size_t)T * 16 + (size_t)HB * 12 * 4 + (size_t)W * HB * 4;
-    const int threads = 32 * W;
-    const float4 *c4 = reinterpret_cast<const float4 *>(corr);
 #define ACA_SCORE(HPTV)                                                                                       \
     {                                                                                                          \
         auto k = ransac_score_kernel<HPTV, false>;                                                             \

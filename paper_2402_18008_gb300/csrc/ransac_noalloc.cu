@@ -22,7 +22,9 @@
 // library's context is created).  All calls share the one array and each call re-initialises what
 // must start at zero (the work counter, the overflow flag and the counts),
 // so calls whose kernels overlap on the GPU (two streams, or two host threads)
-// race on it and must be serialised by the caller.
+// race on it and must be serialised by the caller.  The done counter of the
+// one-launch path (at most 8 problems) must be zero before a call and every
+// call leaves it zero; the array is zero when the module loads.
 #include <mutex>
 #include <vector>
 
@@ -82,7 +84,8 @@ extern "C" aca_status ransac_aca_noalloc(const float *corr, const int64_t *offse
     // n_hyp above it is caught by ransac_aca's overflow check (best_hyp = -2,
     // nothing scored, no write past the caller's hyp_counts) as it is with a
     // caller workspace of the same size.
-    const size_t bytes = ransac_aca_workspace_size(P, 0) + sizeof(int32_t) * (size_t)total_hyps;
+    const size_t bytes =
+        ransac_aca_workspace_size(P, 0) + sizeof(int32_t) * (size_t)total_hyps * aca::ransac_count_slots(P);
     return ransac_aca(corr, offsets, n_hyp, P, params, best_H, best_count, best_hyp, hyp_counts, inlier_mask,
                       scratch, bytes, stream);
 }

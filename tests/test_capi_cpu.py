@@ -37,7 +37,10 @@ def test_library_exports_every_declared_symbol():
 def test_workspace_size_is_host_only_and_monotone():
     ws = _lib.ransac_aca_workspace_size
     assert ws(1, 4096) >= 4 * 4096
-    assert ws(512, 700000) > ws(512, 1000) > ws(1, 1000)
+    assert ws(512, 700000) > ws(512, 1000) > ws(9, 1000)
+    # at most 8 problems: four count slots per hypothesis (one per point
+    # range of the one-launch path)
+    assert ws(8, 1000) - ws(8, 0) >= 4 * 4 * 1000 > ws(9, 1000) - ws(9, 0)
     assert ws(-1, 10) == 0 and ws(4, -1) == 0
     assert ws(1, 0) % 256 == 0
 
@@ -103,7 +106,7 @@ def test_adaptive_ransac_rejects_bad_arguments():
     L = _lib.load()
     p = _lib.RansacParams(threshold_px=3.0, seed=1)
     need = _lib.ransac_aca_adaptive_workspace_size(1, 64)
-    assert need > _lib.ransac_aca_workspace_size(1, 64)
+    assert need > _lib.ransac_aca_workspace_size(9, 64)
     assert _lib.ransac_aca_adaptive_workspace_size(512, 8388608) > _lib.ransac_aca_adaptive_workspace_size(512, 1000)
     assert _lib.ransac_aca_adaptive_workspace_size(-1, 5) == 0
     buf = (ctypes.c_uint8 * (need + 512))()

@@ -135,6 +135,45 @@ def test_tuning_does_not_change_results(tune):
         assert np.array_equal(base[key], alt[key]), key
 
 
+@pytest.mark.parametrize("tune", [dict(), dict(block_warps=4, hyps_per_thread=1, tile_points=256),
+                                  dict(block_warps=16, hyps_per_thread=4, tile_points=4096),
+                                  dict(block_warps=8, hyps_per_thread=2, tile_points=64, grid_blocks=1),
+                                  dict(block_warps=2, hyps_per_thread=2, tile_points=128, grid_blocks=7)])
+def test_one_launch_path_equals_the_multi_kernel_path(tune):
+    # at most 8 problems run the whole RANSAC in one launch (partial counts
+    # per point range, the last block to finish takes the argmax); the same
+    # problems inside a batch of 14 take the multi-kernel path: every output
+    # must agree bit for bit, whatever the launch shape (one block included)
+    rb = workloads.ransac_batch(P=14, seed=12, n_max=3000, cap=1024)
+    big = _np(_run(rb.corr, rb.offsets, rb.n_hyp, 3.0, 8))
+    hoff = np.concatenate([[0], np.cumsum(rb.n_hyp)])
+    for lo, hi in ((0, 6), (6, 14), (9, 10)):
+        a, b = int(rb.offsets[lo]), int(rb.offsets[hi])
+        small = _np(_run(rb.corr[a:b], rb.offsets[lo:hi + 1] - a, rb.n_hyp[lo:hi], 3.0, 8, problem_base=lo, **tune))
+        for key in ("best_hyp", "best_count", "best_H"):
+            assert np.array_equal(small[key], big[key][lo:hi]), (key, lo)
+        assert np.array_equal(small["hyp_counts"], big["hyp_counts"][hoff[lo]:hoff[hi]]), lo
+        assert np.array_equal(small["inlier_mask"][:b - a], big["inlier_mask"][a:b]), lo
+
+
+def test_one_launch_path_repeated_calls_and_graph_replay():
+    rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=0)
+    plan = api.RansacPlan(cuda(rp.corr), cuda(np.array([0, 2000], np.int64)), cuda(np.array([4096], np.int32)),
+                          3.0, 2024, 4096, want_counts=True, want_mask=True)
+    ref = _np(plan.run())
+    for _ in range(3):
+        r = _np(plan.run())
+        for key in ("best_hyp", "best_count", "best_H", "hyp_counts", "inlier_mask"):
+            assert np.array_equal(r[key], ref[key]), key
+    plan.capture()
+    for _ in range(5):
+        r = _np(plan.replay())
+    for key in ("best_hyp", "best_count", "best_H", "hyp_counts", "inlier_mask"):
+        assert np.array_equal(r[key], ref[key]), key
+    # every call leaves the done counter of the control block at zero
+    assert int(plan.workspace[16:20].cpu().view(torch.int32).item()) == 0
+
+
 def test_graph_capture_replay_matches_eager():
     rb = workloads.ransac_batch(P=32, seed=5, n_max=2000, cap=1024)
     tot = int(rb.n_hyp.sum())
