@@ -89,13 +89,32 @@ def _check(st: int):
         raise AcaError(st, load().aca_last_error().decode())
 
 
-def _stream(stream=None) -> int:
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return int(s.cuda_stream)
+def _L():
+    """The loaded library (no lock once it is loaded)."""
+    return _lib if _lib is not None else load()
+
+
+try:                                   # the current stream as a raw handle, without a Stream object
+    _raw_stream = torch._C._cuda_getCurrentRawStream
+except AttributeError:                 # pragma: no cover
+    def _raw_stream(device: int) -> int:
+        return int(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _stream(stream=None, like=None) -> int:
+    """Raw handle of `stream`, else of the current stream of `like`'s device
+    (of the current device for a host tensor or None)."""
+    if stream is not None:
+        return int(stream.cuda_stream)
+    dev = like.get_device() if like is not None else -1
+    return _raw_stream(dev if dev >= 0 else torch.cuda.current_device())
 
 
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    return None if t is None else t.data_ptr()
+
+
+_F32, _U8 = torch.float32, torch.uint8
 
 
 def _need(t, name, dtype, rows=None, host_ok=False):
@@ -103,20 +122,25 @@ def _need(t, name, dtype, rows=None, host_ok=False):
     # writes them over the host link itself; nothing runs on the CPU)
     if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
         raise ValueError(f"{name} must be a CUDA tensor" + (" or a pinned host tensor" if host_ok else ""))
-    if t.dtype != dtype:
+    if t.dtype is not dtype:
         raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     if rows is not None:
-        if t.dim() != 2 or t.shape[0] != rows or t.stride(1) != 1:
+        sh = t.shape
+        if len(sh) != 2 or sh[0] != rows or t.stride(1) != 1:
             raise ValueError(f"{name} must be ({rows}, ld) with unit stride along ld")
 
 
 def _ld(*ts):
-    lds = {t.stride(0) for t in ts if t is not None}
-    if len(lds) != 1:
-        raise ValueError("all planes must share one leading dimension (row stride)")
-    ld = lds.pop()
+    ld = None
     for t in ts:
-        if t is not None and t.shape[1] > ld:
+        if t is None:
+            continue
+        s0 = t.stride(0)
+        if ld is None:
+            ld = s0
+        elif s0 != ld:
+            raise ValueError("all planes must share one leading dimension (row stride)")
+        if t.shape[1] > ld:
             raise ValueError("row length exceeds the leading dimension")
     return ld
 
@@ -130,7 +154,7 @@ def aca_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
         _need(flags, "flags", torch.uint8, host_ok=True)
     ld = _ld(pts, H)
     n = pts.shape[1] if n is None else n
-    _check(load().aca_solve(_ptr(pts), _ptr(H), _ptr(flags), n, ld, norm, ctypes.c_void_p(_stream(stream))))
+    _check(_L().aca_solve(pts.data_ptr(), H.data_ptr(), _ptr(flags), n, ld, norm, _stream(stream, pts)))
 
 
 def sks_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
@@ -141,7 +165,7 @@ def sks_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
         _need(flags, "flags", torch.uint8)
     ld = _ld(pts, H)
     n = pts.shape[1] if n is None else n
-    _check(load().sks_solve(_ptr(pts), _ptr(H), _ptr(flags), n, ld, norm, ctypes.c_void_p(_stream(stream))))
+    _check(_L().sks_solve(pts.data_ptr(), H.data_ptr(), _ptr(flags), n, ld, norm, _stream(stream, pts)))
 
 
 def aca_rect_solve(tgt, rect, H, n=None, stream=None):
@@ -151,7 +175,7 @@ def aca_rect_solve(tgt, rect, H, n=None, stream=None):
     ld = _ld(tgt, H)
     n = tgt.shape[1] if n is None else n
     x0, y0, w, r = (float(v) for v in rect)
-    _check(load().aca_rect_solve(_ptr(tgt), x0, y0, w, r, _ptr(H), n, ld, ctypes.c_void_p(_stream(stream))))
+    _check(_L().aca_rect_solve(tgt.data_ptr(), x0, y0, w, r, H.data_ptr(), n, ld, _stream(stream, tgt)))
 
 
 def aca_affine_solve(pts, H, n=None, norm=ACA_NORM_NONE, stream=None):
@@ -160,7 +184,7 @@ def aca_affine_solve(pts, H, n=None, norm=ACA_NORM_NONE, stream=None):
     _need(H, "H", torch.float32, 9)
     ld = _ld(pts, H)
     n = pts.shape[1] if n is None else n
-    _check(load().aca_affine_solve(_ptr(pts), _ptr(H), n, ld, norm, ctypes.c_void_p(_stream(stream))))
+    _check(_L().aca_affine_solve(pts.data_ptr(), H.data_ptr(), n, ld, norm, _stream(stream, pts)))
 
 
 def aca_backward(pts, grad_H, grad_tgt, n=None, stream=None):
@@ -170,7 +194,7 @@ def aca_backward(pts, grad_H, grad_tgt, n=None, stream=None):
     _need(grad_tgt, "grad_tgt", torch.float32, 8)
     ld = _ld(pts, grad_H, grad_tgt)
     n = pts.shape[1] if n is None else n
-    _check(load().aca_backward(_ptr(pts), _ptr(grad_H), _ptr(grad_tgt), n, ld, ctypes.c_void_p(_stream(stream))))
+    _check(_L().aca_backward(pts.data_ptr(), grad_H.data_ptr(), grad_tgt.data_ptr(), n, ld, _stream(stream, pts)))
 
 
 def aca_rect_backward(tgt, rect, grad_H, grad_tgt, n=None, stream=None):
@@ -181,8 +205,8 @@ def aca_rect_backward(tgt, rect, grad_H, grad_tgt, n=None, stream=None):
     ld = _ld(tgt, grad_H, grad_tgt)
     n = tgt.shape[1] if n is None else n
     x0, y0, w, r = (float(v) for v in rect)
-    _check(load().aca_rect_backward(_ptr(tgt), x0, y0, w, r, _ptr(grad_H), _ptr(grad_tgt), n, ld,
-                                    ctypes.c_void_p(_stream(stream))))
+    _check(_L().aca_rect_backward(tgt.data_ptr(), x0, y0, w, r, grad_H.data_ptr(), grad_tgt.data_ptr(), n, ld,
+                                  _stream(stream, tgt)))
 
 
 def ransac_aca_workspace_size(P: int, total_hyps: int) -> int:
@@ -220,7 +244,7 @@ def ransac_aca(corr, offsets, n_hyp, params: RansacParams, best_H, best_count, b
             raise ValueError("inlier_mask too small")
     _check(load().ransac_aca(_ptr(corr), _ptr(offsets), _ptr(n_hyp), P, ctypes.byref(params), _ptr(best_H),
                              _ptr(best_count), _ptr(best_hyp), _ptr(hyp_counts), _ptr(inlier_mask),
-                             _ptr(workspace), workspace.numel(), ctypes.c_void_p(_stream(stream))))
+                             _ptr(workspace), workspace.numel(), _stream(stream, corr)))
 
 
 def aca_sample_indices(N: int, n_hyp: int, seed: int, problem: int, idx, stream=None):
@@ -229,7 +253,7 @@ def aca_sample_indices(N: int, n_hyp: int, seed: int, problem: int, idx, stream=
     if not idx.is_contiguous() or idx.numel() < 4 * n_hyp:
         raise ValueError("idx must be a contiguous (n_hyp, 4) int32 tensor")
     _check(load().aca_sample_indices(int(N), int(n_hyp), int(seed), int(problem), _ptr(idx),
-                                     ctypes.c_void_p(_stream(stream))))
+                                     _stream(stream, idx)))
 
 
 def ransac_aca_noalloc(corr, offsets, n_hyp, total_hyps: int, params: RansacParams, best_H, best_count, best_hyp,
@@ -263,7 +287,7 @@ def ransac_aca_noalloc(corr, offsets, n_hyp, total_hyps: int, params: RansacPara
             raise ValueError("inlier_mask too small")
     _check(load().ransac_aca_noalloc(_ptr(corr), _ptr(offsets), _ptr(n_hyp), P, int(total_hyps), ctypes.byref(params),
                                      _ptr(best_H), _ptr(best_count), _ptr(best_hyp), _ptr(hyp_counts),
-                                     _ptr(inlier_mask), ctypes.c_void_p(_stream(stream))))
+                                     _ptr(inlier_mask), _stream(stream, corr)))
 
 
 def aca_refit(corr, offsets, H, mask=None, lm_iters=10, n_used=None, rms=None, stream=None):
@@ -288,7 +312,7 @@ def aca_refit(corr, offsets, H, mask=None, lm_iters=10, n_used=None, rms=None, s
             if t.numel() < P or not t.is_contiguous():
                 raise ValueError(f"{nm} must be a contiguous (P,) tensor")
     _check(load().aca_refit(_ptr(corr), _ptr(offsets), _ptr(mask), P, int(lm_iters), _ptr(H), _ptr(n_used),
-                            _ptr(rms), ctypes.c_void_p(_stream(stream))))
+                            _ptr(rms), _stream(stream, corr)))
 
 
 def ransac_aca_adaptive_workspace_size(P: int, total_max_hyps: int) -> int:
@@ -333,4 +357,4 @@ def ransac_aca_adaptive(corr, offsets, max_hyp, total_max_hyps, params: RansacPa
     _check(load().ransac_aca_adaptive(_ptr(corr), _ptr(offsets), _ptr(max_hyp), P, int(total_max_hyps),
                                       ctypes.byref(params), float(confidence), _ptr(best_H), _ptr(best_count),
                                       _ptr(best_hyp), _ptr(n_evaluated), _ptr(hyp_counts), _ptr(inlier_mask),
-                                      _ptr(workspace), workspace.numel(), ctypes.c_void_p(_stream(stream))))
+                                      _ptr(workspace), workspace.numel(), _stream(stream, corr)))

@@ -70,6 +70,27 @@ class PinnedSolver:
             cur.wait_stream(s)
 
 
+def shard_ranges(costs, world: int):
+    """Split problems 0..P-1 over `world` ranks as contiguous ranges of about
+    equal total cost (e.g. hypotheses x points per RANSAC problem): rank r
+    takes [start_r, start_{r+1}), start_r the first problem whose cost prefix
+    reaches r / world of the total.  Contiguous ranges keep the sampling
+    streams: a rank runs its range with problem_base = start_r and gets the
+    same results as one run over all problems.  Host logic only."""
+    import numpy as np
+    c = np.asarray(costs, dtype=np.float64)
+    P = c.size
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    pre = np.concatenate([[0.0], np.cumsum(c)])
+    tot = pre[-1]
+    starts = [0] + [int(np.searchsorted(pre[1:], tot * r / world, side="left")) + 1 if tot > 0 else (P * r) // world
+                    for r in range(1, world)] + [P]
+    for r in range(1, world + 1):                      # non-decreasing, within [0, P]
+        starts[r] = min(P, max(starts[r], starts[r - 1]))
+    return [(starts[r], starts[r + 1]) for r in range(world)]
+
+
 def rect_solve(tgt: torch.Tensor, rect, out: torch.Tensor | None = None):
     """Rectangle-source ACA (Eq. 42).  tgt: (8, ld) float32; rect = (x0, y0, w, r)."""
     _require_cuda(tgt, "tgt")

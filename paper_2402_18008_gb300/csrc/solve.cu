@@ -8,11 +8,11 @@
 // with streaming (evict-first) stores.  A persistent grid strides over the
 // quads; each thread copies its next quad's 16 float4 into its own slots of a
 // two-stage shared-memory ring (cp.async) while it solves the current one, so
-// the loads of the next step are in flight during the arithmetic (the ACA
-// paths; SKS, bound by its arithmetic, loads directly and runs two sets per
-// packed f32x2 instruction).  When the layout does
-// not allow 16-byte accesses a scalar variant (one set per thread, coalesced
-// 4-byte accesses) runs instead.
+// the loads of the next step are in flight during the arithmetic (ACA, and
+// SKS without flags, which runs two sets per packed f32x2 instruction; the
+// flagged SKS loads directly).  When the layout does not allow 16-byte
+// accesses a scalar variant (one set per thread, coalesced 4-byte accesses)
+// runs instead.
 #include "aca_math.cuh"
 #include "common.cuh"
 
@@ -286,14 +286,18 @@ static aca_status launch_solve(const float *pts, float *H, uint8_t *flags, int64
     // prefetching pays (0.95 -> 0.98 of copy bandwidth) at 2 blocks of 128
     // threads per SM.  With the flags (~490 instructions) the arithmetic
     // leads and a third block per SM pays (58.8 against 55.1 G sets/s with
-    // direct loads).  SKS, bound by its arithmetic, runs best on direct loads
-    // in 256-thread blocks (43.0 against 42.2 on the ring at 3 blocks).
-    constexpr bool kRing = SOLVER == kAca;
-    constexpr int kRingBlocks = FLAGS ? 3 : kRingBlocksPerSm;
+    // direct loads).  SKS without flags, division-free and packed, runs best
+    // on the ring with 4 blocks per SM (2^26 sets: 46.98 G sets/s, against
+    // 46.48 at 3 blocks, 45.26 at 2 and 45.55 with direct loads in
+    // 256-thread blocks); with flags it takes its sets one by one on direct
+    // loads.
+    constexpr bool kRing = SOLVER == kAca || !FLAGS;
+    constexpr int kRingBlocks = SOLVER == kSks ? 4 : (FLAGS ? 3 : kRingBlocksPerSm);
     if (kRing && vec) {
         if constexpr (kRing) {
-            const aca_status r = launch_ring<16, kRingBlocks>(solve_ring_kernel<SOLVER, NORM, FLAGS>, "aca_solve", n,
-                                                              st, pts, H, flags, n, ld);
+            const aca_status r = launch_ring<16, kRingBlocks>(solve_ring_kernel<SOLVER, NORM, FLAGS>,
+                                                              SOLVER == kAca ? "aca_solve" : "sks_solve", n, st, pts,
+                                                              H, flags, n, ld);
             if (r != ACA_OK)
                 return r;
         }
