@@ -542,8 +542,10 @@ def row_latency(torch, _lib, pts, H, n_total, stream):
         torch.cuda.synchronize()
         t = time_region(torch, g.replay, 10, stream) / 100
         eager = time_region(torch, f, 200, stream)
+        prepared = _lib.prepare_aca_solve(pts, H, None, n=m)
+        prep = time_region(torch, prepared, 200, stream)
         res[str(m)] = {"us": t * 1e3, "ns_per_set": t * 1e6 / m, "eager_call_us": eager * 1e3,
-                       "paper_rtx3090_fp64_us": PAPER_TABLE8_ACA_US.get(m)}
+                       "prepared_call_us": prep * 1e3, "paper_rtx3090_fp64_us": PAPER_TABLE8_ACA_US.get(m)}
     return {"aca_latency_sweep": res}
 
 
@@ -902,7 +904,15 @@ def row_diff(torch, _lib, rect, stream, dev, ctx):
     for f in (fwd_bwd, plain, torch_fwd_bwd):
         for _ in range(5):
             f()
+    fwd_p = _lib.prepare_aca_rect_solve(tgt, rect.rect, Hr)
+    bwd_p = _lib.prepare_aca_rect_backward(tgt, rect.rect, gH, gT)
+
+    def fwd_bwd_prepared():
+        fwd_p()
+        bwd_p()
+    fwd_bwd_prepared()
     tfb = time_region(torch, fwd_bwd, 200, stream)
+    tfp = time_region(torch, fwd_bwd_prepared, 200, stream)
     tpl = time_region(torch, plain, 200, stream)
     ttt = time_region(torch, torch_fwd_bwd, 50, stream)
     # device time: 50 forward + backward pairs captured in one CUDA graph
@@ -931,7 +941,8 @@ def row_diff(torch, _lib, rect, stream, dev, ctx):
         np.einsum("nik,ni->nk", Jbuf, gHh)
     out["diff_aca_rect_65536"] = {
         "value": B / (tfb * 1e-3), "unit": "sets/s (fwd+bwd, eager calls)",
-        "ms_fwd_bwd": tfb, "ms_fwd_bwd_device": tdev, "sets_per_s_device": B / (tdev * 1e-3),
+        "ms_fwd_bwd": tfb, "ms_fwd_bwd_prepared_calls": tfp, "ms_fwd_bwd_device": tdev,
+        "sets_per_s_device": B / (tdev * 1e-3),
         "ms_plain_aca_solve": tpl, "ratio_vs_plain": tfb / tpl,
         "ms_torch_ops_autograd_fwd_bwd": ttt, "speedup_vs_torch_ops": ttt / tfb,
         # forward 32 B in + 36 out, backward 32 + 36 in + 32 out, per set

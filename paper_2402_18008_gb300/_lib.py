@@ -209,6 +209,62 @@ def aca_rect_backward(tgt, rect, grad_H, grad_tgt, n=None, stream=None):
                                   _stream(stream, tgt)))
 
 
+class Prepared:
+    """One C-ABI call bound to fixed tensors: the arguments are checked once,
+    when it is made, and every call then passes the precomputed pointers and
+    sizes and the current stream (for loops that call the same entry point
+    on the same buffers, where per-call marshalling would exceed the kernel's
+    own time).  It keeps references to its tensors."""
+
+    __slots__ = ("_fn", "_args", "_dev", "_keep")
+
+    def __init__(self, fn, args, like, keep):
+        self._fn, self._args, self._keep = fn, tuple(args), keep
+        dev = like.get_device()
+        self._dev = dev if dev >= 0 else torch.cuda.current_device()
+
+    def __call__(self, stream=None):
+        st = int(stream.cuda_stream) if stream is not None else _raw_stream(self._dev)
+        r = self._fn(*self._args, st)
+        if r:
+            _check(r)
+
+
+def prepare_aca_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE) -> Prepared:
+    """aca_solve bound to pts, H (and flags): see aca_solve and Prepared."""
+    _need(pts, "pts", torch.float32, 16, host_ok=True)
+    _need(H, "H", torch.float32, 9, host_ok=True)
+    if flags is not None:
+        _need(flags, "flags", torch.uint8, host_ok=True)
+    ld = _ld(pts, H)
+    n = pts.shape[1] if n is None else int(n)
+    return Prepared(_L().aca_solve, (pts.data_ptr(), H.data_ptr(), _ptr(flags), n, ld, int(norm)), pts,
+                    (pts, H, flags))
+
+
+def prepare_aca_rect_solve(tgt, rect, H, n=None) -> Prepared:
+    """aca_rect_solve bound to tgt, rect and H: see Prepared."""
+    _need(tgt, "tgt", torch.float32, 8)
+    _need(H, "H", torch.float32, 9)
+    ld = _ld(tgt, H)
+    n = tgt.shape[1] if n is None else int(n)
+    x0, y0, w, r = (float(v) for v in rect)
+    return Prepared(_L().aca_rect_solve, (tgt.data_ptr(), x0, y0, w, r, H.data_ptr(), n, ld), tgt, (tgt, H))
+
+
+def prepare_aca_rect_backward(tgt, rect, grad_H, grad_tgt, n=None) -> Prepared:
+    """aca_rect_backward bound to its tensors: see Prepared."""
+    _need(tgt, "tgt", torch.float32, 8)
+    _need(grad_H, "grad_H", torch.float32, 9)
+    _need(grad_tgt, "grad_tgt", torch.float32, 8)
+    ld = _ld(tgt, grad_H, grad_tgt)
+    n = tgt.shape[1] if n is None else int(n)
+    x0, y0, w, r = (float(v) for v in rect)
+    return Prepared(_L().aca_rect_backward,
+                    (tgt.data_ptr(), x0, y0, w, r, grad_H.data_ptr(), grad_tgt.data_ptr(), n, ld), tgt,
+                    (tgt, grad_H, grad_tgt))
+
+
 def ransac_aca_workspace_size(P: int, total_hyps: int) -> int:
     return int(load().ransac_aca_workspace_size(P, total_hyps))
 

@@ -326,3 +326,34 @@ def test_solve_beyond_32_bit_offsets():
     bound_gate(unit_aligned_err(g, oracle.aca(sub)), oracle.aca_fp32_bound(sub), "2^30 + 3 sets")
     del pts, H
     torch.cuda.empty_cache()
+
+
+def test_prepared_calls_match_plain_calls():
+    # one call bound to fixed buffers, checked once: the same bits as the
+    # plain binding, on the current stream and on an explicit one
+    ms = workloads.minimal_sets(5000, seed=31)
+    pts = cuda(ms.pts)
+    H1 = torch.empty((9, 5000), device="cuda")
+    H2 = torch.full((9, 5000), 7.0, device="cuda")
+    _lib.aca_solve(pts, H1)
+    prep = _lib.prepare_aca_solve(pts, H2)
+    prep()
+    torch.cuda.synchronize()
+    assert torch.equal(H1, H2)
+    s = torch.cuda.Stream()
+    H2.fill_(7.0)
+    torch.cuda.synchronize()
+    prep(stream=s)
+    s.synchronize()
+    assert torch.equal(H1, H2)
+    rb = workloads.rect_batch(4096, seed=3)
+    tgt = cuda(rb.tgt)
+    gH = torch.randn((9, 4096), device="cuda")
+    Ha, Hb = torch.empty((9, 4096), device="cuda"), torch.empty((9, 4096), device="cuda")
+    ga, gb = torch.empty((8, 4096), device="cuda"), torch.empty((8, 4096), device="cuda")
+    _lib.aca_rect_solve(tgt, rb.rect, Ha)
+    _lib.aca_rect_backward(tgt, rb.rect, gH, ga)
+    _lib.prepare_aca_rect_solve(tgt, rb.rect, Hb)()
+    _lib.prepare_aca_rect_backward(tgt, rb.rect, gH, gb)()
+    torch.cuda.synchronize()
+    assert torch.equal(Ha, Hb) and torch.equal(ga, gb)
