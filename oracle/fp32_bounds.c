@@ -6,35 +6,39 @@
  * the exact one), not a solver; the library never calls it and it includes
  * nothing of the library.
  *
- * Method: running error analysis (Wilkinson, "Rounding Errors in Algebraic
- * Processes", 1963; Higham, "Accuracy and Stability of Numerical
- * Algorithms", 2nd ed., 2002, Sec. 3.3).  Every quantity q of an FP32
- * evaluation carries
- *   v  its exact value (computed here in FP64; that rounding, ~1e-16
- *      relative, is neglected against u = 2^-24),
- *   e  a bound on |fl(q) - v|, valid to first order in u,
- *   m  its magnitude: the same expression evaluated on absolute values
- *      (used only by the u^2 terms of the double-float steps).
- * Rules (u = 2^-24, round to nearest, no underflow or overflow):
- *   exact FP32 input                 e = 0
- *   exact difference (TwoSum pair)   e = e_a + e_b (no rounding)
- *   rounded + - * fma /              propagated first-order terms + u |v|
- *   Kahan's FMA determinant ad - bc  propagated terms + 2u |v|
+ * Method: first-order rounding-error analysis (Wilkinson, "Rounding Errors
+ * in Algebraic Processes", 1963; Higham, "Accuracy and Stability of
+ * Numerical Algorithms", 2nd ed., 2002, Ch. 2-3).  An FP32 evaluation is
+ * recorded on a tape: every quantity q carries its exact value v (computed
+ * here in FP64, whose own rounding, ~1e-16 relative, is neglected against
+ * u = 2^-24) and the size C of its own rounding event, fl(q) = q + eps with
+ * |eps| <= u C, the events independent.  A reverse sweep gives dout/d(event)
+ * for every event, and the bound on |fl(out) - out| is u sum |dout/d(event)| C:
+ * the worst case over the events to first order, which keeps the
+ * cancellations between correlated errors that absolute values taken at
+ * every step would lose.  Event sizes (u = 2^-24, round to nearest, no
+ * underflow or overflow):
+ *   exact FP32 input, exact difference (TwoSum pair)   C = 0
+ *   rounded + - * fma /                                C = |v|
+ *   Kahan's FMA determinant ad - bc                    C = 2 |v|
  *       (Jeannerod, Louvet and Muller, Math. Comp. 82, 2013: relative
  *       error at most 2u for exact operands)
  *   cross product of two exact differences given as value + remainder,
  *   evaluated as Kahan's determinant of the values plus the four
- *   first-order remainder products          2u |v| + 16 u^2 (|ux vy| + |uy vx|)
+ *   first-order remainder products          C = 2 |v| + 16 u (|ux vy| + |uy vx|)
  *       (the dropped remainder-by-remainder products are at most
  *       u^2 (|ux vy| + |uy vx|), the four remainder products are summed with
  *       at most 4 roundings of a sum bounded by 2u (|ux vy| + |uy vx|), and
  *       the two final additions add u |v| plus u^2 terms)
- *   double-float product / sum       propagated terms + 16 u^2 m
- *       (TwoProduct and TwoSum are exact; the low parts, themselves of size
- *       at most a few u m, are added with one or two roundings)
- *   rounding a double-float to FP32  + u |v|
- * Each final bound gets an allowance of 64 u^2 m for the neglected products
- * of first-order terms.
+ *   double-float product / sum                         C = 16 u m
+ *       (TwoProduct and TwoSum are exact; the low parts, of size at most a
+ *       few u m with m the magnitude accumulated within the double-float
+ *       chain, are added with one or two roundings)
+ *   rounding a double-float to FP32                    C = |v|
+ * Each output gets a token event of 64 u |v| for the neglected products of
+ * first-order terms; where a first-order term vanishes (the squared
+ * residuals of the inlier test at a point mapped exactly), the squares of the
+ * first-order bounds of the squared quantities are added explicitly.
  *
  * The evaluation orders (which quantities are rounded where) are those the
  * library states for its solvers: ACA in local frames anchored at M1 / M2
@@ -62,8 +66,10 @@
 /* One tape per chain: node k holds its exact value v, its magnitude m, the
  * size C of its own rounding event (fl(q) = q + eps with |eps| <= u C, the
  * eps of different nodes independent) and the partial derivatives of v
- * with respect to up to four earlier nodes. */
-#define TAPE_MAX 640
+ * with respect to up to four earlier nodes.  The ACA chain takes 118 nodes,
+ * SKS 184 and the inlier test about 40; push() stops the process rather than
+ * write past the end. */
+#define TAPE_MAX 320
 typedef struct {
     double v, m, C;
     int p[4];
@@ -79,6 +85,7 @@ static const double U = 0x1p-24;
 
 static int push(tape *t, double v, double m, double C)
 {
+    if (t->len >= TAPE_MAX) abort();
     node *q = &t->n[t->len];
     q->v = v;
     q->m = m;
@@ -552,7 +559,7 @@ static void test_parts_of(const hyp_model *h, const double *Eh, double thr, cons
     const int e = final_(t, fma3(t, du, du, fma3(t, dvv, dvv, mul(t, w, neg(t, w)))));
     o->E = V(e);
     const int tgt[4] = {e, du, dvv, w};
-    double adj[64], cr[4];
+    double adj[TAPE_MAX], cr[4];
     for (int q = 0; q < 4; ++q) {
         const double one = 1.0;
         sweep(t, &tgt[q], &one, 1, adj);
