@@ -17,7 +17,8 @@
 //      problems" (2004), Alg. 3.16; each trial step is one pass.
 //
 // Precision and speed on GB300, where FP64 runs at 1/64 of the FP32 rate and
-// a serial FP64 chain on one warp is the slowest thing in the block:
+// each FP64 instruction (conversions included) of a serial chain costs
+// hundreds of cycles:
 //   - per-point arithmetic is FP32 on O(1) normalised coordinates;
 //   - sums whose cancellation matters (the DLT moments, the gradient J^T r
 //     and the cost) are double-float: FP32 partials over chunks of 8 points,
@@ -30,13 +31,20 @@
 //     (lm_iters = 0) and in FP32 when it only starts LM, which converges to
 //     the same minimiser from either start;
 //   - the 8x8 LM steps are FP32 (an inexact step only slows the iteration;
-//     its fixed point is set by the gradient); parameters and costs stay in
-//     FP64; the small solves run on one warp with lane i owning row i;
+//     its fixed point is set by the gradient); the parameters and the cost
+//     are double-float, and so is the map back to pixels, whose translation
+//     column cancels; nothing on the LM path uses FP64;
+//   - the small solves run in registers, every lane of the leader warp
+//     computing the same values (no shuffle or shared-memory access in
+//     their dependent chains);
 //   - the cost of a trial point carries FP32 rounding noise of about 2^-16
 //     relative, so near the optimum, where the predicted decrease is below
 //     that noise, a step is accepted unless the cost rises by more than the
 //     noise: the gain ratio could not tell such steps apart.
 #include <math.h>
+
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "fp32.cuh"
@@ -52,7 +60,7 @@ constexpr int kPad = 33;              // transposition row stride (floats per va
 constexpr int kInvIters = 16;         // inverse-iteration cap (FP64 DLT)
 constexpr float kTau = 1e-3f;         // mu0 = tau * max diag(J^T J)
 constexpr float kEpsStep = 5.9604644775390625e-8f;   // 2^-24: parameters are used in FP32
-constexpr double kCostNoise = 1.52587890625e-05;     // 2^-16: FP32 noise of the cost, relative
+constexpr float kCostNoise = 1.52587890625e-05f;     // 2^-16: FP32 noise of the cost, relative
 
 constexpr int kDF_DLT = 24;           // moments of the normalised points (the DLT)
 constexpr int kDF_P2 = kDF_DLT + 2;   // double-float sums of pass 2 (moments + 2 distance sums)
@@ -65,19 +73,21 @@ struct Shared {
     float tr[kWarps][kTr];            // per-warp transposition scratch
     DF wpart[kWarps][kDF_P2];         // per-warp double-float sums
     float wpartf[kWarps][kF_LM];
-    double sum[kDF_P2];               // block sums (leader warp)
+    DF sum[kDF_P2];                   // block sums (leader warp), renormalised
     float sumf[kF_LM];
-    double M[81], L9[81], r9[9];      // DLT (FP64 variant)
-    float Mf[81], L9f[81], r9f[9];    // DLT (FP32 variant)
-    double v[9];                      // DLT eigenvector
-    float S8[64], L8[64], r8[8];      // LM step matrix, factor, 1 / diagonal
+    double dsum[kDF_DLT];             // the DLT moments in FP64 (when the DLT is the result)
+    double M[81], L9[81], r9[9];      // DLT (FP64, when it is the result)
+    double v[9];                      // its eigenvector
+    DF hn[9];                         // the DLT fit in the normalised frames
     float par[8];                     // parameters broadcast to the pass
-    float mu1x, mu1y, s1, mu2x, mu2y, s2;
+    float mu1x, mu1y, s1, mu2x, mu2y, s2, cnt;
+    int64_t used;
     int go;                           // leader -> block decision
     // Levenberg-Marquardt state (leader warp)
-    float A[64];                      // J^T J at pd
-    double g[8], F;                   // J^T r and ||r||^2 / 2 at pd
-    double pd[8];                     // parameters
+    float Asum[kF_LM];                // the FP32 sums of J^T J at pd
+    float g[8];                       // J^T r at pd
+    DF F;                             // ||r||^2 / 2 at pd
+    DF pd[8];                         // parameters
     float d[8], mu, nu;               // step, damping
     int it;                           // trial steps taken
 };
@@ -179,7 +189,7 @@ __device__ void warp_partials_shfl(const DF (&s)[K], Shared &sh)
 }
 
 // Leader warp, after the block barrier: sums over the warps into sh.sum
-// (FP64) and sh.sumf; visible to the leader warp on return.
+// (double-float) and sh.sumf; visible to the leader warp on return.
 template <int K, int KF>
 __device__ void leader_sums(Shared &sh)
 {
@@ -188,7 +198,7 @@ __device__ void leader_sums(Shared &sh)
         DF a = sh.wpart[0][lane];
 #pragma unroll
         for (int w = 1; w < kWarps; ++w) a = df_renorm(df_add(a, sh.wpart[w][lane]));
-        sh.sum[lane] = (double)a.h + (double)a.l;
+        sh.sum[lane] = df_renorm(a);
     } else if (lane < K + KF) {
         float a = sh.wpartf[0][lane - K];
 #pragma unroll
@@ -254,29 +264,156 @@ __device__ T warp_chol_solve(const T *L, const T *rd, T x)
     return x;
 }
 
+// Small dense algebra in registers, run redundantly by every lane of the
+// leader warp: each lane holds the whole packed matrix, all lanes execute the
+// same instructions on the same values (so they agree bit for bit), and no
+// step of the dependent chain is a shuffle or a shared-memory access.  Those
+// go through the SM's memory-instruction queue, which the other resident
+// block's point loads keep full; a chain of shuffles there runs an order of
+// magnitude slower than on an idle SM.  Packed lower triangle, row-major:
+// entry (i, j), j <= i, at tri(i, j).
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// In-place Cholesky L L^T of the packed n x n matrix a (right-looking: after
+// column j the trailing block holds S - sum_{k <= j} l_k l_k^T), pivots below
+// `floor` raised to it; rd[j] = 1 / L[j][j].  False on a non-positive or
+// non-finite pivot.
+template <int n>
+__device__ __forceinline__ bool reg_cholesky(float (&a)[n * (n + 1) / 2], float (&rd)[n], float floor)
+{
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+        float d = a[tri(j, j)];
+        if (d < floor) d = floor;
+        ok = ok && d > 0.0f && isfinite(d);
+        const float l = sqrtf(d), r = 1.0f / l;
+        a[tri(j, j)] = l;
+        rd[j] = r;
+#pragma unroll
+        for (int i = j + 1; i < n; ++i) a[tri(i, j)] *= r;
+#pragma unroll
+        for (int i = j + 1; i < n; ++i)
+#pragma unroll
+            for (int k = j + 1; k <= i; ++k) a[tri(i, k)] = fmaf(-a[tri(i, j)], a[tri(k, j)], a[tri(i, k)]);
+    }
+    return ok;
+}
+
+// x := (L L^T)^-1 x with the factor of reg_cholesky.
+template <int n>
+__device__ __forceinline__ void reg_chol_solve(const float (&a)[n * (n + 1) / 2], const float (&rd)[n], float (&x)[n])
+{
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int k = 0; k < i; ++k) x[i] = fmaf(-a[tri(i, k)], x[k], x[i]);
+        x[i] *= rd[i];
+    }
+#pragma unroll
+    for (int i = n - 1; i >= 0; --i) {
+#pragma unroll
+        for (int k = i + 1; k < n; ++k) x[i] = fmaf(-a[tri(k, i)], x[k], x[i]);
+        x[i] *= rd[i];
+    }
+}
+
+// x[lane] for lane < n (else 0) without an indexed register access.
+template <int n>
+__device__ __forceinline__ float lane_pick(const float (&x)[n], int lane)
+{
+    float v = 0.0f;
+#pragma unroll
+    for (int i = 0; i < n; ++i) v = lane == i ? x[i] : v;
+    return v;
+}
+
 __device__ __forceinline__ bool take(const uint8_t *mask, int64_t i) { return mask == nullptr || mask[i] != 0; }
 
-// Calls f(q) for every used point of the block's problem, the block's threads
-// striding over them; each thread keeps kUnroll loads in flight (the passes
-// are otherwise bound by one L2 round trip per point).
-constexpr int kUnroll = 4;
-template <class Fn>
-__device__ __forceinline__ void for_points(const float4 *__restrict__ c, const uint8_t *__restrict__ m, int64_t n,
-                                           Fn &&f)
+// The block's problem: its correspondences and mask bytes in global memory,
+// and a copy of the first nr of them (points and mask bytes) in shared
+// memory, filled by the first pass.  The later passes read that copy, so
+// for problems that fit it (most of them) only the first pass touches
+// global memory; the rest of a larger problem is read from global memory
+// (L2) on every pass.
+extern __shared__ __align__(16) unsigned char s_pts[];   // cap points, then cap mask bytes
+
+struct Points {
+    const float4 *c;
+    const uint8_t *m;                 // null: every point is used
+    int64_t n;
+    int nr;                           // points in the shared copy
+    int cap;                          // its capacity
+    __device__ float4 *sc() const { return reinterpret_cast<float4 *>(s_pts); }
+    __device__ uint8_t *sm() const { return s_pts + (size_t)cap * sizeof(float4); }
+};
+
+// Calls f(q, t) for every slot of the block's problem: the block's threads
+// stride over the points, all of them taking the same number of steps, and
+// t says whether the slot holds a used point (q is zero otherwise), so the
+// per-point code runs without divergence and the accumulators' chunk flushes
+// happen on the same step in every lane; f must make an unused slot add
+// nothing.  Each thread keeps U loads in flight (the passes are otherwise
+// bound by one memory round trip per step).  A correspondence is loaded
+// whether or not its mask byte is set, so both loads are in flight at once;
+// the masked-out points share cache sectors with the used ones.
+template <int U, class Fn>
+__device__ __forceinline__ void for_global(const Points &P, int64_t from, bool fill, Fn &&f)
 {
-    for (int64_t i0 = threadIdx.x; i0 < n; i0 += kUnroll * kThreads) {
-        float4 q[kUnroll];
-        bool t[kUnroll];
+    for (int64_t b0 = from; b0 < P.n; b0 += U * kThreads) {
+        float4 q[U];
+        bool t[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int64_t i = i0 + (int64_t)u * kThreads;
-            t[u] = i < n && take(m, i);
-            q[u] = t[u] ? c[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = b0 + (int64_t)(u * kThreads) + threadIdx.x;
+            const bool in = i < P.n;
+            q[u] = in ? P.c[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            t[u] = in && take(P.m, i);
+        }
+        if (fill) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = b0 + (int64_t)(u * kThreads) + threadIdx.x;
+                if (i < P.nr) {
+                    P.sc()[i] = q[u];
+                    P.sm()[i] = t[u] ? 1 : 0;
+                }
+            }
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (t[u]) f(q[u]);
+        for (int u = 0; u < U; ++u) f(t[u] ? q[u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), t[u]);
     }
+}
+
+constexpr int kUnroll = 4;
+
+// The first pass: every point from global memory, eight loads in flight a
+// thread (first touch: HBM latency), filling the shared copy.
+template <class Fn>
+__device__ __forceinline__ void for_points_fill(const Points &P, Fn &&f)
+{
+    for_global<8>(P, 0, true, f);
+}
+
+// A later pass: the shared copy (US loads in flight a thread), then the rest
+// from global memory (UG).
+template <int US = kUnroll, int UG = kUnroll, class Fn>
+__device__ __forceinline__ void for_points(const Points &P, Fn &&f)
+{
+    for (int b0 = 0; b0 < P.nr; b0 += US * kThreads) {
+        float4 q[US];
+        bool t[US];
+#pragma unroll
+        for (int u = 0; u < US; ++u) {
+            const int i = b0 + u * kThreads + (int)threadIdx.x;
+            const bool in = i < P.nr;
+            q[u] = in ? P.sc()[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            t[u] = in && P.sm()[i] != 0;
+        }
+#pragma unroll
+        for (int u = 0; u < US; ++u) f(t[u] ? q[u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), t[u]);
+    }
+    for_global<UG>(P, P.nr, false, f);
 }
 
 struct Frame {
@@ -292,7 +429,7 @@ struct Frame {
     }
 };
 
-// Leader warp: the normalised DLT from the 24 moments in sh.sum, in precision
+// Leader warp: the normalised DLT from the 24 moments in sh.dsum, in precision
 // T.  Rows of Eq. 2 per point: (xb, 0, -X xb) and (0, -xb, Y xb), so M has
 // blocks S_1 (twice), -S_X, -S_Y and S_R, S_w = sum w {xx, xy, yy, x, y, 1}.
 // Writes the unit eigenvector to sh.v; returns false if the factorisation
@@ -306,13 +443,13 @@ __device__ bool dlt_leader(Shared &sh, T *M, T *L, T *rd, T floor_rel, T tol, in
     if (lane < 9) {
         const int mi[3][3] = {{0, 1, 3}, {1, 2, 4}, {3, 4, 5}};
         const int i = lane / 3, j = lane % 3, k = mi[i][j];
-        M[i * 9 + j] = (T)sh.sum[k];
-        M[(3 + i) * 9 + 3 + j] = (T)sh.sum[k];
-        M[i * 9 + 6 + j] = -(T)sh.sum[6 + k];
-        M[(6 + j) * 9 + i] = -(T)sh.sum[6 + k];
-        M[(3 + i) * 9 + 6 + j] = -(T)sh.sum[12 + k];
-        M[(6 + j) * 9 + 3 + i] = -(T)sh.sum[12 + k];
-        M[(6 + i) * 9 + 6 + j] = (T)sh.sum[18 + k];
+        M[i * 9 + j] = (T)sh.dsum[k];
+        M[(3 + i) * 9 + 3 + j] = (T)sh.dsum[k];
+        M[i * 9 + 6 + j] = -(T)sh.dsum[6 + k];
+        M[(6 + j) * 9 + i] = -(T)sh.dsum[6 + k];
+        M[(3 + i) * 9 + 6 + j] = -(T)sh.dsum[12 + k];
+        M[(6 + j) * 9 + 3 + i] = -(T)sh.dsum[12 + k];
+        M[(6 + i) * 9 + 6 + j] = (T)sh.dsum[18 + k];
     }
     __syncwarp();
     const T dmax = warp_max(lane < 9 ? M[lane * 10] : T(0));
@@ -362,7 +499,7 @@ __device__ bool dlt_leader(Shared &sh, T *M, T *L, T *rd, T floor_rel, T tol, in
 //   FP32: sum q {xx, xy, yy, x, y, 1}, sum q u {xx, xy, yy, x, y},
 //         sum q v {...}, sum q (u^2 + v^2) {xx, xy, yy}, the blocks of J^T J.
 // Ends with a block barrier; the leader warp then calls leader_sums.
-__device__ void lm_pass(const float4 *c, const uint8_t *m, int64_t n, Shared &sh)
+__device__ void lm_pass(const Points &P, Shared &sh)
 {
     DFAcc<kDF_LM> a;
     a.zero();
@@ -372,11 +509,12 @@ __device__ void lm_pass(const float4 *c, const uint8_t *m, int64_t n, Shared &sh
     const Frame fr(sh);
     const float p0 = sh.par[0], p1 = sh.par[1], p2 = sh.par[2], p3 = sh.par[3];
     const float p4 = sh.par[4], p5 = sh.par[5], p6 = sh.par[6], p7 = sh.par[7];
-    for_points(c, m, n, [&](float4 pt) {
+    for_points(P, [&](float4 pt, bool t) {
         float x, y, X, Y;
         fr.apply(pt, x, y, X, Y);
         const float w = fmaf(p6, x, fmaf(p7, y, 1.0f));
-        const float iw = 1.0f / w;
+        // an unused slot: 1/w = 0 zeroes every gradient and J^T J term
+        const float iw = t ? 1.0f / w : 0.0f;
         const float u = fmaf(p0, x, fmaf(p1, y, p2)) * iw;
         const float v = fmaf(p3, x, fmaf(p4, y, p5)) * iw;
         const float ru = u - X, rv = v - Y;
@@ -384,7 +522,7 @@ __device__ void lm_pass(const float4 *c, const uint8_t *m, int64_t n, Shared &sh
         a.f[0] = fmaf(gu, x, a.f[0]); a.f[1] = fmaf(gu, y, a.f[1]); a.f[2] += gu;
         a.f[3] = fmaf(gv, x, a.f[3]); a.f[4] = fmaf(gv, y, a.f[4]); a.f[5] += gv;
         a.f[6] = fmaf(-gw, x, a.f[6]); a.f[7] = fmaf(-gw, y, a.f[7]);
-        a.f[8] = fmaf(ru, ru, fmaf(rv, rv, a.f[8]));
+        a.f[8] += t ? fmaf(ru, ru, rv * rv) : 0.0f;
         a.tick();
         const float q = iw * iw;
         const float xx = x * x, xy = x * y, yy = y * y;
@@ -402,135 +540,248 @@ __device__ void lm_pass(const float4 *c, const uint8_t *m, int64_t n, Shared &sh
     __syncthreads();
 }
 
-// J^T J (8x8, FP32) from the FP32 sums of lm_pass: blocks
-// sum q xb xb^T (twice), -sum q u xb b^T, -sum q v xb b^T and
-// sum q (u^2 + v^2) b b^T.  Leader warp, lane-parallel.
-__device__ void lm_assemble(const float *s, float A[64])
+// Moment index of xb_i xb_j, xb = (x, y, 1), in {xx, xy, yy, x, y, 1}.
+__host__ __device__ constexpr int mom(int i, int j)
 {
-    const int lane = threadIdx.x & 31;
-    // index of the moment {xx, xy, yy, x, y, 1} of xb_i xb_j
-    const int mi[3][3] = {{0, 1, 3}, {1, 2, 4}, {3, 4, 5}};
-    for (int e = lane; e < 64; e += 32) {
-        const int r = e / 8, c = e % 8;
-        float v = 0.0f;
-        if (r < 3 && c < 3) v = s[mi[r][c]];
-        else if (r >= 3 && r < 6 && c >= 3 && c < 6) v = s[mi[r - 3][c - 3]];
-        else if (r < 3 && c >= 6) v = -s[6 + mi[r][c - 6]];
-        else if (r >= 6 && c < 3) v = -s[6 + mi[c][r - 6]];
-        else if (r >= 3 && r < 6 && c >= 6) v = -s[11 + mi[r - 3][c - 6]];
-        else if (r >= 6 && c >= 3 && c < 6) v = -s[11 + mi[c - 3][r - 6]];
-        else if (r >= 6 && c >= 6) v = s[16 + mi[r - 6][c - 6]];
-        A[e] = v;
+    return i == 2 ? (j == 2 ? 5 : 3 + j) : (j == 2 ? 3 + i : i + j);
+}
+
+// Entry (r, c), r >= c, of the DLT normal matrix in the 24 moments S_1, S_X,
+// S_Y, S_R (6 each): 1 + index, negated for a negative entry, 0 for zero.
+__host__ __device__ constexpr int dlt_code(int r, int c)
+{
+    return r < 3   ? 1 + mom(r, c)
+           : r < 6 ? (c < 3 ? 0 : 1 + mom(r - 3, c - 3))
+           : c < 3 ? -(1 + 6 + mom(c, r - 6))
+           : c < 6 ? -(1 + 12 + mom(c - 3, r - 6))
+                   : 1 + 18 + mom(r - 6, c - 6);
+}
+
+// Entry (r, c), r >= c, of J^T J (8 x 8) in the 19 FP32 sums of lm_pass:
+// blocks sum q xb xb^T (twice), -sum q u xb b^T, -sum q v xb b^T and
+// sum q (u^2 + v^2) b b^T; same code convention.
+__host__ __device__ constexpr int jtj_code(int r, int c)
+{
+    return r < 3   ? 1 + mom(r, c)
+           : r < 6 ? (c < 3 ? 0 : 1 + mom(r - 3, c - 3))
+           : c < 3 ? -(1 + 6 + mom(c, r - 6))
+           : c < 6 ? -(1 + 11 + mom(c - 3, r - 6))
+                   : 1 + 16 + mom(r - 6, c - 6);
+}
+
+// The packed matrix from its sums: the DLT normal matrix (n = 9) or J^T J
+// (n = 8).
+template <int n, int K>
+__device__ __forceinline__ void fill_packed(const float (&m)[K], float (&a)[n * (n + 1) / 2])
+{
+    static_assert((n == 9 && K == kDF_DLT) || (n == 8 && K == kF_LM), "DLT (9, 24 sums) or J^T J (8, 19 sums)");
+#pragma unroll
+    for (int r = 0; r < n; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) {
+            const int k = n == 9 ? dlt_code(r, c) : jtj_code(r, c);
+            a[tri(r, c)] = k == 0 ? 0.0f : k > 0 ? m[k - 1] : -m[-k - 1];
+        }
+}
+
+// Leader warp, every lane: the FP32 normalised DLT that starts LM, from the
+// 24 moments of the normalised points: M, its Cholesky factor (pivot floor
+// 2^-20 of the largest diagonal entry: near FP32's rounding of M, far below
+// the eigenvalue gap), the start e_k with k the largest diagonal entry of
+// M^-1 (the squared column norms of L^-1), then three inverse-iteration
+// steps (error ratio lambda1 / lambda2 per step).  False if the
+// factorisation failed.
+__device__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
+{
+    float a[45], rd[9];
+    fill_packed<9>(m, a);
+    float dmax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dmax = fmaxf(dmax, a[tri(k, k)]);
+    if (!reg_cholesky<9>(a, rd, dmax * 9.5367431640625e-07f)) return false;
+    float best = -1.0f;
+    int kb = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        float z[9], dk = 0.0f;
+#pragma unroll
+        for (int i = k; i < 9; ++i) {
+            float t = i == k ? 1.0f : 0.0f;
+#pragma unroll
+            for (int j = k; j < i; ++j) t = fmaf(-a[tri(i, j)], z[j], t);
+            z[i] = t * rd[i];
+            dk = fmaf(z[i], z[i], dk);
+        }
+        if (dk > best) {
+            best = dk;
+            kb = k;
+        }
     }
-    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = i == kb ? 1.0f : 0.0f;
+    for (int it = 0; it < 3; ++it) {
+        float y[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) y[i] = x[i];
+        reg_chol_solve<9>(a, rd, y);
+        float ny = 0.0f, dot = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            ny = fmaf(y[i], y[i], ny);
+            dot = fmaf(y[i], x[i], dot);
+        }
+        const float sc = (dot < 0.0f ? -1.0f : 1.0f) / sqrtf(ny);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) x[i] = y[i] * sc;
+    }
+    return true;
 }
 
 // Leader warp: the next trial step (J^T J + mu I) d = -g, counting every
 // trial (a non-positive-definite matrix is a rejected step).  Returns 1
 // (evaluate pd + d, in sh.par) or 0 (no more trials: the budget is spent, the
 // step is below the FP32 resolution of the parameters, or the damping is no
-// longer finite).
+// longer finite).  Every lane factors and solves in registers.
 __device__ int lm_trial(Shared &sh, int budget)
 {
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        if (sh.it >= budget || !(isfinite(sh.mu) && sh.mu > 0.0f)) return 0;
-        if (lane < 8) {
+    float m[kF_LM], g[8], p[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) sh.S8[lane * 8 + k] = sh.A[lane * 8 + k];
-            sh.S8[lane * 9] += sh.mu;
-        }
-        __syncwarp();
-        const bool ok = warp_cholesky<8, float>(sh.S8, sh.L8, sh.r8, 0.0f);
-        __syncwarp();
-        if (lane == 0) sh.it += 1;
+    for (int k = 0; k < kF_LM; ++k) m[k] = sh.Asum[k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        g[k] = sh.g[k];
+        p[k] = sh.pd[k].h;
+    }
+    float mu = sh.mu, nu = sh.nu;
+    int it = sh.it, go = 0;
+    float d[8];
+    for (;;) {
+        if (it >= budget || !(isfinite(mu) && mu > 0.0f)) break;
+        float a[36], rd[8];
+        fill_packed<8>(m, a);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[tri(k, k)] += mu;
+        const bool ok = reg_cholesky<8>(a, rd, 0.0f);
+        ++it;
         if (!ok) {
-            if (lane == 0) {
-                sh.mu *= sh.nu;
-                sh.nu *= 2.0f;
-            }
-            __syncwarp();
+            mu *= nu;
+            nu *= 2.0f;
             continue;
         }
-        const float dl = warp_chol_solve<8, float>(sh.L8, sh.r8, lane < 8 ? (float)-sh.g[lane] : 0.0f);
-        const float dd = lane < 8 ? dl : 0.0f;
-        const float pp = lane < 8 ? (float)sh.pd[lane] : 0.0f;
-        const float nd = warp_sum(dd * dd), np = warp_sum(pp * pp);
-        if (!(sqrtf(nd) > kEpsStep * (sqrtf(np) + kEpsStep))) return 0;
-        if (lane < 8) {
-            sh.d[lane] = dd;
-            sh.par[lane] = (float)(sh.pd[lane] + (double)dd);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d[k] = -g[k];
+        reg_chol_solve<8>(a, rd, d);
+        float nd = 0.0f, np = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            nd = fmaf(d[k], d[k], nd);
+            np = fmaf(p[k], p[k], np);
         }
-        __syncwarp();
-        return 1;
+        go = sqrtf(nd) > kEpsStep * (sqrtf(np) + kEpsStep) ? 1 : 0;
+        break;
     }
+    if (go && lane < 8) {
+        const float dl = lane_pick<8>(d, lane);
+        sh.d[lane] = dl;
+        sh.par[lane] = df_round(df_add(sh.pd[lane], DF{dl, 0.0f}));
+    }
+    if (lane == 0) {
+        sh.mu = mu;
+        sh.nu = nu;
+        sh.it = it;
+    }
+    __syncwarp();
+    return go;
 }
 
 // Leader warp: gain ratio of the evaluated step; accept or reject it.
 __device__ void lm_update(Shared &sh)
 {
     const int lane = threadIdx.x & 31;
-    const double Fn = 0.5 * sh.sum[8];
-    const float pl = lane < 8 ? sh.d[lane] * (sh.mu * sh.d[lane] - (float)sh.g[lane]) : 0.0f;
-    const float pred = 0.5f * warp_sum(pl);
-    const float rho = (float)(sh.F - Fn) / pred;
-    const double noise = kCostNoise * sh.F;
-    const bool accept = isfinite(Fn) && (rho > 0.0f || ((double)pred <= noise && Fn <= sh.F + noise));
+    const DF F = sh.F, sn = sh.sum[8];
+    const DF Fn{0.5f * sn.h, 0.5f * sn.l};
+    const float mu = sh.mu, nu = sh.nu;
+    float pred = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float dk = sh.d[k];
+        pred = fmaf(dk, fmaf(mu, dk, -sh.g[k]), pred);
+    }
+    pred *= 0.5f;
+    const float dF = df_round(df_sub(F, Fn));            // the decrease, from the double-float costs
+    const float rho = dF / pred;
+    const float noise = kCostNoise * F.h;
+    const bool accept = isfinite(Fn.h) && (rho > 0.0f || (pred <= noise && -dF <= noise));
     __syncwarp();
     if (accept) {
         if (lane < 8) {
-            sh.pd[lane] += (double)sh.d[lane];
-            sh.g[lane] = sh.sum[lane];
+            sh.pd[lane] = df_renorm(df_add(sh.pd[lane], DF{sh.d[lane], 0.0f}));
+            sh.g[lane] = df_round(sh.sum[lane]);
         }
-        lm_assemble(sh.sumf, sh.A);
+        if (lane < kF_LM) sh.Asum[lane] = sh.sumf[lane];
         if (lane == 0) {
             sh.F = Fn;
             const float t = rho > 0.0f && rho < 1.0f ? 2.0f * rho - 1.0f : 1.0f;
-            sh.mu *= fmaxf(1.0f / 3.0f, 1.0f - t * t * t);
+            sh.mu = mu * fmaxf(1.0f / 3.0f, 1.0f - t * t * t);
             sh.nu = 2.0f;
         }
     } else if (lane == 0) {
-        sh.mu *= sh.nu;
-        sh.nu *= 2.0f;
+        sh.mu = mu * nu;
+        sh.nu = nu * 2.0f;
     }
     __syncwarp();
 }
 
-// Leader warp: H = T2^-1 Hn T1 in pixels, unit Frobenius norm with the sign
-// so that h33 > 0 (or, when |h33| < 1e-6 |H|, the first entry of largest
+// (x.h + x.l) / b: the quotient's leading part, then the remainder's
+// (TwoProduct makes x - q b exact up to x.l's rounding).
+__device__ __forceinline__ DF df_div(DF x, float b)
+{
+    const float q = x.h / b;
+    const DF r = df_sub(x, df_prod(q, b));
+    return DF{q, df_round(r) / b};
+}
+
+// Leader warp, every lane: H = T2^-1 Hn T1 in pixels, in double-float (the
+// translation columns cancel), with unit Frobenius norm and the sign that
+// makes h33 > 0 (or, when |h33| < 1e-6 |H|, the first entry of largest
 // magnitude > 0); lane i writes entry i.
-__device__ void leader_store(const Shared &sh, const double *hn, float *out)
+__device__ void leader_store(const Shared &sh, const DF (&hn)[9], float *out)
 {
     const int lane = threadIdx.x & 31;
-    double h = 0.0;
-    if (lane < 9) {
-        const int r = lane / 3, col = lane % 3;
-        const double s1 = sh.s1, a1x = sh.mu1x, a1y = sh.mu1y;
-        // (Hn T1)[r][col]: columns 0, 1 scale by s1, column 2 picks up -s1 mu1
-        auto B = [&](int rr) {
-            return col < 2 ? hn[rr * 3 + col] * s1
-                           : hn[rr * 3 + 2] - s1 * (hn[rr * 3 + 0] * a1x + hn[rr * 3 + 1] * a1y);
-        };
-        // T2^-1 B: rows 0, 1 scaled by 1/s2 plus mu2 times row 2
-        const double b2 = B(2);
-        h = r == 2 ? b2 : B(r) / (double)sh.s2 + (r == 0 ? (double)sh.mu2x : (double)sh.mu2y) * b2;
-    }
-    const double nrm = sqrt(warp_sum(h * h));
-    double ab = lane < 9 ? fabs(h) : -1.0;
-    int big = lane;
+    const float s1 = sh.s1, s2 = sh.s2, a1x = sh.mu1x, a1y = sh.mu1y, a2x = sh.mu2x, a2y = sh.mu2y;
+    // B = Hn T1: columns 0, 1 scale by s1, column 2 picks up -s1 (h_r0 mu1x + h_r1 mu1y)
+    DF B[9];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double oa = __shfl_xor_sync(0xffffffffu, ab, o);
-        const int ob = __shfl_xor_sync(0xffffffffu, big, o);
-        if (oa > ab || (oa == ab && ob < big)) { ab = oa; big = ob; }
+    for (int r = 0; r < 3; ++r) {
+        B[3 * r] = df_mul(hn[3 * r], s1);
+        B[3 * r + 1] = df_mul(hn[3 * r + 1], s1);
+        B[3 * r + 2] = df_sub(hn[3 * r + 2], df_mul(df_add(df_mul(hn[3 * r], a1x), df_mul(hn[3 * r + 1], a1y)), s1));
     }
-    const double h8 = __shfl_sync(0xffffffffu, h, 8), hb = __shfl_sync(0xffffffffu, h, big);
+    // H = T2^-1 B: rows 0, 1 are B_r / s2 + mu2 B_2, row 2 is B_2
+    float h[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        h[c] = df_round(df_add(df_div(B[c], s2), df_mul(B[6 + c], a2x)));
+        h[3 + c] = df_round(df_add(df_div(B[3 + c], s2), df_mul(B[6 + c], a2y)));
+        h[6 + c] = df_round(B[6 + c]);
+    }
+    float n2 = 0.0f, ab = -1.0f, hb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        n2 = fmaf(h[k], h[k], n2);
+        if (fabsf(h[k]) > ab) {
+            ab = fabsf(h[k]);
+            hb = h[k];
+        }
+    }
+    const float nrm = sqrtf(n2);
     if (lane < 9) {
-        if (!(nrm > 0.0) || !isfinite(nrm)) {
+        if (!(nrm > 0.0f) || !isfinite(nrm)) {
             out[lane] = 0.0f;
         } else {
-            const double sgn = fabs(h8) >= 1e-6 * nrm ? (h8 > 0 ? 1.0 : -1.0) : (hb > 0 ? 1.0 : -1.0);
-            out[lane] = (float)(sgn * h / nrm);
+            const float sgn = fabsf(h[8]) >= 1e-6f * nrm ? (h[8] > 0.0f ? 1.0f : -1.0f) : (hb > 0.0f ? 1.0f : -1.0f);
+            out[lane] = sgn * lane_pick<9>(h, lane) / nrm;
         }
     }
 }
@@ -617,7 +868,7 @@ __device__ void write_empty(float *H_out, float *rms, int p, float rms_value)
 __global__ void __launch_bounds__(kThreads, 2)
 refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offsets,
              const uint8_t *__restrict__ mask, int lm_iters, float *__restrict__ H_out,
-             int32_t *__restrict__ n_used, float *__restrict__ rms)
+             int32_t *__restrict__ n_used, float *__restrict__ rms, int cap)
 {
     __shared__ Shared sh;
     __shared__ int32_t s_hist[kClasses], s_scr[4 + kWarps];
@@ -630,15 +881,14 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
     const int64_t o0 = offsets[p];
     int64_t n = offsets[p + 1] - o0;
     if (n < 0) n = 0;
-    const float4 *c = corr + o0;
-    const uint8_t *m = mask ? mask + o0 : nullptr;
+    const Points pts{corr + o0, mask ? mask + o0 : nullptr, n, (int)(n < cap ? n : cap), cap};
 
     // Pass 1: count and centroids.
     {
         DFAcc<5> a;
         a.zero();
-        for_points(c, m, n, [&](float4 q) {
-            a.f[0] += 1.0f; a.f[1] += q.x; a.f[2] += q.y; a.f[3] += q.z; a.f[4] += q.w;
+        for_points_fill(pts, [&](float4 q, bool t) {
+            a.f[0] += t ? 1.0f : 0.0f; a.f[1] += q.x; a.f[2] += q.y; a.f[3] += q.z; a.f[4] += q.w;
             a.tick();
         });
         a.flush();
@@ -647,15 +897,18 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         if (leader) {
             leader_sums<5, 0>(sh);
             if (lane == 0) {
-                const double cnt = sh.sum[0];
-                sh.mu1x = (float)(sh.sum[1] / cnt); sh.mu1y = (float)(sh.sum[2] / cnt);
-                sh.mu2x = (float)(sh.sum[3] / cnt); sh.mu2y = (float)(sh.sum[4] / cnt);
+                const DF c0 = sh.sum[0];                    // an exact integer
+                const int64_t used = (int64_t)c0.h + (int64_t)c0.l;
+                const float cnt = (float)used;
+                sh.used = used;
+                sh.cnt = cnt;
+                sh.mu1x = df_round(sh.sum[1]) / cnt; sh.mu1y = df_round(sh.sum[2]) / cnt;
+                sh.mu2x = df_round(sh.sum[3]) / cnt; sh.mu2y = df_round(sh.sum[4]) / cnt;
             }
         }
         __syncthreads();
     }
-    const double cnt = sh.sum[0];
-    const int64_t used = (int64_t)(cnt + 0.5);
+    const int64_t used = sh.used;
     if (threadIdx.x == 0 && n_used) n_used[p] = (int32_t)used;
     if (used < 4) {
         write_empty(H_out, rms, p, 0.0f);
@@ -670,11 +923,13 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         DFAcc<kDF_P2> a;
         a.zero();
         const float m1x = sh.mu1x, m1y = sh.mu1y, m2x = sh.mu2x, m2y = sh.mu2y;
-        for_points(c, m, n, [&](float4 q) {
-            const float x = q.x - m1x, y = q.y - m1y, X = q.z - m2x, Y = q.w - m2y;
+        for_points<2, kUnroll>(pts, [&](float4 q, bool t) {
+            // an unused slot: zero centred coordinates and weight
+            const float x = t ? q.x - m1x : 0.0f, y = t ? q.y - m1y : 0.0f;
+            const float X = t ? q.z - m2x : 0.0f, Y = t ? q.w - m2y : 0.0f;
             a.f[kDF_DLT] += sqrtf(fmaf(x, x, y * y));
             a.f[kDF_DLT + 1] += sqrtf(fmaf(X, X, Y * Y));
-            const float mo[6] = {x * x, x * y, y * y, x, y, 1.0f};
+            const float mo[6] = {x * x, x * y, y * y, x, y, t ? 1.0f : 0.0f};
             const float R = fmaf(X, X, Y * Y);
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -690,38 +945,64 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         __syncthreads();
     }
 
-    // DLT, then the LM set-up and first trial, by the leader warp.
+    // DLT, then the LM set-up and first trial, by the leader warp.  FP64 runs
+    // at 1/64 of the FP32 rate on this part, and each FP64 instruction of a
+    // serial chain costs hundreds of cycles, so only the DLT that is itself
+    // the result (lm_iters = 0) uses it; everything else is FP32 and
+    // double-float.
     if (leader) {
         leader_sums<kDF_P2, 0>(sh);
-        const double d1 = sh.sum[kDF_DLT], d2 = sh.sum[kDF_DLT + 1];
-        const float s1 = d1 > 0.0 ? (float)(1.4142135623730951 * cnt / d1) : 1.0f;
-        const float s2 = d2 > 0.0 ? (float)(1.4142135623730951 * cnt / d2) : 1.0f;
-        if (lane < kDF_DLT) {
-            const int dm[6] = {2, 2, 2, 1, 1, 0}, dw[4] = {0, 1, 1, 2};
-            double f = 1.0;
-            for (int e = 0; e < dm[lane % 6]; ++e) f *= (double)s1;
-            for (int e = 0; e < dw[lane / 6]; ++e) f *= (double)s2;
-            sh.sum[lane] *= f;
-        }
+        const float cnt = sh.cnt;
+        const float d1 = df_round(sh.sum[kDF_DLT]), d2 = df_round(sh.sum[kDF_DLT + 1]);
+        const float s1 = d1 > 0.0f ? 1.41421356f * cnt / d1 : 1.0f;
+        const float s2 = d2 > 0.0f ? 1.41421356f * cnt / d2 : 1.0f;
         if (lane == 0) {
             sh.s1 = s1;
             sh.s2 = s2;
         }
-        __syncwarp();
-        // FP64 to convergence when the DLT is the result; FP32 and three
-        // steps (error ratio lambda1 / lambda2 per step) when it only starts
-        // LM.  Pivot floors 2^-44 and 2^-20 of the largest diagonal entry:
-        // near each precision's rounding of M, far below the eigenvalue gap.
-        const bool ok = lm_iters == 0
-                            ? dlt_leader<double>(sh, sh.M, sh.L9, sh.r9, 5.684341886080802e-14, 1e-11, kInvIters)
-                            : dlt_leader<float>(sh, sh.Mf, sh.L9f, sh.r9f, 9.5367431640625e-07f, 0.0f, 3);
-        // LM gauge h33 = 1 needs the normalised h33 away from zero (v has unit norm)
-        const bool gauge = ok && fabs(sh.v[8]) >= 1e-3;
-        if (gauge && lane < 8) {
-            sh.pd[lane] = sh.v[lane] / sh.v[8];
-            sh.par[lane] = (float)sh.pd[lane];
+        // the factor s1^(degree in x, y) s2^(degree in X, Y) of moment k
+        const float f1[3] = {1.0f, s1, s1 * s1}, f2[3] = {1.0f, s2, s2 * s2};
+        constexpr int dm[6] = {2, 2, 2, 1, 1, 0}, dw[4] = {0, 1, 1, 2};
+        bool fact, gauge;                           // factorisation done; LM gauge h33 = 1 usable
+        if (lm_iters == 0) {
+            // FP64 to convergence: the DLT is the result (pivot floor 2^-44 of
+            // the largest diagonal entry)
+            if (lane < kDF_DLT) {
+                const DF sk = sh.sum[lane];
+                const int am = lane % 6 == 5 ? 0 : (lane % 6 < 3 ? 2 : 1), aw = lane < 6 ? 0 : (lane < 18 ? 1 : 2);
+                sh.dsum[lane] = ((double)sk.h + (double)sk.l) * ((double)f1[am] * (double)f2[aw]);
+            }
+            __syncwarp();
+            fact = dlt_leader<double>(sh, sh.M, sh.L9, sh.r9, 5.684341886080802e-14, 1e-11, kInvIters);
+            // LM gauge h33 = 1 needs the normalised h33 away from zero (v has unit norm)
+            gauge = fact && fabs(sh.v[8]) >= 1e-3;
+            if (lane < 9) {
+                const double vk = sh.v[lane];
+                const float h = (float)vk;
+                sh.hn[lane] = DF{h, (float)(vk - (double)h)};
+            }
+            if (gauge && lane < 8) {
+                const double pk = sh.v[lane] / sh.v[8];
+                const float h = (float)pk;
+                sh.pd[lane] = DF{h, (float)(pk - (double)h)};
+                sh.par[lane] = h;
+            }
+        } else {
+            // FP32 in registers: it only starts LM
+            float mo[kDF_DLT];
+#pragma unroll
+            for (int k = 0; k < kDF_DLT; ++k) mo[k] = df_round(sh.sum[k]) * (f1[dm[k % 6]] * f2[dw[k / 6]]);
+            float x[9];
+            fact = dlt_start(mo, x);
+            gauge = fact && fabsf(x[8]) >= 1e-3f;
+            if (lane < 9) sh.hn[lane] = DF{fact ? lane_pick<9>(x, lane) : 0.0f, 0.0f};
+            if (gauge && lane < 8) {
+                const float pk = lane_pick<9>(x, lane) / x[8];
+                sh.pd[lane] = DF{pk, 0.0f};
+                sh.par[lane] = pk;
+            }
         }
-        if (lane == 0) sh.go = gauge ? 1 : (ok ? 0 : -1);
+        if (lane == 0) sh.go = gauge ? 1 : (fact ? 0 : -1);
     }
     __syncthreads();
     if (sh.go < 0) {                                // factorisation failed: no fit
@@ -733,20 +1014,25 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
     // the DLT when lm_iters = 0), then one pass per evaluated trial step.
     bool lm_ok = false;
     if (sh.go) {
-        lm_pass(c, m, n, sh);
+        lm_pass(pts, sh);
         if (leader) {
             leader_sums<kDF_LM, kF_LM>(sh);
-            lm_assemble(sh.sumf, sh.A);
-            if (lane < 8) sh.g[lane] = sh.sum[lane];
-            float dmax = warp_max(lane < 8 ? sh.A[lane * 9] : 0.0f);
+            if (lane < kF_LM) sh.Asum[lane] = sh.sumf[lane];
+            if (lane < 8) sh.g[lane] = df_round(sh.sum[lane]);
+            // largest diagonal entry of J^T J: sums q xx, q yy, q and q (u^2 + v^2) {xx, yy}
+            const float *f = sh.sumf;
+            const float dmax = fmaxf(fmaxf(fmaxf(f[0], f[2]), fmaxf(f[5], f[16])), fmaxf(f[18], 0.0f));
+            const DF s8 = sh.sum[8];
+            const DF F{0.5f * s8.h, 0.5f * s8.l};
+            const float mu = kTau * dmax;
             if (lane == 0) {
-                sh.F = 0.5 * sh.sum[8];
-                sh.mu = kTau * dmax;
+                sh.F = F;
+                sh.mu = mu;
                 sh.nu = 2.0f;
                 sh.it = 0;
             }
             __syncwarp();
-            const bool ok = isfinite(sh.F) && isfinite(sh.mu) && sh.mu > 0.0f;
+            const bool ok = isfinite(F.h) && isfinite(mu) && mu > 0.0f;
             const int go = ok ? lm_trial(sh, lm_iters) : 0;
             if (lane == 0) sh.go = ok ? 1 + go : 0;   // 0: no LM; 1: LM, no more steps; 2: evaluate
         }
@@ -754,7 +1040,7 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         lm_ok = sh.go != 0;
         // sh.go is rewritten by the leader only after the barrier in lm_pass
         while (sh.go == 2) {
-            lm_pass(c, m, n, sh);
+            lm_pass(pts, sh);
             if (leader) {
                 leader_sums<kDF_LM, kF_LM>(sh);
                 lm_update(sh);
@@ -767,16 +1053,62 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
 
     // Back to pixels.
     if (leader) {
-        double hn[9];
+        DF hn[9];
         if (lm_ok) {
+#pragma unroll
             for (int k = 0; k < 8; ++k) hn[k] = sh.pd[k];
-            hn[8] = 1.0;
+            hn[8] = DF{1.0f, 0.0f};
         } else {
-            for (int k = 0; k < 9; ++k) hn[k] = sh.v[k];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) hn[k] = sh.hn[k];
         }
         leader_store(sh, hn, H_out + 9 * (int64_t)p);
-        if (lane == 0 && rms) rms[p] = lm_ok ? (float)(sqrt(2.0 * sh.F / cnt) / (double)sh.s2) : -1.0f;
+        if (lane == 0 && rms) rms[p] = lm_ok ? sqrtf(2.0f * sh.F.h / sh.cnt) / sh.s2 : -1.0f;
     }
+}
+
+// The points a block keeps in shared memory: what is left of half an SM's
+// shared memory (two blocks per SM) after the block's static part, in whole
+// block strides, at 17 bytes a point (the float4 and its mask byte); fewer if
+// two blocks would not fit.  Sets the kernel's dynamic shared memory limit;
+// cached per device.
+struct RefitLaunch {
+    int cap;
+    size_t smem;
+};
+
+RefitLaunch refit_launch()
+{
+    static std::mutex mu;
+    static std::map<int, RefitLaunch> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = cache.find(dev);
+        if (it != cache.end()) return it->second;
+    }
+    int per_sm = 0, reserved = 0, optin = 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, refit_kernel);
+    long avail = (long)per_sm / 2 - reserved - (long)fa.sharedSizeBytes;
+    if (avail > (long)optin - (long)fa.sharedSizeBytes) avail = (long)optin - (long)fa.sharedSizeBytes;
+    constexpr int kBytesPerPoint = (int)sizeof(float4) + 1;
+    int cap = avail > 0 ? (int)(avail / kBytesPerPoint) / kThreads * kThreads : 0;
+    for (; cap > 0; cap -= kThreads) {
+        const size_t smem = (size_t)cap * kBytesPerPoint;
+        if (cudaFuncSetAttribute(refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+            blocks_per_sm(reinterpret_cast<const void *>(refit_kernel), kThreads, smem) >= 2)
+            break;
+    }
+    cudaGetLastError();                     // a refused size above is not an error of this call
+    const RefitLaunch r{cap, (size_t)cap * kBytesPerPoint};
+    std::lock_guard<std::mutex> lock(mu);
+    cache[dev] = r;
+    return r;
 }
 
 }  // namespace
@@ -792,7 +1124,8 @@ extern "C" aca_status aca_refit(const float *corr, const int64_t *offsets, const
     if (P == 0) return ACA_OK;
     if (!corr || !offsets || !H) return set_error(ACA_ERR_INVALID_ARG, "aca_refit: null corr, offsets or H");
     if (!aligned16(corr)) return set_error(ACA_ERR_INVALID_ARG, "aca_refit: corr must be 16-byte aligned");
-    launch_after_previous(refit_kernel, dim3(P), dim3(kThreads), 0, as_stream(stream),
-                          reinterpret_cast<const float4 *>(corr), offsets, mask, lm_iters, H, n_used, rms);
+    const RefitLaunch L = refit_launch();
+    launch_after_previous(refit_kernel, dim3(P), dim3(kThreads), L.smem, as_stream(stream),
+                          reinterpret_cast<const float4 *>(corr), offsets, mask, lm_iters, H, n_used, rms, L.cap);
     return check_launch("aca_refit");
 }
