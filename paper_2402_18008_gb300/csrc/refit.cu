@@ -23,8 +23,8 @@
 //   - sums whose cancellation matters (the DLT moments, the gradient J^T r
 //     and the cost) are double-float: FP32 partials over chunks of 8 points,
 //     TwoSum accumulation, then per warp a transposition through shared
-//     memory (lane k adds up value k of the 32 lanes; a shuffle tree for the
-//     24 DLT moments, summed once) and a sum over the warps, all in a fixed
+//     memory (lane k adds up value k of the 32 lanes; in two rounds for the
+//     26 sums of the DLT pass) and a sum over the warps, all in a fixed
 //     order (deterministic); J^T J, which only shapes the step, is summed in
 //     FP32;
 //   - the DLT eigenvector is computed in FP64 when it is the result
@@ -92,7 +92,7 @@ struct Shared {
     int it;                           // trial steps taken
 };
 
-// Double-float accumulator: FP32 partials per chunk of kChunk points, then
+// Double-float accumulator: FP32 partials per chunk of kChunk slots, then
 // TwoSum into (h, l).
 template <int K>
 struct DFAcc {
@@ -111,9 +111,11 @@ struct DFAcc {
         for (int k = 0; k < K; ++k) { s[k] = df_add(s[k], DF{f[k], 0.0f}); f[k] = 0.0f; }
         c = 0;
     }
-    __device__ void tick()
+    // after `slots` more slots (the same count in every lane)
+    __device__ void tick(int slots)
     {
-        if (++c == kChunk) flush();
+        c += slots;
+        if (c >= kChunk) flush();
     }
 };
 
@@ -170,22 +172,29 @@ __device__ void warp_partials(const DF (&s)[K], const float *f, Shared &sh)
     }
 }
 
-// Per-warp sums by a shuffle tree, for passes with more values than the
-// transposition scratch holds (the DLT moments, once per problem).
-template <int K>
-__device__ void warp_partials_shfl(const DF (&s)[K], Shared &sh)
+// Per-warp sums of the double-float values [K0, K0 + KN) of s by
+// transposition, for passes with more values than the scratch holds at once
+// (the DLT moments: two rounds, once per problem); same order as
+// warp_partials.
+template <int K0, int KN, int K>
+__device__ void warp_partials_part(const DF (&s)[K], Shared &sh)
 {
+    static_assert(KN * 2 * kPad <= kTr && K0 + KN <= K, "round does not fit the transposition scratch");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *t = sh.tr[warp];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        DF x = s[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const DF y{__shfl_xor_sync(0xffffffffu, x.h, o), __shfl_xor_sync(0xffffffffu, x.l, o)};
-            x = df_renorm(df_add(x, y));
-        }
-        if (lane == 0) sh.wpart[warp][k] = x;
+    for (int k = 0; k < KN; ++k) {
+        t[(k * kPad + lane) * 2] = s[K0 + k].h;
+        t[(k * kPad + lane) * 2 + 1] = s[K0 + k].l;
     }
+    __syncwarp();
+    if (lane < KN) {
+        const float *r = t + lane * kPad * 2;
+        DF a{r[0], r[1]};
+        for (int i = 1; i < 32; ++i) a = df_add(a, DF{r[2 * i], r[2 * i + 1]});
+        sh.wpart[warp][K0 + lane] = df_renorm(a);
+    }
+    __syncwarp();
 }
 
 // Leader warp, after the block barrier: sums over the warps into sh.sum
@@ -348,17 +357,18 @@ struct Points {
     __device__ uint8_t *sm() const { return s_pts + (size_t)cap * sizeof(float4); }
 };
 
-// Calls f(q, t) for every slot of the block's problem: the block's threads
-// stride over the points, all of them taking the same number of steps, and
-// t says whether the slot holds a used point (q is zero otherwise), so the
-// per-point code runs without divergence and the accumulators' chunk flushes
+// Calls f(q, t) for every slot of the block's problem, and step(U) after
+// each U slots: the block's threads stride over the points, all of them
+// taking the same number of steps, and t says whether the slot holds a used
+// point (q is zero otherwise), so the per-point code runs without divergence
+// and the accumulators' chunk flushes (in step, one copy of the code a loop)
 // happen on the same step in every lane; f must make an unused slot add
 // nothing.  Each thread keeps U loads in flight (the passes are otherwise
 // bound by one memory round trip per step).  A correspondence is loaded
 // whether or not its mask byte is set, so both loads are in flight at once;
 // the masked-out points share cache sectors with the used ones.
-template <int U, class Fn>
-__device__ __forceinline__ void for_global(const Points &P, int64_t from, bool fill, Fn &&f)
+template <int U, class Fn, class Step>
+__device__ __forceinline__ void for_global(const Points &P, int64_t from, bool fill, Fn &&f, Step &&step)
 {
     for (int64_t b0 = from; b0 < P.n; b0 += U * kThreads) {
         float4 q[U];
@@ -382,6 +392,7 @@ __device__ __forceinline__ void for_global(const Points &P, int64_t from, bool f
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) f(t[u] ? q[u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), t[u]);
+        step(U);
     }
 }
 
@@ -389,16 +400,16 @@ constexpr int kUnroll = 4;
 
 // The first pass: every point from global memory, eight loads in flight a
 // thread (first touch: HBM latency), filling the shared copy.
-template <class Fn>
-__device__ __forceinline__ void for_points_fill(const Points &P, Fn &&f)
+template <class Fn, class Step>
+__device__ __forceinline__ void for_points_fill(const Points &P, Fn &&f, Step &&step)
 {
-    for_global<8>(P, 0, true, f);
+    for_global<8>(P, 0, true, f, step);
 }
 
 // A later pass: the shared copy (US loads in flight a thread), then the rest
 // from global memory (UG).
-template <int US = kUnroll, int UG = kUnroll, class Fn>
-__device__ __forceinline__ void for_points(const Points &P, Fn &&f)
+template <int US = kUnroll, int UG = kUnroll, class Fn, class Step>
+__device__ __forceinline__ void for_points(const Points &P, Fn &&f, Step &&step)
 {
     for (int b0 = 0; b0 < P.nr; b0 += US * kThreads) {
         float4 q[US];
@@ -412,8 +423,9 @@ __device__ __forceinline__ void for_points(const Points &P, Fn &&f)
         }
 #pragma unroll
         for (int u = 0; u < US; ++u) f(t[u] ? q[u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), t[u]);
+        step(US);
     }
-    for_global<UG>(P, P.nr, false, f);
+    for_global<UG>(P, P.nr, false, f, step);
 }
 
 struct Frame {
@@ -435,7 +447,7 @@ struct Frame {
 // Writes the unit eigenvector to sh.v; returns false if the factorisation
 // failed.
 template <typename T>
-__device__ bool dlt_leader(Shared &sh, T *M, T *L, T *rd, T floor_rel, T tol, int max_iters)
+__device__ __noinline__ bool dlt_leader(Shared &sh, T *M, T *L, T *rd, T floor_rel, T tol, int max_iters)
 {
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < 81; i += 32) M[i] = T(0);
@@ -523,7 +535,6 @@ __device__ void lm_pass(const Points &P, Shared &sh)
         a.f[3] = fmaf(gv, x, a.f[3]); a.f[4] = fmaf(gv, y, a.f[4]); a.f[5] += gv;
         a.f[6] = fmaf(-gw, x, a.f[6]); a.f[7] = fmaf(-gw, y, a.f[7]);
         a.f[8] += t ? fmaf(ru, ru, rv * rv) : 0.0f;
-        a.tick();
         const float q = iw * iw;
         const float xx = x * x, xy = x * y, yy = y * y;
         const float qu = q * u, qv = q * v, qr = q * fmaf(u, u, v * v);
@@ -534,7 +545,7 @@ __device__ void lm_pass(const Points &P, Shared &sh)
         f[11] = fmaf(qv, xx, f[11]); f[12] = fmaf(qv, xy, f[12]); f[13] = fmaf(qv, yy, f[13]);
         f[14] = fmaf(qv, x, f[14]); f[15] = fmaf(qv, y, f[15]);
         f[16] = fmaf(qr, xx, f[16]); f[17] = fmaf(qr, xy, f[17]); f[18] = fmaf(qr, yy, f[18]);
-    });
+    }, [&](int slots) { a.tick(slots); });
     a.flush();
     warp_partials<kDF_LM, kF_LM>(a.s, f, sh);
     __syncthreads();
@@ -591,7 +602,7 @@ __device__ __forceinline__ void fill_packed(const float (&m)[K], float (&a)[n * 
 // M^-1 (the squared column norms of L^-1), then three inverse-iteration
 // steps (error ratio lambda1 / lambda2 per step).  False if the
 // factorisation failed.
-__device__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
+__device__ __noinline__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
 {
     float a[45], rd[9];
     fill_packed<9>(m, a);
@@ -637,12 +648,36 @@ __device__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
     return true;
 }
 
+// Leader warp, after the first pass: the LM state at the start (gradient,
+// J^T J sums, cost, damping mu0 = tau * max diag(J^T J)); false if the cost
+// or the damping is not finite and positive.
+__device__ __noinline__ bool lm_start(Shared &sh)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < kF_LM) sh.Asum[lane] = sh.sumf[lane];
+    if (lane < 8) sh.g[lane] = df_round(sh.sum[lane]);
+    // largest diagonal entry of J^T J: sums q xx, q yy, q and q (u^2 + v^2) {xx, yy}
+    const float *f = sh.sumf;
+    const float dmax = fmaxf(fmaxf(fmaxf(f[0], f[2]), fmaxf(f[5], f[16])), fmaxf(f[18], 0.0f));
+    const DF s8 = sh.sum[8];
+    const DF F{0.5f * s8.h, 0.5f * s8.l};
+    const float mu = kTau * dmax;
+    if (lane == 0) {
+        sh.F = F;
+        sh.mu = mu;
+        sh.nu = 2.0f;
+        sh.it = 0;
+    }
+    __syncwarp();
+    return isfinite(F.h) && isfinite(mu) && mu > 0.0f;
+}
+
 // Leader warp: the next trial step (J^T J + mu I) d = -g, counting every
 // trial (a non-positive-definite matrix is a rejected step).  Returns 1
 // (evaluate pd + d, in sh.par) or 0 (no more trials: the budget is spent, the
 // step is below the FP32 resolution of the parameters, or the damping is no
 // longer finite).  Every lane factors and solves in registers.
-__device__ int lm_trial(Shared &sh, int budget)
+__device__ __noinline__ int lm_trial(Shared &sh, int budget)
 {
     const int lane = threadIdx.x & 31;
     float m[kF_LM], g[8], p[8];
@@ -696,7 +731,7 @@ __device__ int lm_trial(Shared &sh, int budget)
 }
 
 // Leader warp: gain ratio of the evaluated step; accept or reject it.
-__device__ void lm_update(Shared &sh)
+__device__ __noinline__ void lm_update(Shared &sh)
 {
     const int lane = threadIdx.x & 31;
     const DF F = sh.F, sn = sh.sum[8];
@@ -746,7 +781,7 @@ __device__ __forceinline__ DF df_div(DF x, float b)
 // translation columns cancel), with unit Frobenius norm and the sign that
 // makes h33 > 0 (or, when |h33| < 1e-6 |H|, the first entry of largest
 // magnitude > 0); lane i writes entry i.
-__device__ void leader_store(const Shared &sh, const DF (&hn)[9], float *out)
+__device__ __noinline__ void leader_store(const Shared &sh, const DF (&hn)[9], float *out)
 {
     const int lane = threadIdx.x & 31;
     const float s1 = sh.s1, s2 = sh.s2, a1x = sh.mu1x, a1y = sh.mu1y, a2x = sh.mu2x, a2y = sh.mu2y;
@@ -806,7 +841,7 @@ __device__ __forceinline__ int size_class(int64_t N)
     return c < kClasses ? c : kClasses - 1;
 }
 
-__device__ int32_t longest_first(const int64_t *__restrict__ offsets, int32_t P, int32_t b, int32_t *hist,
+__device__ __noinline__ int32_t longest_first(const int64_t *__restrict__ offsets, int32_t P, int32_t b, int32_t *hist,
                                  int32_t *scratch)
 {
     for (int k = threadIdx.x; k < kClasses; k += kThreads) hist[k] = 0;
@@ -889,8 +924,7 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         a.zero();
         for_points_fill(pts, [&](float4 q, bool t) {
             a.f[0] += t ? 1.0f : 0.0f; a.f[1] += q.x; a.f[2] += q.y; a.f[3] += q.z; a.f[4] += q.w;
-            a.tick();
-        });
+        }, [&](int slots) { a.tick(slots); });
         a.flush();
         warp_partials<5, 0>(a.s, nullptr, sh);
         __syncthreads();
@@ -938,10 +972,10 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
                 a.f[12 + k] = fmaf(Y, mo[k], a.f[12 + k]);
                 a.f[18 + k] = fmaf(R, mo[k], a.f[18 + k]);
             }
-            a.tick();
-        });
+        }, [&](int slots) { a.tick(slots); });
         a.flush();
-        warp_partials_shfl<kDF_P2>(a.s, sh);
+        warp_partials_part<0, kDF_P2 / 2>(a.s, sh);
+        warp_partials_part<kDF_P2 / 2, kDF_P2 - kDF_P2 / 2>(a.s, sh);
         __syncthreads();
     }
 
@@ -1014,41 +1048,22 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
     // the DLT when lm_iters = 0), then one pass per evaluated trial step.
     bool lm_ok = false;
     if (sh.go) {
-        lm_pass(pts, sh);
-        if (leader) {
-            leader_sums<kDF_LM, kF_LM>(sh);
-            if (lane < kF_LM) sh.Asum[lane] = sh.sumf[lane];
-            if (lane < 8) sh.g[lane] = df_round(sh.sum[lane]);
-            // largest diagonal entry of J^T J: sums q xx, q yy, q and q (u^2 + v^2) {xx, yy}
-            const float *f = sh.sumf;
-            const float dmax = fmaxf(fmaxf(fmaxf(f[0], f[2]), fmaxf(f[5], f[16])), fmaxf(f[18], 0.0f));
-            const DF s8 = sh.sum[8];
-            const DF F{0.5f * s8.h, 0.5f * s8.l};
-            const float mu = kTau * dmax;
-            if (lane == 0) {
-                sh.F = F;
-                sh.mu = mu;
-                sh.nu = 2.0f;
-                sh.it = 0;
-            }
-            __syncwarp();
-            const bool ok = isfinite(F.h) && isfinite(mu) && mu > 0.0f;
-            const int go = ok ? lm_trial(sh, lm_iters) : 0;
-            if (lane == 0) sh.go = ok ? 1 + go : 0;   // 0: no LM; 1: LM, no more steps; 2: evaluate
-        }
-        __syncthreads();
-        lm_ok = sh.go != 0;
-        // sh.go is rewritten by the leader only after the barrier in lm_pass
-        while (sh.go == 2) {
+        bool first = true;
+        do {
             lm_pass(pts, sh);
             if (leader) {
                 leader_sums<kDF_LM, kF_LM>(sh);
-                lm_update(sh);
-                const int go = lm_trial(sh, lm_iters);
-                if (lane == 0) sh.go = 1 + go;
+                bool ok = true;
+                if (first) ok = lm_start(sh);
+                else lm_update(sh);
+                const int go = ok ? 1 + lm_trial(sh, lm_iters) : 0;
+                if (lane == 0) sh.go = go;        // 0: no LM; 1: LM, no more steps; 2: evaluate
             }
             __syncthreads();
-        }
+            if (first) lm_ok = sh.go != 0;
+            first = false;
+            // sh.go is rewritten by the leader only after the barrier in lm_pass
+        } while (sh.go == 2);
     }
 
     // Back to pixels.
