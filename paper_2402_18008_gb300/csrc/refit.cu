@@ -27,9 +27,10 @@
 //     26 sums of the DLT pass) and a sum over the warps, all in a fixed
 //     order (deterministic); J^T J, which only shapes the step, is summed in
 //     FP32;
-//   - the DLT eigenvector is computed in FP64 when it is the result
-//     (lm_iters = 0) and in FP32 when it only starts LM, which converges to
-//     the same minimiser from either start;
+//   - the DLT eigenvector is refined to double-float accuracy (FP32 factor,
+//     double-float residuals) when it is the result (lm_iters = 0), and is
+//     FP32 when it only starts LM, which converges to the same minimiser
+//     from either start;
 //   - the 8x8 LM steps are FP32 (an inexact step only slows the iteration;
 //     its fixed point is set by the gradient); the parameters and the cost
 //     are double-float, and so is the map back to pixels, whose translation
@@ -57,7 +58,9 @@ constexpr int kThreads = 256;         // 2 blocks (of <= 128 registers a thread)
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 8;
 constexpr int kPad = 33;              // transposition row stride (floats per value, padded)
-constexpr int kInvIters = 16;         // inverse-iteration cap (FP64 DLT)
+constexpr int kRefineMax = 16;        // refinement steps of the DLT eigenvector (lm_iters = 0), at most
+constexpr int kBisect = 12;           // bisection steps for its shift, when it needs one
+constexpr float kSlow = 0.01f;        // contraction per step above which the refinement shifts
 constexpr float kTau = 1e-3f;         // mu0 = tau * max diag(J^T J)
 constexpr float kEpsStep = 5.9604644775390625e-8f;   // 2^-24: parameters are used in FP32
 constexpr float kCostNoise = 1.52587890625e-05f;     // 2^-16: FP32 noise of the cost, relative
@@ -75,9 +78,8 @@ struct Shared {
     float wpartf[kWarps][kF_LM];
     DF sum[kDF_P2];                   // block sums (leader warp), renormalised
     float sumf[kF_LM];
-    double dsum[kDF_DLT];             // the DLT moments in FP64 (when the DLT is the result)
-    double M[81], L9[81], r9[9];      // DLT (FP64, when it is the result)
-    double v[9];                      // its eigenvector
+    DF mdf[kDF_DLT];                  // the DLT moments of the normalised points (lm_iters = 0)
+    DF Mdf[45];                       // the DLT normal matrix from them, packed lower triangle
     DF hn[9];                         // the DLT fit in the normalised frames
     float par[8];                     // parameters broadcast to the pass
     float mu1x, mu1y, s1, mu2x, mu2y, s2, cnt;
@@ -215,62 +217,6 @@ __device__ void leader_sums(Shared &sh)
         sh.sumf[lane - K] = a;
     }
     __syncwarp();
-}
-
-// Cholesky factor of the n x n symmetric S (row-major, shared) by one warp:
-// lane i builds row i of L in registers.  Pivots below `floor` are raised to
-// it.  Writes L (row-major, lower) and rd[j] = 1 / L[j][j]; returns false on
-// a non-positive or non-finite pivot (all lanes agree).
-template <int n, typename T>
-__device__ bool warp_cholesky(const T *S, T *L, T *rd, T floor)
-{
-    const int lane = threadIdx.x & 31;
-    T row[n];
-#pragma unroll
-    for (int k = 0; k < n; ++k) row[k] = T(0);
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < n; ++j) {
-        T s = lane < n ? S[lane * n + j] : T(0);
-#pragma unroll
-        for (int k = 0; k < j; ++k) s -= row[k] * __shfl_sync(0xffffffffu, row[k], j);
-        T d = __shfl_sync(0xffffffffu, s, j);
-        if (d < floor) d = floor;
-        ok = ok && d > T(0) && isfinite(d);
-        const T ljj = sqrt(d);
-        const T r = T(1) / ljj;
-        if (lane == j) row[j] = ljj;
-        else if (lane > j && lane < n) row[j] = s * r;
-        if (lane == 0) rd[j] = r;
-    }
-    if (lane < n) {
-#pragma unroll
-        for (int k = 0; k < n; ++k) L[lane * n + k] = k <= lane ? row[k] : T(0);
-    }
-    __syncwarp();
-    return ok;
-}
-
-// x := (L L^T)^-1 x by one warp; lane i holds x_i (lanes >= n hold 0).
-template <int n, typename T>
-__device__ T warp_chol_solve(const T *L, const T *rd, T x)
-{
-    const int lane = threadIdx.x & 31;
-    // L y = x (column-oriented: y_j final at step j, then eliminated below)
-#pragma unroll
-    for (int j = 0; j < n; ++j) {
-        const T yj = __shfl_sync(0xffffffffu, x, j) * rd[j];
-        if (lane == j) x = yj;
-        else if (lane > j && lane < n) x -= L[lane * n + j] * yj;
-    }
-    // L^T z = y
-#pragma unroll
-    for (int j = n - 1; j >= 0; --j) {
-        const T zj = __shfl_sync(0xffffffffu, x, j) * rd[j];
-        if (lane == j) x = zj;
-        else if (lane < j) x -= L[j * n + lane] * zj;
-    }
-    return x;
 }
 
 // Small dense algebra in registers, run redundantly by every lane of the
@@ -441,69 +387,6 @@ struct Frame {
     }
 };
 
-// Leader warp: the normalised DLT from the 24 moments in sh.dsum, in precision
-// T.  Rows of Eq. 2 per point: (xb, 0, -X xb) and (0, -xb, Y xb), so M has
-// blocks S_1 (twice), -S_X, -S_Y and S_R, S_w = sum w {xx, xy, yy, x, y, 1}.
-// Writes the unit eigenvector to sh.v; returns false if the factorisation
-// failed.
-template <typename T>
-__device__ __noinline__ bool dlt_leader(Shared &sh, T *M, T *L, T *rd, T floor_rel, T tol, int max_iters)
-{
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < 81; i += 32) M[i] = T(0);
-    __syncwarp();
-    if (lane < 9) {
-        const int mi[3][3] = {{0, 1, 3}, {1, 2, 4}, {3, 4, 5}};
-        const int i = lane / 3, j = lane % 3, k = mi[i][j];
-        M[i * 9 + j] = (T)sh.dsum[k];
-        M[(3 + i) * 9 + 3 + j] = (T)sh.dsum[k];
-        M[i * 9 + 6 + j] = -(T)sh.dsum[6 + k];
-        M[(6 + j) * 9 + i] = -(T)sh.dsum[6 + k];
-        M[(3 + i) * 9 + 6 + j] = -(T)sh.dsum[12 + k];
-        M[(6 + j) * 9 + 3 + i] = -(T)sh.dsum[12 + k];
-        M[(6 + i) * 9 + 6 + j] = (T)sh.dsum[18 + k];
-    }
-    __syncwarp();
-    const T dmax = warp_max(lane < 9 ? M[lane * 10] : T(0));
-    // the pivot floor is a shift far below the eigenvalue gap
-    const bool ok = warp_cholesky<9, T>(M, L, rd, dmax * floor_rel);
-    // diag(M^-1)_k = |L^-1 e_k|^2: lane k solves L z = e_k on its own
-    T dk = T(-1);
-    if (ok && lane < 9) {
-        T z[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            T s = i == lane ? T(1) : T(0);
-#pragma unroll
-            for (int j = 0; j < i; ++j) s -= L[i * 9 + j] * z[j];
-            z[i] = s * rd[i];
-        }
-        dk = T(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dk += z[i] * z[i];
-    }
-    int kb = lane;
-    T best = dk;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int okb = __shfl_xor_sync(0xffffffffu, kb, o);
-        if (ob > best || (ob == best && okb < kb)) { best = ob; kb = okb; }
-    }
-    T x = lane == kb ? T(1) : T(0);
-    for (int it = 0; ok && it < max_iters; ++it) {
-        T y = warp_chol_solve<9, T>(L, rd, x);
-        const T ny = warp_sum(y * y), dot = warp_sum(y * x);
-        y *= (dot < T(0) ? T(-1) : T(1)) / sqrt(ny);
-        const T ch = warp_max(fabs(y - x));
-        x = y;
-        if (ch < tol) break;
-    }
-    if (lane < 9) sh.v[lane] = ok ? (double)x : 0.0;
-    __syncwarp();
-    return ok;
-}
-
 // One LM pass at the parameters in sh.par: per-warp sums of, with
 // xb = (x, y, 1), b = (x, y), q = 1/w^2:
 //   double-float: g = J^T r (u rows: r_u xb / w; v rows: r_v xb / w;
@@ -595,16 +478,15 @@ __device__ __forceinline__ void fill_packed(const float (&m)[K], float (&a)[n * 
         }
 }
 
-// Leader warp, every lane: the FP32 normalised DLT that starts LM, from the
-// 24 moments of the normalised points: M, its Cholesky factor (pivot floor
-// 2^-20 of the largest diagonal entry: near FP32's rounding of M, far below
-// the eigenvalue gap), the start e_k with k the largest diagonal entry of
-// M^-1 (the squared column norms of L^-1), then three inverse-iteration
-// steps (error ratio lambda1 / lambda2 per step).  False if the
-// factorisation failed.
-__device__ __noinline__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
+// Leader warp, every lane: the FP32 normalised DLT from the 24 moments of
+// the normalised points: M, its Cholesky factor (pivot floor 2^-20 of the
+// largest diagonal entry: near FP32's rounding of M, far below the
+// eigenvalue gap), the start e_k with k the largest diagonal entry of M^-1
+// (the squared column norms of L^-1), then three inverse-iteration steps
+// (error ratio lambda1 / lambda2 per step).  False if the factorisation
+// failed.
+__device__ __forceinline__ bool dlt_fp32(const float (&m)[kDF_DLT], float (&a)[45], float (&rd)[9], float (&x)[9])
 {
-    float a[45], rd[9];
     fill_packed<9>(m, a);
     float dmax = 0.0f;
 #pragma unroll
@@ -647,6 +529,257 @@ __device__ __noinline__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
     }
     return true;
 }
+
+__device__ __noinline__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
+{
+    float a[45], rd[9];
+    return dlt_fp32(m, a, rd, x);
+}
+
+// (a.h + a.l)(b.h + b.l) to double-float accuracy (the a.l b.l term is below it).
+__device__ __forceinline__ DF df_mul2(DF a, DF b)
+{
+    const DF p = df_prod(a.h, b.h);
+    return DF{p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l))};
+}
+
+// a / b in double-float: the quotient's leading part, then the remainder's.
+__device__ __forceinline__ DF df_div2(DF a, DF b)
+{
+    const float q = a.h / b.h;
+    const DF r = df_sub(a, df_mul2(b, DF{q, 0.0f}));
+    return DF{q, df_round(r) / b.h};
+}
+
+// Leader warp, every lane: the DLT eigenvector when it is the result, to
+// double-float accuracy without FP64 (fac: 72 floats of scratch, for the
+// FP32 factor and M v).  The FP32 start of dlt_fp32, then steps of
+// eigenvector refinement: with the Rayleigh quotient
+// lambda = v^T M v / v^T v and the residual r = M v - lambda v, both in
+// double-float from the double-float matrix Mdf (shared, packed), the
+// correction solves (M - sigma I) d = r with the FP32 factor and keeps the
+// part of d orthogonal to v: v := v - (d - (d.v / v.v) v).  Against the
+// exact correction (M - lambda I)^-1 r this errs by
+// (lambda - sigma) / (lambda_j - sigma) on each other eigendirection j and
+// by FP32 rounding relative to the complement's conditioning, so each step
+// shrinks the error by about
+// max((lambda_min - sigma) / (lambda_2 - sigma), 2^-24 lambda_max / lambda_2),
+// The first steps use sigma = 0, which suffices for inlier sets
+// (lambda_min / lambda_2 ~ 1e-4); when a step shrinks the correction by less
+// than kSlow (a DLT over sets with many outliers, where lambda_min is near
+// lambda_2 and unshifted inverse iteration crawls), sigma moves to just
+// below lambda_min (bisection on whether M - sigma I factors, from the
+// Rayleigh quotient down), the factor with it, and three inverse-iteration
+// steps with that factor bring v close before refining on.  Steps until the
+// correction is below 2^-36 of v (far below what the FP32 result resolves,
+// above the double-float residual's floor of about 2^-48 lambda_max /
+// lambda_2; two or three steps for inlier sets), kRefineMax at most.
+// The factor of M - sigma I (pivot floor 2^-20 of M's largest diagonal
+// entry) to the scratch; false if it failed.
+__device__ __forceinline__ bool store_factor(const float (&m)[kDF_DLT], float sigma, float *fac)
+{
+    float a[45], rd[9];
+    fill_packed<9>(m, a);
+    float dmax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        dmax = fmaxf(dmax, a[tri(k, k)]);
+        a[tri(k, k)] -= sigma;
+    }
+    const bool ok = reg_cholesky<9>(a, rd, dmax * 9.5367431640625e-07f);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int e = 0; e < 45; ++e) fac[e] = a[e];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fac[45 + i] = rd[i];
+    }
+    __syncwarp();
+    return ok;
+}
+
+// The largest sigma in [0, hi] at which M - sigma I still factors in FP32
+// (every pivot positive), by kBisect bisection steps: M's smallest
+// eigenvalue lies within FP32 rounding of M above it.
+__device__ __forceinline__ float shift_below_min(const float (&m)[kDF_DLT], float hi)
+{
+    float lo = 0.0f;
+    for (int b = 0; b < kBisect; ++b) {
+        const float mid = 0.5f * (lo + hi);
+        float a[45], rd[9];
+        fill_packed<9>(m, a);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a[tri(k, k)] -= mid;
+        if (reg_cholesky<9>(a, rd, 0.0f)) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __noinline__ bool dlt_refined(const DF *Mdf, const float (&m)[kDF_DLT], float *fac, DF (&v)[9])
+{
+    {
+        float a[45], rd[9], x[9];
+        if (!dlt_fp32(m, a, rd, x)) return false;
+        // the factor to the scratch (every lane writes the same values)
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int e = 0; e < 45; ++e) fac[e] = a[e];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fac[45 + i] = rd[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = DF{x[i], 0.0f};
+    }
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    bool shifted = false;
+    float prev = 0.0f;
+    for (int it = 0; it < kRefineMax; ++it) {
+        // w = M v: lane i < 9 forms row i, through the scratch to every lane
+        {
+            const int i = lane < 9 ? lane : 0;
+            DF t{0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < 9; ++j) t = df_add(t, df_mul2(Mdf[i >= j ? tri(i, j) : tri(j, i)], v[j]));
+            if (lane < 9) {
+                fac[54 + 2 * lane] = t.h;
+                fac[55 + 2 * lane] = t.l;
+            }
+        }
+        __syncwarp();
+        DF w[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) w[i] = DF{fac[54 + 2 * i], fac[55 + 2 * i]};
+        __syncwarp();
+        DF num{0.0f, 0.0f}, den{0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            num = df_add(num, df_mul2(v[i], w[i]));
+            den = df_add(den, df_mul2(v[i], v[i]));
+        }
+        const DF lam = df_div2(num, den);
+        float d[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = df_round(df_sub(w[i], df_mul2(lam, v[i])));
+        {
+            float a[45], rd[9];
+#pragma unroll
+            for (int e = 0; e < 45; ++e) a[e] = fac[e];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) rd[i] = fac[45 + i];
+            reg_chol_solve<9>(a, rd, d);
+        }
+        float dv = 0.0f, vv = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            dv = fmaf(d[i], v[i].h, dv);
+            vv = fmaf(v[i].h, v[i].h, vv);
+        }
+        const float c = dv / vv;
+        float dmax = 0.0f, vmax = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float di = fmaf(c, v[i].h, -d[i]);
+            dmax = fmaxf(dmax, fabsf(di));
+            vmax = fmaxf(vmax, fabsf(v[i].h));
+            v[i] = df_renorm(df_add(v[i], DF{di, 0.0f}));
+        }
+        if (!(dmax > 1.4551915228366852e-11f * vmax)) break;      // 2^-36; also ends on NaN
+        // slow contraction (lambda_min not small against lambda_2): shift
+        // the factor to just below lambda_min, the Rayleigh quotient bounding
+        // it from above
+        if (!shifted && it >= 1 && dmax > kSlow * prev) {
+            shifted = true;
+            const float rq = df_round(lam);
+            const float sigma = shift_below_min(m, rq > 0.0f ? rq : 0.0f);
+            if (!store_factor(m, sigma, fac)) return false;
+            // v is still far from the eigenvector: three FP32 inverse-iteration
+            // steps with the shifted factor (error ratio
+            // (lambda_min - sigma) / (lambda_2 - sigma) per step) before the
+            // refinement resumes
+            float a[45], rd[9], x[9];
+#pragma unroll
+            for (int e = 0; e < 45; ++e) a[e] = fac[e];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                rd[i] = fac[45 + i];
+                x[i] = v[i].h;
+            }
+            for (int k = 0; k < 3; ++k) {
+                float y[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) y[i] = x[i];
+                reg_chol_solve<9>(a, rd, y);
+                float ny = 0.0f, dot = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    ny = fmaf(y[i], y[i], ny);
+                    dot = fmaf(y[i], x[i], dot);
+                }
+                const float sc = (dot < 0.0f ? -1.0f : 1.0f) / sqrtf(ny);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) x[i] = y[i] * sc;
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) v[i] = DF{x[i], 0.0f};
+        }
+        prev = dmax;
+    }
+    return true;
+}
+
+// v[lane] for lane < 9 (else zero) without an indexed register access.
+__device__ __forceinline__ DF lane_pick_df(const DF (&v)[9], int lane)
+{
+    DF r{0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r = lane == i ? v[i] : r;
+    return r;
+}
+
+// Leader warp: the DLT as the result (lm_iters = 0).  Double-float moments
+// of the normalised points and the normal matrix from them, the refined
+// eigenvector; writes sh.hn and, when the gauge h33 = 1 is usable, the LM
+// parameters sh.pd / sh.par.  Returns 0 (the factorisation failed), 1 (no
+// gauge) or 2.
+__device__ __noinline__ int dlt_result(Shared &sh, float s1, float s2)
+{
+    const int lane = threadIdx.x & 31;
+    constexpr int dm[6] = {2, 2, 2, 1, 1, 0}, dw[4] = {0, 1, 1, 2};
+    if (lane < kDF_DLT) {
+        const int am = dm[lane % 6], aw = dw[lane / 6];
+        const float fa = am == 0 ? 1.0f : (am == 1 ? s1 : s1 * s1), fb = aw == 0 ? 1.0f : (aw == 1 ? s2 : s2 * s2);
+        sh.mdf[lane] = df_mul(sh.sum[lane], fa * fb);
+    }
+    __syncwarp();
+    for (int e = lane; e < 45; e += 32) {
+        int r = 0;
+        while (tri(r + 1, 0) <= e) ++r;
+        const int k = dlt_code(r, e - tri(r, 0));
+        sh.Mdf[e] = k == 0 ? DF{0.0f, 0.0f} : (k > 0 ? sh.mdf[k - 1] : df_neg(sh.mdf[-k - 1]));
+    }
+    __syncwarp();
+    float mo[kDF_DLT];
+#pragma unroll
+    for (int k = 0; k < kDF_DLT; ++k) mo[k] = df_round(sh.mdf[k]);
+    DF v[9];
+    const bool fact = dlt_refined(sh.Mdf, mo, sh.tr[0], v);
+    float n2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) n2 = fmaf(v[i].h, v[i].h, n2);
+    // LM gauge h33 = 1 needs the normalised h33 away from zero
+    const bool gauge = fact && fabsf(v[8].h) >= 1e-3f * sqrtf(n2);
+    if (lane < 9) sh.hn[lane] = fact ? lane_pick_df(v, lane) : DF{0.0f, 0.0f};
+    if (gauge && lane < 8) {
+        const DF pk = df_div2(lane_pick_df(v, lane), v[8]);
+        sh.pd[lane] = pk;
+        sh.par[lane] = pk.h;
+    }
+    __syncwarp();
+    return gauge ? 2 : (fact ? 1 : 0);
+}
+
 
 // Leader warp, after the first pass: the LM state at the start (gradient,
 // J^T J sums, cost, damping mu0 = tau * max diag(J^T J)); false if the cost
@@ -981,9 +1114,8 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
 
     // DLT, then the LM set-up and first trial, by the leader warp.  FP64 runs
     // at 1/64 of the FP32 rate on this part, and each FP64 instruction of a
-    // serial chain costs hundreds of cycles, so only the DLT that is itself
-    // the result (lm_iters = 0) uses it; everything else is FP32 and
-    // double-float.
+    // serial chain costs hundreds of cycles, so none is used: FP32 and
+    // double-float only.
     if (leader) {
         leader_sums<kDF_P2, 0>(sh);
         const float cnt = sh.cnt;
@@ -999,28 +1131,9 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
         constexpr int dm[6] = {2, 2, 2, 1, 1, 0}, dw[4] = {0, 1, 1, 2};
         bool fact, gauge;                           // factorisation done; LM gauge h33 = 1 usable
         if (lm_iters == 0) {
-            // FP64 to convergence: the DLT is the result (pivot floor 2^-44 of
-            // the largest diagonal entry)
-            if (lane < kDF_DLT) {
-                const DF sk = sh.sum[lane];
-                const int am = lane % 6 == 5 ? 0 : (lane % 6 < 3 ? 2 : 1), aw = lane < 6 ? 0 : (lane < 18 ? 1 : 2);
-                sh.dsum[lane] = ((double)sk.h + (double)sk.l) * ((double)f1[am] * (double)f2[aw]);
-            }
-            __syncwarp();
-            fact = dlt_leader<double>(sh, sh.M, sh.L9, sh.r9, 5.684341886080802e-14, 1e-11, kInvIters);
-            // LM gauge h33 = 1 needs the normalised h33 away from zero (v has unit norm)
-            gauge = fact && fabs(sh.v[8]) >= 1e-3;
-            if (lane < 9) {
-                const double vk = sh.v[lane];
-                const float h = (float)vk;
-                sh.hn[lane] = DF{h, (float)(vk - (double)h)};
-            }
-            if (gauge && lane < 8) {
-                const double pk = sh.v[lane] / sh.v[8];
-                const float h = (float)pk;
-                sh.pd[lane] = DF{h, (float)(pk - (double)h)};
-                sh.par[lane] = h;
-            }
+            const int r = dlt_result(sh, s1, s2);
+            fact = r != 0;
+            gauge = r == 2;
         } else {
             // FP32 in registers: it only starts LM
             float mo[kDF_DLT];

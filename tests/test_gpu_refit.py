@@ -92,12 +92,33 @@ def test_refit_lm_matches_converged_oracle(batch48, iters):
 
 def test_refit_full_size_512_pairs():
     # the batched-RANSAC workload at full size (512 pairs, N log-uniform in
-    # [200, 8000]); masks = the generated inliers; the launch the bench times
+    # [200, 8000]); masks = the generated inliers; the launches the bench
+    # times (10 LM steps, and the DLT alone)
     rb = workloads.ransac_batch(P=512, seed=0)
     H, n_used, rms = _gpu_refit(rb.corr, rb.offsets, rb.is_inlier, 10)
     ref, used = _gate(H, rb.corr, rb.offsets, rb.is_inlier, 200, "refit LM 10 steps (512 pairs)")
     assert np.array_equal(n_used, used)
     _cost_gate(H, ref, rb.corr, rb.offsets, rb.is_inlier, "512 pairs")
+    Hd, nd, _ = _gpu_refit(rb.corr, rb.offsets, rb.is_inlier, 0)
+    _gate(Hd, rb.corr, rb.offsets, rb.is_inlier, 0, "refit DLT (512 pairs)")
+    assert np.array_equal(nd, used)
+
+
+def test_refit_dlt_on_contaminated_sets():
+    # the DLT over every point of pairs with 10-60 % outliers (mask = None):
+    # the smallest eigenvalue of the normal matrix is no longer small against
+    # the next one, so the eigenvector refinement contracts slowly; the
+    # result must still meet the gate
+    probs = [workloads.ransac_problem(n, eps, 1.0, seed=40 + i)
+             for i, (n, eps) in enumerate([(300, 0.9), (800, 0.7), (1500, 0.55), (4000, 0.4), (6000, 0.6)])]
+    corr = np.concatenate([q.corr for q in probs])
+    offsets = np.concatenate([[0], np.cumsum([len(q.corr) for q in probs])]).astype(np.int64)
+    allpts = np.ones(len(corr), bool)
+    H, n_used, _ = _gpu_refit(corr, offsets, None, 0)
+    ref, used = _gate(H, corr, offsets, allpts, 0, "refit DLT, contaminated (5 problems)")
+    assert np.array_equal(n_used, used)
+    H10, _, _ = _gpu_refit(corr, offsets, None, 10)
+    ref10, _ = _gate(H10, corr, offsets, allpts, 200, "refit LM 10 steps, contaminated (5 problems)")
 
 
 def test_refit_noise_free_recovers_the_true_map():
