@@ -232,7 +232,10 @@ __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j
 // In-place Cholesky L L^T of the packed n x n matrix a (right-looking: after
 // column j the trailing block holds S - sum_{k <= j} l_k l_k^T), pivots below
 // `floor` raised to it; rd[j] = 1 / L[j][j].  False on a non-positive or
-// non-finite pivot.
+// non-finite pivot.  The pivot's reciprocal square root is the hardware
+// approximation (a few ulp): every factor here only steers an iteration
+// (the LM step, the DLT start, the refinement's preconditioner), and it
+// halves the dependent chain of a column.
 template <int n>
 __device__ __forceinline__ bool reg_cholesky(float (&a)[n * (n + 1) / 2], float (&rd)[n], float floor)
 {
@@ -242,7 +245,7 @@ __device__ __forceinline__ bool reg_cholesky(float (&a)[n * (n + 1) / 2], float 
         float d = a[tri(j, j)];
         if (d < floor) d = floor;
         ok = ok && d > 0.0f && isfinite(d);
-        const float l = sqrtf(d), r = 1.0f / l;
+        const float r = rsqrtf(d), l = d * r;
         a[tri(j, j)] = l;
         rd[j] = r;
 #pragma unroll
