@@ -1097,10 +1097,14 @@ refit_kernel(const float4 *__restrict__ corr, const int64_t *__restrict__ offset
             // an unused slot: zero centred coordinates and weight
             const float x = t ? q.x - m1x : 0.0f, y = t ? q.y - m1y : 0.0f;
             const float X = t ? q.z - m2x : 0.0f, Y = t ? q.w - m2y : 0.0f;
-            a.f[kDF_DLT] += sqrtf(fmaf(x, x, y * y));
-            a.f[kDF_DLT + 1] += sqrtf(fmaf(X, X, Y * Y));
+            // distances by the hardware reciprocal square root (a few ulp: they
+            // only set the normalising scales); zero for an unused slot (the
+            // argument floored at the smallest normal), without the
+            // special-case path of a correctly rounded sqrt(0)
+            const float r1 = fmaf(x, x, y * y), R = fmaf(X, X, Y * Y);
+            a.f[kDF_DLT] += r1 * rsqrtf(fmaxf(r1, 1.17549435e-38f));
+            a.f[kDF_DLT + 1] += R * rsqrtf(fmaxf(R, 1.17549435e-38f));
             const float mo[6] = {x * x, x * y, y * y, x, y, t ? 1.0f : 0.0f};
-            const float R = fmaf(X, X, Y * Y);
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 a.f[k] += mo[k];
