@@ -41,7 +41,12 @@
 //   - the cost of a trial point carries FP32 rounding noise of about 2^-16
 //     relative, so near the optimum, where the predicted decrease is below
 //     that noise, a step is accepted unless the cost rises by more than the
-//     noise: the gain ratio could not tell such steps apart.
+//     noise: the gain ratio could not tell such steps apart; after two such
+//     accepted steps in a row that also moved the parameters by less than
+//     2^-20 LM stops, since what further steps change is rounding (without
+//     that, a few pairs random-walked at the noise floor through the whole
+//     step budget; the size condition keeps slow linear convergence, as on
+//     sets with many outliers, going).
 #include <math.h>
 
 #include <map>
@@ -64,6 +69,8 @@ constexpr float kSlow = 0.01f;        // contraction per step above which the re
 constexpr float kTau = 1e-3f;         // mu0 = tau * max diag(J^T J)
 constexpr float kEpsStep = 5.9604644775390625e-8f;   // 2^-24: parameters are used in FP32
 constexpr float kCostNoise = 1.52587890625e-05f;     // 2^-16: FP32 noise of the cost, relative
+constexpr int kQuietSteps = 2;        // LM stops after this many accepted quiet steps in a row
+constexpr float kQuietStep = 9.5367431640625e-07f;   // 2^-20: a quiet step's size, relative to the parameters
 
 constexpr int kDF_DLT = 24;           // moments of the normalised points (the DLT)
 constexpr int kDF_P2 = kDF_DLT + 2;   // double-float sums of pass 2 (moments + 2 distance sums)
@@ -92,6 +99,8 @@ struct Shared {
     DF pd[8];                         // parameters
     float d[8], mu, nu;               // step, damping
     int it;                           // trial steps taken
+    int quiet;                        // consecutive accepted quiet steps (small, and below the cost's noise)
+    int small;                        // the evaluated step is below kQuietStep of the parameters
 };
 
 // Double-float accumulator: FP32 partials per chunk of kChunk slots, then
@@ -803,6 +812,7 @@ __device__ __noinline__ bool lm_start(Shared &sh)
         sh.mu = mu;
         sh.nu = 2.0f;
         sh.it = 0;
+        sh.quiet = 0;
     }
     __syncwarp();
     return isfinite(F.h) && isfinite(mu) && mu > 0.0f;
@@ -811,7 +821,9 @@ __device__ __noinline__ bool lm_start(Shared &sh)
 // Leader warp: the next trial step (J^T J + mu I) d = -g, counting every
 // trial (a non-positive-definite matrix is a rejected step).  Returns 1
 // (evaluate pd + d, in sh.par) or 0 (no more trials: the budget is spent, the
-// step is below the FP32 resolution of the parameters, or the damping is no
+// step is below the FP32 resolution of the parameters, the last kQuietSteps
+// accepted steps were quiet (each below 2^-20 of the parameters and
+// predicting a decrease below the cost's FP32 noise), or the damping is no
 // longer finite).  Every lane factors and solves in registers.
 __device__ __noinline__ int lm_trial(Shared &sh, int budget)
 {
@@ -828,7 +840,7 @@ __device__ __noinline__ int lm_trial(Shared &sh, int budget)
     int it = sh.it, go = 0;
     float d[8];
     for (;;) {
-        if (it >= budget || !(isfinite(mu) && mu > 0.0f)) break;
+        if (it >= budget || sh.quiet >= kQuietSteps || !(isfinite(mu) && mu > 0.0f)) break;
         float a[36], rd[8];
         fill_packed<8>(m, a);
 #pragma unroll
@@ -850,6 +862,7 @@ __device__ __noinline__ int lm_trial(Shared &sh, int budget)
             np = fmaf(p[k], p[k], np);
         }
         go = sqrtf(nd) > kEpsStep * (sqrtf(np) + kEpsStep) ? 1 : 0;
+        if (lane == 0) sh.small = sqrtf(nd) <= kQuietStep * (sqrtf(np) + kQuietStep);
         break;
     }
     if (go && lane < 8) {
@@ -893,6 +906,7 @@ __device__ __noinline__ void lm_update(Shared &sh)
         if (lane < kF_LM) sh.Asum[lane] = sh.sumf[lane];
         if (lane == 0) {
             sh.F = Fn;
+            sh.quiet = pred <= noise && sh.small ? sh.quiet + 1 : 0;
             const float t = rho > 0.0f && rho < 1.0f ? 2.0f * rho - 1.0f : 1.0f;
             sh.mu = mu * fmaxf(1.0f / 3.0f, 1.0f - t * t * t);
             sh.nu = 2.0f;
