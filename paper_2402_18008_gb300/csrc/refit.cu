@@ -542,7 +542,7 @@ __device__ __forceinline__ bool dlt_fp32(const float (&m)[kDF_DLT], float (&a)[4
     return true;
 }
 
-__device__ __noinline__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
+__device__ __forceinline__ bool dlt_start(const float (&m)[kDF_DLT], float (&x)[9])
 {
     float a[45], rd[9];
     return dlt_fp32(m, a, rd, x);
@@ -628,7 +628,7 @@ __device__ __forceinline__ float shift_below_min(const float (&m)[kDF_DLT], floa
     return lo;
 }
 
-__device__ __noinline__ bool dlt_refined(const DF *Mdf, const float (&m)[kDF_DLT], float *fac, DF (&v)[9])
+__device__ __forceinline__ bool dlt_refined(const DF *Mdf, const float (&m)[kDF_DLT], float *fac, DF (&v)[9])
 {
     {
         float a[45], rd[9], x[9];
@@ -755,7 +755,7 @@ __device__ __forceinline__ DF lane_pick_df(const DF (&v)[9], int lane)
 // eigenvector; writes sh.hn and, when the gauge h33 = 1 is usable, the LM
 // parameters sh.pd / sh.par.  Returns 0 (the factorisation failed), 1 (no
 // gauge) or 2.
-__device__ __noinline__ int dlt_result(Shared &sh, float s1, float s2)
+__device__ __forceinline__ int dlt_result(Shared &sh, float s1, float s2)
 {
     const int lane = threadIdx.x & 31;
     constexpr int dm[6] = {2, 2, 2, 1, 1, 0}, dw[4] = {0, 1, 1, 2};
@@ -796,7 +796,7 @@ __device__ __noinline__ int dlt_result(Shared &sh, float s1, float s2)
 // Leader warp, after the first pass: the LM state at the start (gradient,
 // J^T J sums, cost, damping mu0 = tau * max diag(J^T J)); false if the cost
 // or the damping is not finite and positive.
-__device__ __noinline__ bool lm_start(Shared &sh)
+__device__ __forceinline__ bool lm_start(Shared &sh)
 {
     const int lane = threadIdx.x & 31;
     if (lane < kF_LM) sh.Asum[lane] = sh.sumf[lane];
@@ -825,7 +825,7 @@ __device__ __noinline__ bool lm_start(Shared &sh)
 // accepted steps were quiet (each below 2^-20 of the parameters and
 // predicting a decrease below the cost's FP32 noise), or the damping is no
 // longer finite).  Every lane factors and solves in registers.
-__device__ __noinline__ int lm_trial(Shared &sh, int budget)
+__device__ __forceinline__ int lm_trial(Shared &sh, int budget)
 {
     const int lane = threadIdx.x & 31;
     float m[kF_LM], g[8], p[8];
@@ -880,7 +880,7 @@ __device__ __noinline__ int lm_trial(Shared &sh, int budget)
 }
 
 // Leader warp: gain ratio of the evaluated step; accept or reject it.
-__device__ __noinline__ void lm_update(Shared &sh)
+__device__ __forceinline__ void lm_update(Shared &sh)
 {
     const int lane = threadIdx.x & 31;
     const DF F = sh.F, sn = sh.sum[8];
@@ -931,7 +931,7 @@ __device__ __forceinline__ DF df_div(DF x, float b)
 // translation columns cancel), with unit Frobenius norm and the sign that
 // makes h33 > 0 (or, when |h33| < 1e-6 |H|, the first entry of largest
 // magnitude > 0); lane i writes entry i.
-__device__ __noinline__ void leader_store(const Shared &sh, const DF (&hn)[9], float *out)
+__device__ __forceinline__ void leader_store(const Shared &sh, const DF (&hn)[9], float *out)
 {
     const int lane = threadIdx.x & 31;
     const float s1 = sh.s1, s2 = sh.s2, a1x = sh.mu1x, a1y = sh.mu1y, a2x = sh.mu2x, a2y = sh.mu2y;
@@ -991,7 +991,7 @@ __device__ __forceinline__ int size_class(int64_t N)
     return c < kClasses ? c : kClasses - 1;
 }
 
-__device__ __noinline__ int32_t longest_first(const int64_t *__restrict__ offsets, int32_t P, int32_t b, int32_t *hist,
+__device__ __forceinline__ int32_t longest_first(const int64_t *__restrict__ offsets, int32_t P, int32_t b, int32_t *hist,
                                  int32_t *scratch)
 {
     for (int k = threadIdx.x; k < kClasses; k += kThreads) hist[k] = 0;
