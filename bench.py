@@ -341,6 +341,8 @@ def main():
             res["err"] = error_stats(H.cpu().numpy(), flags.cpu().numpy(), ms.pts, n, np.random.default_rng(1))
         if rows_on:
             ctx = {"peaks": peaks, "sms": sms, "pts_np": ms.pts, "cpu_s": args.row_cpu_seconds}
+            if args.row_set & {"ransac1", "ransac512", "adaptive"}:
+                ctx["fma"] = measure_fma(torch, _lib, sms, stream, dev)
             res.update(run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev, ctx))
     clk = clocks.summary()
     if rank != 0:
@@ -421,6 +423,23 @@ def fp32_peak_tflops(sms, mhz):
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def measure_fma(torch, _lib, sms, stream, dev):
+    """The FP32 rate measured by the library's FMA probe (aca_fma_probe: 8
+    independent FMA chains per thread, 4 blocks of 256 threads per SM), as
+    scalar FMAs and as packed f32x2 FMAs (the form the RANSAC scoring
+    issues), TFLOP/s from CUDA events over 10 launches."""
+    blocks, threads, steps = sms * 4, 256, 4096
+    sink = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    out = {"blocks": blocks, "threads": threads, "steps": steps}
+    for name, packed in (("scalar_tflops", False), ("packed_f32x2_tflops", True)):
+        f = lambda: _lib.fma_probe(sink, packed, blocks, threads, steps)
+        flops = f()
+        for _ in range(3):
+            f()
+        out[name] = flops / (time_region(torch, f, 10, stream) * 1e-3) / 1e12
+    return out
+
+
 def row_counter(row):
     """The ncu counter behind a row's roofline, from the committed capture
     (profiles/row_counters.json); marked stale when the kernel's sources
@@ -451,13 +470,18 @@ def roofline_hbm(row, bytes_per_launch, ms, ctx, kernel, note=None):
 
 
 def roofline_alu(row, flops, ms, ctx, kernel, note=None):
-    """FP32-pipe bound: peak = SMs x 128 FP32 lanes x 2 (FMA) x max SM clock."""
+    """FP32-pipe bound: peak = SMs x 128 FP32 lanes x 2 (FMA) x max SM clock,
+    with the FMA probe's measured rates beside it."""
     peak = fp32_peak_tflops(ctx["sms"], ctx["peaks"]["sm_max_mhz"])
     achieved = flops / (ms * 1e-3) / 1e12
     r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
          "peak_source": f"derived: {ctx['sms']} SMs x 128 FP32 lanes x 2 x {ctx['peaks']['sm_max_mhz']:.0f} MHz",
          "kernel": kernel, "algorithmic_flops_per_launch": flops, "flops_per_test": FLOPS_PER_TEST,
          "counter": row_counter(row)}
+    fma = ctx.get("fma")
+    if fma:
+        best = max(fma["scalar_tflops"], fma["packed_f32x2_tflops"])
+        r["peak_measured"] = {"fma_probe": fma, "tflops": best, "frac_of_measured": achieved / best}
     if note:
         r["note"] = note
     return r

@@ -333,6 +333,21 @@ aca_status ransac_aca_adaptive(const float *corr, const int64_t *offsets, const 
 aca_status aca_refit(const float *corr, const int64_t *offsets, const uint8_t *mask, int32_t P, int32_t lm_iters,
                      float *H, int32_t *n_used, float *rms, void *stream);
 
+/*
+ * FP32 FMA throughput probe (a diagnostic, not part of the method): `blocks`
+ * blocks of `threads` threads each run 8 independent FMA chains of `steps`
+ * steps, as scalar FMAs (packed = 0) or as packed f32x2 FMAs (packed != 0),
+ * and write one float per thread to `sink` (blocks * threads floats, device,
+ * caller-owned).  Timing it gives the measured FP32 rate that the FP32-pipe
+ * rooflines (Sec. 6.2's verification loop on the GPU) are stated against,
+ * beside the rate derived from the SM count and the clock.
+ * aca_fma_probe_flops returns the FLOPs of one launch (an FMA counts 2).
+ * Returns ACA_ERR_INVALID_ARG for blocks < 1, threads not a multiple of 32
+ * in 32..1024, steps not a positive multiple of 16, or a null sink.
+ */
+aca_status aca_fma_probe(int32_t packed, int32_t blocks, int32_t threads, int32_t steps, float *sink, void *stream);
+int64_t aca_fma_probe_flops(int32_t packed, int32_t blocks, int32_t threads, int32_t steps);
+
 /* Message describing the last non-OK status returned on this thread. */
 const char *aca_last_error(void);
 

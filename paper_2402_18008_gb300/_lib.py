@@ -24,7 +24,8 @@ _STATUS = {0: "ACA_OK", -1: "ACA_ERR_INVALID_ARG", -2: "ACA_ERR_CUDA", -3: "ACA_
 
 EXPORTED = ("aca_solve", "sks_solve", "aca_rect_solve", "aca_affine_solve", "aca_backward", "aca_rect_backward",
             "ransac_aca_workspace_size", "ransac_aca", "ransac_aca_noalloc", "ransac_aca_adaptive_workspace_size",
-            "ransac_aca_adaptive", "aca_sample_indices", "aca_refit", "aca_last_error", "aca_version")
+            "ransac_aca_adaptive", "aca_sample_indices", "aca_refit", "aca_fma_probe", "aca_fma_probe_flops",
+            "aca_last_error", "aca_version")
 ACA_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 
 
@@ -74,9 +75,12 @@ def load(build_if_missing: bool = True):
         L.ransac_aca_adaptive_workspace_size.restype = ctypes.c_size_t
         L.ransac_aca_adaptive.argtypes = [vp, vp, vp, i32, i64, ctypes.POINTER(RansacParams), ctypes.c_double, vp,
                                           vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.aca_fma_probe.argtypes = [i32, i32, i32, i32, vp, vp]
+        L.aca_fma_probe_flops.argtypes = [i32, i32, i32, i32]
+        L.aca_fma_probe_flops.restype = ctypes.c_int64
         for name in EXPORTED:
             if name not in ("ransac_aca_workspace_size", "ransac_aca_adaptive_workspace_size", "aca_last_error",
-                            "aca_version"):
+                            "aca_version", "aca_fma_probe_flops"):
                 getattr(L, name).restype = ctypes.c_int
         L.aca_last_error.restype = ctypes.c_char_p
         L.aca_version.restype = ctypes.c_char_p
@@ -414,3 +418,14 @@ def ransac_aca_adaptive(corr, offsets, max_hyp, total_max_hyps, params: RansacPa
                                       ctypes.byref(params), float(confidence), _ptr(best_H), _ptr(best_count),
                                       _ptr(best_hyp), _ptr(n_evaluated), _ptr(hyp_counts), _ptr(inlier_mask),
                                       _ptr(workspace), workspace.numel(), _stream(stream, corr)))
+
+
+def fma_probe(sink, packed: bool, blocks: int, threads: int, steps: int, stream=None) -> int:
+    """One launch of the FP32 FMA throughput probe (aca_fma_probe); returns its
+    FLOPs.  sink: float32 CUDA tensor of at least blocks * threads elements."""
+    _need(sink, "sink", torch.float32)
+    if sink.numel() < blocks * threads:
+        raise ValueError("fma_probe: sink holds fewer than blocks * threads floats")
+    L = _L()
+    _check(L.aca_fma_probe(int(bool(packed)), blocks, threads, steps, sink.data_ptr(), _stream(stream, sink)))
+    return int(L.aca_fma_probe_flops(int(bool(packed)), blocks, threads, steps))

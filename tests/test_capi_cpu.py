@@ -140,3 +140,13 @@ def test_refit_and_affine_reject_bad_arguments():
     assert _call("aca_affine_solve", None, None, 5, 4, 0, None)[0] == -1
     assert _call("aca_affine_solve", None, None, 4, 4, 9, None)[0] == -1
     assert _call("aca_affine_solve", None, None, 0, 0, 0, None)[0] == 0
+
+
+def test_fma_probe_rejects_bad_arguments_before_launch():
+    L = _lib.load()
+    assert L.aca_fma_probe(0, 0, 256, 4096, None, None) == -1
+    assert L.aca_fma_probe(1, 4, 100, 4096, None, None) == -1
+    assert L.aca_fma_probe(1, 4, 256, 4095, None, None) == -1
+    assert b"steps" in L.aca_last_error()
+    assert L.aca_fma_probe(1, 4, 256, 4096, None, None) == -1     # null sink
+    assert L.aca_fma_probe_flops(1, 608, 256, 4096) == 608 * 256 * 4096 * 8 * 2 * 2
