@@ -215,3 +215,18 @@ def test_refit_many_small_problems_beyond_the_ordering_limit():
     idx = np.arange(0, P, 7001)
     sel = np.concatenate([np.arange(i * k, (i + 1) * k) for i in idx])
     _gate(H[idx], corr[sel], np.arange(idx.size + 1) * k, np.ones(sel.size, bool), 200, "70000 problems, sampled")
+
+
+def test_refit_sizes_around_the_shared_copy():
+    # the refit keeps the first points of each pair in shared memory (4096 on
+    # GB300, fewer where an SM has less of it) and reads the rest from global
+    # memory on every pass: pairs just below, at and above the copy's size
+    sizes = [3839, 3840, 3841, 4095, 4096, 4097, 9001]
+    probs = [workloads.ransac_problem(n, 0.7, 1.0, seed=60 + i) for i, n in enumerate(sizes)]
+    corr = np.concatenate([q.corr for q in probs])
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    mask = np.concatenate([q.is_inlier for q in probs])
+    for iters, oracle_iters in ((0, 0), (10, 200)):
+        H, n_used, _ = _gpu_refit(corr, offsets, mask, iters)
+        ref, used = _gate(H, corr, offsets, mask, oracle_iters, f"refit {iters} LM steps, pairs around the copy size")
+        assert np.array_equal(n_used, used)
