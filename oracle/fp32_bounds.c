@@ -380,28 +380,23 @@ static void sks_chain(tape *t, const double *s, int H[9])
     const int o1x = rn(t, a.onx), o1y = rn(t, a.ony), o2x = rn(t, b.onx), o2y = rn(t, b.ony);
     const int A00 = dfsub(t, dfmul(t, aK, o1x), dfmul(t, uK, o1y));
     const int A01 = dfadd(t, dfmul(t, aK, o1y), dfmul(t, uK, o1x));
-    const int A02 = dfmul(t, bK, a.fS);
     const int A20 = dfsub(t, dfmul(t, bK, o1x), dfmul(t, vK, o1y));
     const int A21 = dfadd(t, dfmul(t, bK, o1y), dfmul(t, vK, o1x));
     const int A22 = dfmul(t, aK, a.fS);
     const int D1x = dfmul(t, dK, o1x), D1y = dfmul(t, dK, o1y);
     const int L00 = dfadd(t, dfmul(t, A00, o2x), dfmul(t, D1y, o2y));
     const int L01 = dfsub(t, dfmul(t, A01, o2x), dfmul(t, D1x, o2y));
-    const int L02 = dfmul(t, A02, o2x);
     const int L10 = dfsub(t, dfmul(t, A00, o2y), dfmul(t, D1y, o2x));
     const int L11 = dfadd(t, dfmul(t, A01, o2y), dfmul(t, D1x, o2x));
-    const int L12 = dfmul(t, A02, o2y);
-    const int G02 = dfsub(t, dfsub(t, L02, dfmul(t, L00, o1x)), dfmul(t, L01, o1y));
-    const int G12 = dfsub(t, dfsub(t, L12, dfmul(t, L10, o1x)), dfmul(t, L11, o1y));
+    /* J maps M1 to M2 (the frames' origins): its column 3 is (0, 0, J22), and
+     * the first two entries are not formed */
     const int G22 = dfsub(t, dfsub(t, A22, dfmul(t, A20, o1x)), dfmul(t, A21, o1y));
     const int j00 = rn(t, dfadd(t, L00, dfmul(t, A20, o2x))), j01 = rn(t, dfadd(t, L01, dfmul(t, A21, o2x)));
-    const int j02 = rn(t, dfadd(t, G02, dfmul(t, G22, o2x)));
     const int j10 = rn(t, dfadd(t, L10, dfmul(t, A20, o2y))), j11 = rn(t, dfadd(t, L11, dfmul(t, A21, o2y)));
-    const int j12 = rn(t, dfadd(t, G12, dfmul(t, G22, o2y)));
     const int j20 = rn(t, A20), j21 = rn(t, A21), j22 = rn(t, G22);
     const int nM1x = neg(t, x[0]), nM1y = neg(t, x[1]);
-    const int K02 = fma3(t, nM1x, j00, fma3(t, nM1y, j01, j02));
-    const int K12 = fma3(t, nM1x, j10, fma3(t, nM1y, j11, j12));
+    const int K02 = fma3(t, nM1x, j00, mul(t, nM1y, j01));
+    const int K12 = fma3(t, nM1x, j10, mul(t, nM1y, j11));
     const int K22 = fma3(t, nM1x, j20, fma3(t, nM1y, j21, j22));
     H[0] = fma3(t, x[8], j20, j00);
     H[1] = fma3(t, x[8], j21, j01);

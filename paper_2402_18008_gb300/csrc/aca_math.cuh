@@ -370,35 +370,31 @@ ACA_HD void sks_solve(const SetT<V> &s, V H[9])
     // K R1 (rows), in double-float; row 1 of K R1 is dK (-o1y, o1x, 0)
     const DF A00 = df_sub(df_prod(aK, o1x), df_prod(uK, o1y));
     const DF A01 = df_add(df_prod(aK, o1y), df_prod(uK, o1x));
-    const DF A02 = df_prod(bK, a.fS);
     const DF A20 = df_sub(df_prod(bK, o1x), df_prod(vK, o1y));
     const DF A21 = df_add(df_prod(bK, o1y), df_prod(vK, o1x));
     const DF A22 = df_prod(aK, a.fS);
     const DF D1x = df_prod(dK, o1x), D1y = df_prod(dK, o1y);
-    // R2^-1 (K R1)
+    // R2^-1 (K R1), the first two columns
     const DF L00 = df_add(df_mul(A00, o2x), df_mul(D1y, o2y));
     const DF L01 = df_sub(df_mul(A01, o2x), df_mul(D1x, o2y));
-    const DF L02 = df_mul(A02, o2x);
     const DF L10 = df_sub(df_mul(A00, o2y), df_mul(D1y, o2x));
     const DF L11 = df_add(df_mul(A01, o2y), df_mul(D1x, o2x));
-    const DF L12 = df_mul(A02, o2y);
     // fold T(-ON1) on the right (column 3 -= ON1.x col 1 + ON1.y col 2) and
-    // T(ON2) on the left (rows 1, 2 += ON2 * row 3); ON1, ON2 as value + remainder
-    const DF G02 = df_sub(df_sub(L02, df_mul(L00, o1x)), df_mul(L01, o1y));
-    const DF G12 = df_sub(df_sub(L12, df_mul(L10, o1x)), df_mul(L11, o1y));
+    // T(ON2) on the left (rows 1, 2 += ON2 * row 3); ON1, ON2 as value +
+    // remainder.  J maps M1 to M2, the origins of the two M frames, so its
+    // column 3 is (0, 0, J22): the first two entries, differences of terms
+    // that cancel exactly, are not formed.
     const DF G22 = df_sub(df_sub(A22, df_mul(A20, o1x)), df_mul(A21, o1y));
     const DF J00 = df_add(L00, df_mul(A20, o2x)), J01 = df_add(L01, df_mul(A21, o2x));
-    const DF J02 = df_add(G02, df_mul(G22, o2x));
     const DF J10 = df_add(L10, df_mul(A20, o2y)), J11 = df_add(L11, df_mul(A21, o2y));
-    const DF J12 = df_add(G12, df_mul(G22, o2y));
     // J is the homography in the M frames, rounded once per entry; then
     // H = T(M2) J T(-M1) in FP32, as for ACA
-    const V j00 = df_round(J00), j01 = df_round(J01), j02 = df_round(J02);
-    const V j10 = df_round(J10), j11 = df_round(J11), j12 = df_round(J12);
+    const V j00 = df_round(J00), j01 = df_round(J01);
+    const V j10 = df_round(J10), j11 = df_round(J11);
     const V j20 = df_round(A20), j21 = df_round(A21), j22 = df_round(G22);
     const V nM1x = vneg(s.M1x), nM1y = vneg(s.M1y);
-    const V K02 = vfma(nM1x, j00, vfma(nM1y, j01, j02));
-    const V K12 = vfma(nM1x, j10, vfma(nM1y, j11, j12));
+    const V K02 = vfma(nM1x, j00, vmul(nM1y, j01));
+    const V K12 = vfma(nM1x, j10, vmul(nM1y, j11));
     const V K22 = vfma(nM1x, j20, vfma(nM1y, j21, j22));
     H[0] = vfma(s.M2x, j20, j00);
     H[1] = vfma(s.M2x, j21, j01);
