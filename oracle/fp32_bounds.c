@@ -376,24 +376,24 @@ static void sks_chain(tape *t, const double *s, int H[9])
     const int aK = mul(t, q, A), bK = mul(t, q, B), dK = mul(t, bP3y, bm);
     const int uK = fma3(t, bP3x, bm, neg(t, mul(t, aQ3y, fma3(t, A, aP3x, mul(t, B, afS)))));
     const int vK = fma3(t, bfS, bm, neg(t, mul(t, aQ3y, fma3(t, B, aP3x, mul(t, A, afS)))));
-    /* Eq. 14 in the M frames, double-float; ON rounded once where used */
+    /* Eq. 14 in the M frames, FP32; ON rounded once where used.  J maps M1
+     * to M2 (the frames' origins): its column 3 is (0, 0, J22), and the first
+     * two entries are not formed */
     const int o1x = rn(t, a.onx), o1y = rn(t, a.ony), o2x = rn(t, b.onx), o2y = rn(t, b.ony);
-    const int A00 = dfsub(t, dfmul(t, aK, o1x), dfmul(t, uK, o1y));
-    const int A01 = dfadd(t, dfmul(t, aK, o1y), dfmul(t, uK, o1x));
-    const int A20 = dfsub(t, dfmul(t, bK, o1x), dfmul(t, vK, o1y));
-    const int A21 = dfadd(t, dfmul(t, bK, o1y), dfmul(t, vK, o1x));
-    const int A22 = dfmul(t, aK, a.fS);
-    const int D1x = dfmul(t, dK, o1x), D1y = dfmul(t, dK, o1y);
-    const int L00 = dfadd(t, dfmul(t, A00, o2x), dfmul(t, D1y, o2y));
-    const int L01 = dfsub(t, dfmul(t, A01, o2x), dfmul(t, D1x, o2y));
-    const int L10 = dfsub(t, dfmul(t, A00, o2y), dfmul(t, D1y, o2x));
-    const int L11 = dfadd(t, dfmul(t, A01, o2y), dfmul(t, D1x, o2x));
-    /* J maps M1 to M2 (the frames' origins): its column 3 is (0, 0, J22), and
-     * the first two entries are not formed */
-    const int G22 = dfsub(t, dfsub(t, A22, dfmul(t, A20, o1x)), dfmul(t, A21, o1y));
-    const int j00 = rn(t, dfadd(t, L00, dfmul(t, A20, o2x))), j01 = rn(t, dfadd(t, L01, dfmul(t, A21, o2x)));
-    const int j10 = rn(t, dfadd(t, L10, dfmul(t, A20, o2y))), j11 = rn(t, dfadd(t, L11, dfmul(t, A21, o2y)));
-    const int j20 = rn(t, A20), j21 = rn(t, A21), j22 = rn(t, G22);
+    const int A00 = fma3(t, aK, o1x, neg(t, mul(t, uK, o1y)));
+    const int A01 = fma3(t, aK, o1y, mul(t, uK, o1x));
+    const int A20 = fma3(t, bK, o1x, neg(t, mul(t, vK, o1y)));
+    const int A21 = fma3(t, bK, o1y, mul(t, vK, o1x));
+    const int A22 = mul(t, aK, a.fS);
+    const int D1x = mul(t, dK, o1x), D1y = mul(t, dK, o1y);
+    const int L00 = fma3(t, A00, o2x, mul(t, D1y, o2y));
+    const int L01 = fma3(t, A01, o2x, neg(t, mul(t, D1x, o2y)));
+    const int L10 = fma3(t, A00, o2y, neg(t, mul(t, D1y, o2x)));
+    const int L11 = fma3(t, A01, o2y, mul(t, D1x, o2x));
+    const int j22 = fma3(t, neg(t, A20), o1x, fma3(t, neg(t, A21), o1y, A22));
+    const int j00 = fma3(t, A20, o2x, L00), j01 = fma3(t, A21, o2x, L01);
+    const int j10 = fma3(t, A20, o2y, L10), j11 = fma3(t, A21, o2y, L11);
+    const int j20 = A20, j21 = A21;
     const int nM1x = neg(t, x[0]), nM1y = neg(t, x[1]);
     const int K02 = fma3(t, nM1x, j00, mul(t, nM1y, j01));
     const int K12 = fma3(t, nM1x, j10, mul(t, nM1y, j11));
