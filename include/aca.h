@@ -306,11 +306,14 @@ aca_status ransac_aca_adaptive(const float *corr, const int64_t *offsets, const 
  *      distance sqrt(2));
  *   2. the normalised DLT: h minimises the algebraic residual of the two
  *      Eq. 2 rows of every point under |h| = 1 (smallest eigenvector of the
- *      9x9 normal matrix, FP64 inverse iteration);
+ *      9x9 normal matrix: FP32 inverse iteration as the start of step 3;
+ *      refined to double-float accuracy when it is the result, lm_iters = 0);
  *   3. lm_iters trial steps of Levenberg-Marquardt on the reprojection error
  *      sum_i |pi(H x1_i) - x2_i|^2 (eight entries with h33 = 1 in the
  *      normalised frames; damping of Madsen, Nielsen & Tingleff 2004,
- *      Alg. 3.16), stopping early once a step is below FP32 resolution.
+ *      Alg. 3.16), stopping early once a step is below FP32 resolution, or
+ *      after two accepted steps that each moved the parameters by less than
+ *      2^-20 and predicted a decrease below the cost's FP32 noise.
  *      It is skipped when the normalised DLT has |h33| < 1e-3.
  *   corr     [total][4] float (x1, y1, x2, y2), the points of problem p at rows
  *            offsets[p] .. offsets[p+1]-1; 16-byte aligned (device memory).
