@@ -9,7 +9,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import ACA_NORM_FROB, ACA_NORM_H33, ACA_NORM_NONE, RansacParams
+from ._lib import ACA_NORM_NONE, RansacParams
 
 _SOLVERS = {"aca": _lib.aca_solve, "sks": _lib.sks_solve}
 
