@@ -135,6 +135,16 @@ def test_flags_match_near_degenerate_labels_and_nonfinite():
     _, fl2 = _solve(bad, 8, 8, flags=True)
     f2 = fl2.cpu().numpy()
     assert f2[2] & 8 and f2[5] & 8 and not f2[0] & 8
+    # one non-finite coordinate in each of the 16 planes, as NaN, +inf and -inf
+    m = 16 * 3
+    bad = np.ascontiguousarray(np.repeat(ms.pts[:, :1], m + 4, axis=1))
+    for j, v in enumerate((np.nan, np.inf, -np.inf)):
+        for plane in range(16):
+            bad[plane, 16 * j + plane] = v
+    for n_, ld_ in ((m + 4, m + 4), (m + 3, m + 3)):          # vector and scalar kernels
+        _, fl3 = _solve(bad, n_, ld_, flags=True)
+        f3 = fl3.cpu().numpy()
+        assert np.all(f3[:m] & 8) and not np.any(f3[m:n_] & 8)
 
 
 def test_flag_tail_bytes_untouched():
