@@ -951,6 +951,25 @@ def row_diff(torch, _lib, rect, stream, dev, ctx):
     g.replay()
     torch.cuda.synchronize()
     tdev = time_region(torch, g.replay, 10, stream) / 50
+    # the same pair at 2^24 sets (the vectorised kernels, 2.8 GB per pair,
+    # larger than L2): whether the kernels reach the HBM roofline once the
+    # batch is no longer launch-bound
+    BL = 1 << 24
+    tgtL = torch.from_numpy(np.ascontiguousarray(np.tile(rect.tgt, (1, BL // B)))).to(dev)
+    HrL = torch.empty((9, BL), dtype=torch.float32, device=dev)
+    gHL = torch.randn((9, BL), dtype=torch.float32, device=dev)
+    gTL = torch.empty((8, BL), dtype=torch.float32, device=dev)
+    gL = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(gL, stream=s):
+            for _ in range(5):
+                _lib.aca_rect_solve(tgtL, rect.rect, HrL, stream=s)
+                _lib.aca_rect_backward(tgtL, rect.rect, gHL, gTL, stream=s)
+    gL.replay()
+    torch.cuda.synchronize()
+    tdevL = time_region(torch, gL.replay, 4, stream) / 5
+    del tgtL, HrL, gHL, gTL, gL
     import oracle
     tg = np.ascontiguousarray(rect.tgt.T.astype(np.float64))
     x0, y0, w, r = (float(v) for v in rect.rect)
@@ -971,8 +990,14 @@ def row_diff(torch, _lib, rect, stream, dev, ctx):
         "ms_torch_ops_autograd_fwd_bwd": ttt, "speedup_vs_torch_ops": ttt / tfb,
         # forward 32 B in + 36 out, backward 32 + 36 in + 32 out, per set
         "roofline": roofline_hbm("diff_aca_rect_65536", 168 * B, tdev, ctx,
-                                 "rect_vec4_kernel + rect_backward_vec4_kernel",
-                                 note="11 MB per forward + backward: latency-bound at this batch"),
+                                 "rect_scalar_kernel + rect_backward_scalar_kernel",
+                                 note="11 MB per forward + backward: latency-bound at this batch (below 2^18 "
+                                      "sets the library runs one set per thread)"),
+        "large_batch": {"sets": BL, "ms_fwd_bwd_device": tdevL, "sets_per_s_device": BL / (tdevL * 1e-3),
+                        "roofline": roofline_hbm("diff_aca_rect_large", 168 * BL, tdevL, ctx,
+                                                 "rect_vec4_kernel + rect_backward_vec4_kernel",
+                                                 note="the same forward + backward pair at 2^24 sets, one graph "
+                                                      "of 5 pairs; inputs larger than L2")},
         "cpu_baseline": cpu_rate(cpu_fwd_bwd, B, ctx["cpu_s"], "sets/s",
                                  "FP64 Eq. 42 forward + analytic Jacobian oracle and its product with dL/dH, "
                                  f"{B} sets")}
