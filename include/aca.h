@@ -311,7 +311,8 @@ aca_status ransac_aca_adaptive(const float *corr, const int64_t *offsets, const 
  *   3. lm_iters trial steps of Levenberg-Marquardt on the reprojection error
  *      sum_i |pi(H x1_i) - x2_i|^2 (eight entries with h33 = 1 in the
  *      normalised frames; damping of Madsen, Nielsen & Tingleff 2004,
- *      Alg. 3.16), stopping early once a step is below FP32 resolution, or
+ *      Alg. 3.16, mu0 = 1e-6 max diag(J^T J), 1e-3 max diag after a
+ *      rejected first trial), stopping early once a step is below FP32 resolution, or
  *      after two accepted steps that each moved the parameters by less than
  *      2^-20 and predicted a decrease below the cost's FP32 noise.
  *      It is skipped when the normalised DLT has |h33| < 1e-3.

@@ -13,10 +13,15 @@ out plainly, per problem, in float64:
 2. LM on F(h) = 1/2 sum_i ||pi(H x_i) - X_i||^2 over the eight entries of the
    normalised H with h33 = 1, with the damping schedule of Madsen, Nielsen &
    Tingleff, "Methods for non-linear least squares problems" (2004), Alg. 3.16:
-   mu0 = tau max diag(J^T J); a step solves (J^T J + mu I) d = -J^T r; the gain
+   mu0 = tau max diag(J^T J) with tau = 1e-6, their value for a start believed
+   close to the minimiser (the DLT of the same points); a step solves (J^T J + mu I) d = -J^T r; the gain
    ratio rho = (F(h) - F(h + d)) / (1/2 d^T (mu d - g)) accepts (rho > 0, mu
    scaled by max(1/3, 1 - (2 rho - 1)^3), nu = 2) or rejects (mu *= nu,
-   nu *= 2) it; every trial step counts as one iteration.
+   nu *= 2) it; every trial step counts as one iteration.  When the first
+   trial is rejected the start was not close, and mu becomes their value for
+   a poorer start, 1e-3 max diag(J^T J), with nu unchanged.  A numerically
+   singular J^T J + mu I (H sends the points to infinity and J vanishes) is a
+   rejected trial; LM ends when mu is no longer finite.
 
 The target normalisation is a similarity, so F in the normalised frame is the
 pixel reprojection error times a constant: both have the same minimiser.
@@ -110,22 +115,33 @@ def _residuals(h8, x, X):
     return r, J
 
 
-def _lm(h8, x, X, iters, tau=1e-3, eps2=1e-12):
+def _lm(h8, x, X, iters, tau=1e-6, tau_poor=1e-3, eps2=1e-12):
     r, J = _residuals(h8, x, X)
     A, g, F = J.T @ J, J.T @ r, 0.5 * r @ r
     mu, nu = tau * np.max(np.diag(A)), 2.0
-    for _ in range(iters):
-        d = np.linalg.solve(A + mu * np.eye(8), -g)
-        if np.linalg.norm(d) <= eps2 * (np.linalg.norm(h8) + eps2):
+    mu_poor = tau_poor * np.max(np.diag(A))
+    for trial in range(iters):
+        if not (np.isfinite(mu) and mu > 0.0):
             break
-        hn = h8 + d
-        rn, Jn = _residuals(hn, x, X)
-        Fn = 0.5 * rn @ rn
-        rho = (F - Fn) / (0.5 * d @ (mu * d - g))
+        try:
+            d = np.linalg.solve(A + mu * np.eye(8), -g)
+        except np.linalg.LinAlgError:           # numerically singular: a rejected trial
+            d = None
+        if d is not None and np.linalg.norm(d) <= eps2 * (np.linalg.norm(h8) + eps2):
+            break
+        rho = -1.0
+        if d is not None:
+            hn = h8 + d
+            rn, Jn = _residuals(hn, x, X)
+            Fn = 0.5 * rn @ rn
+            with np.errstate(invalid="ignore"):
+                rho = (F - Fn) / (0.5 * d @ (mu * d - g))
         if rho > 0:
             h8, A, g, F = hn, Jn.T @ Jn, Jn.T @ rn, Fn
             mu *= max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
             nu = 2.0
+        elif trial == 0:
+            mu = mu_poor
         else:
             mu *= nu
             nu *= 2.0

@@ -14,7 +14,11 @@
 //   3. Levenberg-Marquardt on the reprojection error in the normalised frames
 //      (the eight entries of H with h33 = 1), with the damping schedule of
 //      Madsen, Nielsen & Tingleff, "Methods for non-linear least squares
-//      problems" (2004), Alg. 3.16; each trial step is one pass.
+//      problems" (2004), Alg. 3.16, with tau = 1e-6, the value they give
+//      for a start believed close to the minimiser; when the first trial
+//      step is rejected the start was not that close, and mu becomes their
+//      value for a poorer start, 1e-3 max diag(J^T J) (nu unchanged).  Each
+//      trial step is one pass.
 //
 // Precision and speed on GB300, where FP64 runs at 1/64 of the FP32 rate and
 // each FP64 instruction (conversions included) of a serial chain costs
@@ -66,7 +70,9 @@ constexpr int kPad = 33;              // transposition row stride (floats per va
 constexpr int kRefineMax = 16;        // refinement steps of the DLT eigenvector (lm_iters = 0), at most
 constexpr int kBisect = 12;           // bisection steps for its shift, when it needs one
 constexpr float kSlow = 0.01f;        // contraction per step above which the refinement shifts
-constexpr float kTau = 1e-3f;         // mu0 = tau * max diag(J^T J)
+constexpr float kTau = 1e-6f;         // mu0 = tau * max diag(J^T J): the value given for a start
+                                      // close to the minimiser (the DLT of the same points)
+constexpr float kTauPoor = 1e-3f;     // mu after a rejected first trial: the value for a poorer start
 constexpr float kEpsStep = 5.9604644775390625e-8f;   // 2^-24: parameters are used in FP32
 constexpr float kCostNoise = 1.52587890625e-05f;     // 2^-16: FP32 noise of the cost, relative
 constexpr int kQuietSteps = 2;        // LM stops after this many accepted quiet steps in a row
@@ -98,6 +104,7 @@ struct Shared {
     DF F;                             // ||r||^2 / 2 at pd
     DF pd[8];                         // parameters
     float d[8], mu, nu;               // step, damping
+    float mu_poor;                    // kTauPoor * max diag(J^T J) at the start
     int it;                           // trial steps taken
     int quiet;                        // consecutive accepted quiet steps (small, and below the cost's noise)
     int small;                        // the evaluated step is below kQuietStep of the parameters
@@ -810,6 +817,7 @@ __device__ __forceinline__ bool lm_start(Shared &sh)
     if (lane == 0) {
         sh.F = F;
         sh.mu = mu;
+        sh.mu_poor = kTauPoor * dmax;
         sh.nu = 2.0f;
         sh.it = 0;
         sh.quiet = 0;
@@ -848,8 +856,12 @@ __device__ __forceinline__ int lm_trial(Shared &sh, int budget)
         const bool ok = reg_cholesky<8>(a, rd, 0.0f);
         ++it;
         if (!ok) {
-            mu *= nu;
-            nu *= 2.0f;
+            if (it == 1) {
+                mu = sh.mu_poor;
+            } else {
+                mu *= nu;
+                nu *= 2.0f;
+            }
             continue;
         }
 #pragma unroll
@@ -912,8 +924,12 @@ __device__ __forceinline__ void lm_update(Shared &sh)
             sh.nu = 2.0f;
         }
     } else if (lane == 0) {
-        sh.mu = mu * nu;
-        sh.nu = nu * 2.0f;
+        if (sh.it == 1) {                           // the first trial: a poorer start
+            sh.mu = sh.mu_poor;
+        } else {
+            sh.mu = mu * nu;
+            sh.nu = nu * 2.0f;
+        }
     }
     __syncwarp();
 }

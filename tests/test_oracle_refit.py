@@ -112,6 +112,55 @@ def test_lm_optimum_matches_minpack(seed, sigma):
     assert cost[0] <= cost[1]                       # LM never worse than its DLT start
     assert cost[0] <= cost[2] * (1 + 1e-12)
 
+def _minpack(sel, h8_start):
+    opt = pytest.importorskip("scipy.optimize")
+
+    def res(h8):
+        h = np.append(h8, 1.0)
+        w = h[6] * sel[:, 0] + h[7] * sel[:, 1] + h[8]
+        return np.r_[(h[0] * sel[:, 0] + h[1] * sel[:, 1] + h[2]) / w - sel[:, 2],
+                     (h[3] * sel[:, 0] + h[4] * sel[:, 1] + h[5]) / w - sel[:, 3]]
+
+    r = opt.least_squares(res, h8_start, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, x_scale="jac")
+    return oracle.normalize_frob(np.append(r.x, 1.0))[0]
+
+
+@pytest.mark.parametrize("seed,n,eps", [(2004, 10, 0.6), (2007, 6, 0.5)])
+def test_lm_from_a_poor_start_rejects_its_first_trial_and_reaches_minpacks_optimum(seed, n, eps):
+    # every point of a small contaminated set: the DLT is far from the
+    # minimiser, the nearly undamped first trial (mu0 = 1e-6 max diag) is
+    # rejected, and the damping restarts at the poor-start value
+    from oracle import inlier_refit as ir
+    rp = workloads.ransac_problem(n, eps, 1.0, seed=seed)
+    off, m = np.array([0, n]), np.ones(n, bool)
+    Hd, _ = oracle.refit_dlt(rp.corr, off, m)
+    sel = rp.corr.astype(np.float64)
+    T1, T2, x, X = ir._frame(sel)
+    Hn = T2 @ Hd[0].reshape(3, 3) @ np.linalg.inv(T1)
+    start = (Hn / Hn[2, 2]).reshape(9)[:8]
+    assert np.array_equal(ir._lm(start, x, X, 1), start)
+    H, _ = oracle.refit(rp.corr, off, m)
+    Hm = _minpack(sel, (Hd[0] / Hd[0, 8])[:8])
+    cost = oracle.reprojection_cost(np.stack([H[0], Hm]), np.r_[rp.corr, rp.corr], np.array([0, n, 2 * n]),
+                                    np.r_[m, m])
+    assert cost[0] <= cost[1] * (1 + 1e-9)
+    assert np.max(np.abs(H[0] - Hm)) < 1e-5
+
+
+def test_lm_on_a_degenerate_set_ends_without_error_and_never_above_its_start():
+    # 8 points, half of them outliers: LM walks towards an H that sends the
+    # points to infinity, where J^T J vanishes and J^T J + mu I becomes
+    # numerically singular; those trials are rejected, mu grows until it is
+    # no longer finite, and the result is finite
+    rp = workloads.ransac_problem(8, 0.5, 1.0, seed=2005)
+    off, m = np.array([0, 8]), np.ones(8, bool)
+    H, used = oracle.refit(rp.corr, off, m)
+    Hd, _ = oracle.refit_dlt(rp.corr, off, m)
+    assert used[0] == 8 and np.all(np.isfinite(H))
+    c = oracle.reprojection_cost(np.stack([H[0], Hd[0]]), np.r_[rp.corr, rp.corr], np.array([0, 8, 16]), np.r_[m, m])
+    assert c[0] <= c[1]
+
+
 def test_lm_optimum_is_stationary_under_central_differences():
     rp, off = _problem(300, 0.8, 1.5, seed=19)
     H, _ = oracle.refit(rp.corr, off, rp.is_inlier)
