@@ -60,6 +60,19 @@
 
 namespace aca {
 
+// Done counters.  One thread of a block adds to the counter after a
+// __syncthreads, with acquire-release semantics at GPU scope: the release
+// half publishes the block's stores (ordered before the add by the barrier),
+// the acquire half makes the stores that the other blocks published before
+// their adds visible to the block after the next __syncthreads.  The same
+// pattern as a grid-wide barrier, with the fences folded into the add.
+__device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t *p, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // Degenerate-sample rule: on either side one of the triples (M,N,P),
 // (M,Q,P), (M,N,Q), (N,P,Q) has |cross(a,b)| <= 1e-3 |a||b| for its edge
 // vectors a, b (sine of the angle at most 1e-3).
@@ -873,12 +886,11 @@ __global__ void __launch_bounds__(512) ransac_score_kernel(const float4 *__restr
             // the last slice of a chunk publishes the chunk's bound
             const int64_t cid = info.cid;
             const int32_t S = info.S, kcap = info.k;
-            __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0) s_last = atomicAdd(&aw.chunk_done[cid], 1) == S - 1;
+            if (threadIdx.x == 0)
+                s_last = (int32_t)atomic_add_acq_rel(reinterpret_cast<uint32_t *>(&aw.chunk_done[cid]), 1u) == S - 1;
             __syncthreads();
             if (s_last && wid == 0) {
-                __threadfence();
                 int32_t bc = -2, bj = 0x7fffffff;
                 for (int t = lane; t < nh; t += 32) {
                     const int32_t c = __ldcg(&ws.counts[hbase + h0 + t]);
@@ -1006,7 +1018,7 @@ __global__ void __launch_bounds__(256) ransac_finish_kernel(const float4 *__rest
 // stores its partial counts with plain stores into the slot of its slice,
 // part[s][hyp], so that no count needs clearing and no atomic adds are made;
 // the slice-0 item also stores each hypothesis's H.  A block that has
-// finished all of its items fences and counts itself done; the last one sums
+// finished all of its items counts itself done (an acquire-release add); the last one sums
 // the slots of every hypothesis, takes each problem's argmax (ties to the
 // lowest index), writes the mask and the outputs from the winner's stored H
 // (the bits its scoring used), and sets the done counter back to zero for
@@ -1197,13 +1209,11 @@ __global__ void __launch_bounds__(512) ransac_fused_kernel(const float4 *__restr
     }
 
     // the last block to finish takes the argmax of every problem
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(ws.done, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) s_last = atomic_add_acq_rel(ws.done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last)
         return;
-    __threadfence();
     const bool overflow = s_overflow != 0;
     for (int32_t p = 0; p < P; ++p) {
         const int64_t base = s_off[p];
