@@ -528,7 +528,7 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
     if rect is not None:
         out.update(row_diff(torch, _lib, rect, stream, dev, ctx))
     if "latency" in args.row_set:
-        out.update(row_latency(torch, _lib, pts, H, n, stream))
+        out.update(row_latency(torch, _lib, pts, H, n, stream, ctx))
     return out
 
 
@@ -537,13 +537,19 @@ def run_rows(torch, _lib, api, pts, H, flags, n, rp, rb, rect, args, stream, dev
 PAPER_TABLE8_ACA_US = {1: 3.11, 10: 3.16, 100: 3.19, 1000: 3.20, 10000: 5.26, 100000: 29.3, 1000000: 245.0}
 
 
-def row_latency(torch, _lib, pts, H, n_total, stream):
+def row_latency(torch, _lib, pts, H, n_total, stream, ctx):
     """aca_solve on the first m sets of the resident batch for the paper's
     sample numbers.  Device time per call: 100 calls captured in one CUDA
     graph, the graph replayed, CUDA events around the replays (host launch
     cost excluded, as in a kernel-time measurement); plus the host-side cost
-    of one eager call through the Python binding."""
-    res = {}
+    of one eager call through the Python binding.  Per size, the fraction of
+    HBM bandwidth the call's 100 B per set reach (small calls are bound by
+    launch latency, not bandwidth); the row's roofline is that of the
+    largest size; the oracle's time per call on the host cores is timed at
+    every size up to 1e5 sets."""
+    import oracle
+    res = {"sizes": {}}
+    peak = ctx["peaks"]["hbm_gbs"]
     # Table 8's sample numbers plus the 1K-20K range of the paper's Fig. 8
     # (where its per-H time levels off, near its GPU's core count), extended
     # to 40K for GB300's 19456 FP32 lanes
@@ -568,8 +574,36 @@ def row_latency(torch, _lib, pts, H, n_total, stream):
         eager = time_region(torch, f, 200, stream)
         prepared = _lib.prepare_aca_solve(pts, H, None, n=m)
         prep = time_region(torch, prepared, 200, stream)
-        res[str(m)] = {"us": t * 1e3, "ns_per_set": t * 1e6 / m, "eager_call_us": eager * 1e3,
-                       "prepared_call_us": prep * 1e3, "paper_rtx3090_fp64_us": PAPER_TABLE8_ACA_US.get(m)}
+        res["sizes"][str(m)] = {"us": t * 1e3, "ns_per_set": t * 1e6 / m, "eager_call_us": eager * 1e3,
+                                "prepared_call_us": prep * 1e3,
+                                "hbm_frac": BYTES_PER_SET * m / (t * 1e-3) / 1e9 / peak,
+                                "paper_rtx3090_fp64_us": PAPER_TABLE8_ACA_US.get(m)}
+        last = (m, t)
+    m, t = last
+    res["unit"] = "us per call"
+    res["value"] = t * 1e3
+    res["value_at_sets"] = m
+    kernel = "solve_scalar_kernel<ACA>" if m < (1 << 18) else "solve_ring_kernel<ACA, NONE, no flags>"
+    res["roofline"] = roofline_hbm("aca_latency_sweep", BYTES_PER_SET * m, t, ctx, kernel,
+                                   note=f"the largest size of the sweep ({m} sets); below 2^18 sets the library "
+                                        "runs solve_scalar_kernel and a call is bound by launch latency "
+                                        "(hbm_frac per size shows it); the counter is that kernel's capture")
+    # the oracle's time per call, per size: about cpu_s in all
+    cpu_sizes = [s for s in res["sizes"] if int(s) <= 100000]
+    mmax = max(int(s) for s in cpu_sizes)
+    aos = oracle.sets_aos(ctx["pts_np"][:, :mmax])
+    buf = np.empty((mmax, 9))
+    per_size = {}
+    for s in cpu_sizes:
+        k = int(s)
+        r = cpu_rate(lambda: oracle.lib().oracle_aca(aos.ctypes.data_as(oracle._d), buf.ctypes.data_as(oracle._d), k),
+                     1, ctx["cpu_s"] / len(cpu_sizes), "calls/s", f"FP64 ACA oracle over {k} sets")
+        per_size[s] = 1e6 / r["value"]
+    top = str(max(int(s) for s in cpu_sizes))
+    res["cpu_baseline"] = {"value": per_size[top], "unit": "us per call", "at_sets": int(top),
+                           "us_per_call_by_size": per_size, "cores": oracle.num_threads(), "kind": "oracle",
+                           "sample": f"FP64 ACA oracle (Eq. 20-29) on the first m sets, m in the sweep up to "
+                                     f"{top}; about {ctx['cpu_s'] / len(cpu_sizes):.2f} s per size"}
     return {"aca_latency_sweep": res}
 
 
