@@ -15,6 +15,7 @@
 // four adjacent sets per thread with float4 SoA loads, like the solvers.
 #include "aca_math.cuh"
 #include "common.cuh"
+#include "pdl.cuh"  // launched as programmatic dependents, as the forward kernels (solve.cu)
 
 namespace aca {
 
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(256) aca_backward_vec4_kernel(const float *__r
                                                                  const float *__restrict__ gH,
                                                                  float *__restrict__ gT, int64_t n, int64_t ld)
 {
+    grid_dependency_wait();
     const int64_t nq = (n + 3) >> 2, ldq = ld >> 2;
     const float4 *in = reinterpret_cast<const float4 *>(pts);
     const float4 *gin = reinterpret_cast<const float4 *>(gH);
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(256) aca_backward_scalar_kernel(const float *_
                                                                    const float *__restrict__ gH,
                                                                    float *__restrict__ gT, int64_t n, int64_t ld)
 {
+    grid_dependency_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         Set s;
         float *sv = &s.M1x;
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(256) rect_backward_vec4_kernel(const float *__
                                                                   const float *__restrict__ gH,
                                                                   float *__restrict__ gT, int64_t n, int64_t ld)
 {
+    grid_dependency_wait();
     const int64_t nq = (n + 3) >> 2, ldq = ld >> 2;
     const float4 *in = reinterpret_cast<const float4 *>(tgt);
     const float4 *gin = reinterpret_cast<const float4 *>(gH);
@@ -238,6 +242,7 @@ __global__ void __launch_bounds__(256) rect_backward_scalar_kernel(const float *
                                                                     const float *__restrict__ gH,
                                                                     float *__restrict__ gT, int64_t n, int64_t ld)
 {
+    grid_dependency_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float t[8], G[9], g[8];
 #pragma unroll
@@ -270,10 +275,12 @@ extern "C" aca_status aca_backward(const float *pts, const float *grad_H, float 
     const int threads = 256;
     if (n >= kSmallBatch && ld % 4 == 0 && aligned16(pts) && aligned16(grad_H) && aligned16(grad_tgt)) {
         const int grid = resident_grid(aca_backward_vec4_kernel, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
-        aca_backward_vec4_kernel<<<grid, threads, 0, st>>>(pts, grad_H, grad_tgt, n, ld);
+        launch_after_previous(aca_backward_vec4_kernel, dim3(grid), dim3(threads), 0, st, pts, grad_H, grad_tgt, n,
+                              ld);
     } else {
         const int grid = resident_grid(aca_backward_scalar_kernel, threads, 0, (n + threads - 1) / threads);
-        aca_backward_scalar_kernel<<<grid, threads, 0, st>>>(pts, grad_H, grad_tgt, n, ld);
+        launch_after_previous(aca_backward_scalar_kernel, dim3(grid), dim3(threads), 0, st, pts, grad_H, grad_tgt, n,
+                              ld);
     }
     return check_launch("aca_backward");
 }
@@ -294,10 +301,12 @@ extern "C" aca_status aca_rect_backward(const float *tgt, float x0, float y0, fl
     const int threads = 256;
     if (n >= kSmallBatch && ld % 4 == 0 && aligned16(tgt) && aligned16(grad_H) && aligned16(grad_tgt)) {
         const int grid = resident_grid(rect_backward_vec4_kernel, threads, 0, ((n + 3) / 4 + threads - 1) / threads);
-        rect_backward_vec4_kernel<<<grid, threads, 0, st>>>(tgt, R, grad_H, grad_tgt, n, ld);
+        launch_after_previous(rect_backward_vec4_kernel, dim3(grid), dim3(threads), 0, st, tgt, R, grad_H,
+                              grad_tgt, n, ld);
     } else {
         const int grid = resident_grid(rect_backward_scalar_kernel, threads, 0, (n + threads - 1) / threads);
-        rect_backward_scalar_kernel<<<grid, threads, 0, st>>>(tgt, R, grad_H, grad_tgt, n, ld);
+        launch_after_previous(rect_backward_scalar_kernel, dim3(grid), dim3(threads), 0, st, tgt, R, grad_H,
+                              grad_tgt, n, ld);
     }
     return check_launch("aca_rect_backward");
 }
