@@ -107,6 +107,12 @@ def lib():
             L.oracle_fp32_rule_bound.restype = ctypes.c_double
             L.oracle_score_bound_E.argtypes = [_d, _f, ctypes.c_int64, ctypes.c_double, _d, _d]
             L.oracle_score_bound_E.restype = None
+            L.oracle_fp32_chain_corner.argtypes = [ctypes.c_int, _d, _d, _d, _d]
+            L.oracle_fp32_chain_corner.restype = ctypes.c_double
+            L.oracle_score_bound_E_fixed.argtypes = [_d, _f, ctypes.c_int64, ctypes.c_double, _d, _d]
+            L.oracle_score_bound_E_fixed.restype = None
+            L.oracle_score_corner.argtypes = [_d, _f, ctypes.c_double, _d, _d, _d]
+            L.oracle_score_corner.restype = None
             _lib = L
     return _lib
 
@@ -397,3 +403,44 @@ def score_bound_E(s16, corr, thr: float):
     B = np.empty(c.shape[0])
     lib().oracle_score_bound_E(_ptr(s, _d), _ptr(c, _f), c.shape[0], float(thr), _ptr(E, _d), _ptr(B, _d))
     return E, B
+
+
+def fp32_chain_corner(solver: str, s16, g9):
+    """The worst corner of a solver's rounding events, re-evaluated (a pin of
+    the bound's reverse sweep; fp32_bounds.c oracle_fp32_chain_corner).  For
+    F = sum g_i H_i of the "aca" or "sks" chain at the set s16: returns
+    (b1, dev, bound), the first-order bound on |fl(F) - F|, F re-run with every
+    event at the sign of its weight times its bound, minus the exact F; and
+    (third) the whole bound, with the allowance for products of events."""
+    s = np.ascontiguousarray(np.asarray(s16, dtype=np.float64).ravel())
+    g = np.ascontiguousarray(np.asarray(g9, dtype=np.float64).ravel())
+    dev = np.zeros(1)
+    b1 = np.zeros(1)
+    b = lib().oracle_fp32_chain_corner({"aca": 0, "sks": 1}[solver], _ptr(s, _d), _ptr(g, _d), _ptr(dev, _d),
+                                       _ptr(b1, _d))
+    return float(b1[0]), float(dev[0]), float(b)
+
+
+def score_bound_E_fixed(H9, corr, thr: float):
+    """The inlier test at an exact H (nine values, no solve events): per
+    point the exact E and the bound of the test's own rounding events.
+    Returns (E, B), each (N,)."""
+    h = np.ascontiguousarray(np.asarray(H9, dtype=np.float64).ravel())
+    c = np.ascontiguousarray(corr, dtype=np.float32)
+    E = np.empty(c.shape[0])
+    B = np.empty(c.shape[0])
+    lib().oracle_score_bound_E_fixed(_ptr(h, _d), _ptr(c, _f), c.shape[0], float(thr), _ptr(E, _d), _ptr(B, _d))
+    return E, B
+
+
+def score_corner(s16, c4, thr: float):
+    """The inlier test at one point c4 under the hypothesis of the minimal set
+    s16, with the solve's rounding events and then the test's placed at the
+    signs of their first-order weights.  Returns (B1, dev, E): the
+    first-order bound of e, the re-evaluated e minus E, and the exact E."""
+    s = np.ascontiguousarray(np.asarray(s16, dtype=np.float64).ravel())
+    c = np.ascontiguousarray(np.asarray(c4, dtype=np.float32).ravel())
+    out = np.zeros(3)
+    lib().oracle_score_corner(_ptr(s, _d), _ptr(c, _f), float(thr), _ptr(out[0:], _d), _ptr(out[1:], _d),
+                              _ptr(out[2:], _d))
+    return float(out[0]), float(out[1]), float(out[2])

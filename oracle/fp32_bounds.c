@@ -35,8 +35,13 @@
  *       few u m with m the magnitude accumulated within the double-float
  *       chain, are added with one or two roundings)
  *   rounding a double-float to FP32                    C = |v|
- * Each output gets a token event of 64 u |v| for the neglected products of
- * first-order terms; where a first-order term vanishes (the squared
+ * Each output gets a token event of 64 u |v|.  The products of two or more
+ * events, which the first-order sum neglects, get an allowance of
+ * n u / (1 - n u) times the same sum taken over the absolute values of the
+ * partial derivatives along every path (n = the number of events on the
+ * tape): a product of events is at most u times the absolute contribution
+ * of one of them along its path, as in the gamma_n = n u / (1 - n u) of
+ * Higham's Lemma 3.1.  Where a first-order term vanishes (the squared
  * residuals of the inlier test at a point mapped exactly), the squares of the
  * first-order bounds of the squared quantities are added explicitly.
  *
@@ -49,14 +54,18 @@
  * differences, the similarity images P3, Q3 as compensated dot and cross
  * products, each side scaled by a power of two, the division-free form of
  * Eq. 11-13 over their common denominator, the composition of
- * Eq. 14 in double-float rounded once per entry and the translation back in
- * FP32; the inlier test in its threshold-folded form.  A bound that fails
+ * Eq. 14 in the M frames in FP32 (the local map's zero entries not formed)
+ * and the translation back in FP32; the inlier test in its threshold-folded
+ * form.  A bound that fails
  * to cover the library's FP32 result therefore means that either the
  * library or its stated evaluation order is wrong.
  *
  * Pinned by tests/test_oracle_fp32_bounds.py: every rule against exact
- * rational arithmetic on random and cancellation-heavy FP32 operands, and
- * the whole chains against an FP32 host evaluation of the same orders.
+ * rational arithmetic on random and cancellation-heavy FP32 operands, the
+ * whole chains against an FP32 host evaluation of the same orders, and the
+ * reverse sweep against the chains re-run at their worst rounding corner
+ * (tape.pert); the inlier test also against every corner of its own
+ * rounding events, enumerated.
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,6 +79,7 @@
  * SKS 184 and the inlier test about 40; push() stops the process rather than
  * write past the end. */
 #define TAPE_MAX 320
+static const double U = 0x1p-24;
 typedef struct {
     double v, m, C;
     int p[4];
@@ -79,15 +89,24 @@ typedef struct {
 typedef struct {
     node n[TAPE_MAX];
     int len;
+    /* nullable: node k's value becomes v + pert[k] u C as it is pushed, so
+     * a chain re-run with pert set evaluates exactly (in FP64) with every
+     * rounding event placed at pert[k] times its bound (the pins of the
+     * sweep below) */
+    const double *pert;
 } tape;
+static void tape_init(tape *t, const double *pert)
+{
+    t->len = 0;
+    t->pert = pert;
+}
 
-static const double U = 0x1p-24;
 
 static int push(tape *t, double v, double m, double C)
 {
     if (t->len >= TAPE_MAX) abort();
     node *q = &t->n[t->len];
-    q->v = v;
+    q->v = t->pert ? v + t->pert[t->len] * U * C : v;
     q->m = m;
     q->C = C;
     q->np = 0;
@@ -267,6 +286,36 @@ static void sweep(const tape *t, const int *out, const double *g, int nout, doub
     }
 }
 
+/* The same sweep over absolute weights: adj[k] = the sum over the paths
+ * from node k to the outputs of |g| times the absolute product of the
+ * partial derivatives along the path. */
+static void sweep_abs(const tape *t, const int *out, const double *g, int nout, double *adj)
+{
+    memset(adj, 0, sizeof(double) * (size_t)t->len);
+    for (int j = 0; j < nout; ++j) adj[out[j]] += fabs(g[j]);
+    for (int k = t->len - 1; k >= 0; --k) {
+        const double a = adj[k];
+        if (a == 0.0) continue;
+        const node *q = &t->n[k];
+        for (int i = 0; i < q->np; ++i) adj[q->p[i]] += a * fabs(q->w[i]);
+    }
+}
+
+static int n_events(const tape *t)
+{
+    int n = 0;
+    for (int k = 0; k < t->len; ++k) n += t->n[k].C > 0;
+    return n;
+}
+
+/* allowance for the products of events among n events, given R = the
+ * first-order sum over absolute paths */
+static double second_order(int n, double R)
+{
+    const double nu = n * U;
+    return nu / (1.0 - nu) * R;
+}
+
 /* u * sum_k |adj[k]| C_k: the first-order bound on |fl(F) - F| */
 static double event_sum(const tape *t, const double *adj)
 {
@@ -422,16 +471,23 @@ static double chain_bounds(const tape *t, const int H[9], double *Hv, double *He
         n2 += h[i] * h[i];
     }
     const double n = sqrt(n2);
+    const int nev = n_events(t);
     double beta = 0;
     for (int i = 0; i < 9; ++i) {
         double g[9];
         const double one = 1.0;
-        sweep(t, &H[i], &one, 1, adj);
-        if (He) He[i] = event_sum(t, adj);
+        if (He) {
+            sweep(t, &H[i], &one, 1, adj);
+            He[i] = event_sum(t, adj);
+            sweep_abs(t, &H[i], &one, 1, adj);
+            He[i] += second_order(nev, event_sum(t, adj));
+        }
         if (Hv) Hv[i] = h[i];
         for (int k = 0; k < 9; ++k) g[k] = ((k == i ? 1.0 : 0.0) - h[i] * h[k] / n2) / n;
         sweep(t, H, g, 9, adj);
-        const double b = event_sum(t, adj);
+        double b = event_sum(t, adj);
+        sweep_abs(t, H, g, 9, adj);
+        b += second_order(nev, event_sum(t, adj));
         beta = b > beta ? b : beta;
     }
     return beta;
@@ -447,7 +503,7 @@ void oracle_aca_fp32_bound(const double *pts, double *beta, double *Hv, double *
 #pragma omp for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             int H[9];
-            t->len = 0;
+            tape_init(t, NULL);
             aca_chain(t, pts + 16 * i, H);
             beta[i] = chain_bounds(t, H, Hv ? Hv + 9 * i : NULL, He ? He + 9 * i : NULL);
         }
@@ -463,7 +519,7 @@ void oracle_sks_fp32_bound(const double *pts, double *beta, double *Hv, double *
 #pragma omp for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             int H[9];
-            t->len = 0;
+            tape_init(t, NULL);
             sks_chain(t, pts + 16 * i, H);
             beta[i] = chain_bounds(t, H, Hv ? Hv + 9 * i : NULL, He ? He + 9 * i : NULL);
         }
@@ -493,12 +549,13 @@ typedef struct {
     int nev;          /* rounding events of the solve */
     int *ev;          /* their tape indices */
     double *J;        /* [9][nev]: dH_k / d(event node) */
+    double Rabs[9];   /* per entry, the solve's first-order sum over absolute paths */
 } hyp_model;
 
 static void hyp_model_init(hyp_model *h, const double *s16)
 {
     h->t = (tape *)malloc(sizeof(tape));
-    h->t->len = 0;
+    tape_init(h->t, NULL);
     aca_chain(h->t, s16, h->H);
     tape *t = h->t;
     h->ev = (int *)malloc(sizeof(int) * (size_t)t->len);
@@ -511,6 +568,8 @@ static void hyp_model_init(hyp_model *h, const double *s16)
         const double one = 1.0;
         sweep(t, &h->H[i], &one, 1, adj);
         for (int j = 0; j < h->nev; ++j) h->J[i * h->nev + j] = adj[h->ev[j]];
+        sweep_abs(t, &h->H[i], &one, 1, adj);
+        h->Rabs[i] = event_sum(t, adj);
     }
 }
 
@@ -535,15 +594,14 @@ typedef struct {
     double crude;     /* upper bound of the exact B (per-entry bounds of H) */
     double own[4];    /* u sum |adj| C over the test's own events: e, du, dv, w' */
     double g[4][9];   /* d(e, du, dv, w') / dH_k */
+    double s2[4];     /* allowance for the products of events, solve included */
 } test_parts;
 
-static void test_parts_of(const hyp_model *h, const double *Eh, double thr, const float *c, test_parts *o)
+/* The test's tape: inputs the nine entries Hval of H (nodes Hn) and the
+ * point; tgt = (e, du, dv, w') */
+static void test_chain(tape *t, const double *Hval, double thr, const float *c, int Hn[9], int tgt[4])
 {
-    tape tt;
-    tape *t = &tt;
-    t->len = 0;
-    int Hn[9];
-    for (int k = 0; k < 9; ++k) Hn[k] = in(t, h->t->n[h->H[k]].v);
+    for (int k = 0; k < 9; ++k) Hn[k] = in(t, Hval[k]);
     const int x = in(t, c[0]), y = in(t, c[1]), X = in(t, c[2]), Y = in(t, c[3]), T = in(t, thr);
     const int rt = dv(t, in(t, 1.0), T);
     const int Xs = mul(t, X, rt), Ys = mul(t, Y, rt);
@@ -552,9 +610,24 @@ static void test_parts_of(const hyp_model *h, const double *Eh, double thr, cons
     const int nv = fma3(t, neg(t, Hn[3]), x, fma3(t, neg(t, Hn[4]), y, neg(t, Hn[5])));
     const int du = fma3(t, Xs, w, nu), dvv = fma3(t, Ys, w, nv);
     const int e = final_(t, fma3(t, du, du, fma3(t, dvv, dvv, mul(t, w, neg(t, w)))));
-    o->E = V(e);
-    const int tgt[4] = {e, du, dvv, w};
+    tgt[0] = e;
+    tgt[1] = du;
+    tgt[2] = dvv;
+    tgt[3] = w;
+}
+
+static void test_parts_of(const hyp_model *h, const double *Eh, double thr, const float *c, test_parts *o)
+{
+    tape tt;
+    tape *t = &tt;
+    tape_init(t, NULL);
+    int Hn[9], tgt[4];
+    double Hval[9];
+    for (int k = 0; k < 9; ++k) Hval[k] = h->t->n[h->H[k]].v;
+    test_chain(t, Hval, thr, c, Hn, tgt);
+    o->E = V(tgt[0]);
     double adj[TAPE_MAX], cr[4];
+    const int nev = h->nev + n_events(t);
     for (int q = 0; q < 4; ++q) {
         const double one = 1.0;
         sweep(t, &tgt[q], &one, 1, adj);
@@ -564,6 +637,11 @@ static void test_parts_of(const hyp_model *h, const double *Eh, double thr, cons
             o->g[q][k] = adj[Hn[k]];
             cr[q] += fabs(adj[Hn[k]]) * Eh[k];
         }
+        sweep_abs(t, &tgt[q], &one, 1, adj);
+        double R = event_sum(t, adj);
+        for (int k = 0; k < 9; ++k) R += adj[Hn[k]] * h->Rabs[k];
+        o->s2[q] = second_order(nev, R);
+        cr[q] += o->s2[q];
     }
     o->crude = cr[0] + cr[1] * cr[1] + cr[2] * cr[2] + cr[3] * cr[3];
 }
@@ -579,7 +657,7 @@ static double test_exact_bound(const hyp_model *h, const test_parts *o)
             for (int k = 0; k < 9; ++k) d += o->g[q][k] * h->J[k * h->nev + j];
             s += fabs(d) * h->t->n[h->ev[j]].C;
         }
-        b[q] = o->own[q] + U * s;
+        b[q] = o->own[q] + U * s + o->s2[q];
     }
     return b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
 }
@@ -717,7 +795,7 @@ double oracle_fp32_rule_bound(int op, const double *a, double *v)
 {
     tape tt;
     tape *t = &tt;
-    t->len = 0;
+    tape_init(t, NULL);
     int x[8];
     for (int k = 0; k < 8; ++k) x[k] = in(t, a[k]);
     int r;
@@ -744,5 +822,110 @@ void oracle_score_bound_E(const double *s16, const float *corr, int64_t N, doubl
     hyp_model h;
     hyp_model_init(&h, s16);
     for (int64_t i = 0; i < N; ++i) B[i] = test_bound(&h, thr, corr + 4 * i, &E[i]);
+    hyp_model_free(&h);
+}
+
+/* ------------------------------------------------------------------ */
+/* Hooks for the pins of the sweep: each chain re-run with its rounding */
+/* events placed at the corner the bound says is the worst (tests only).*/
+/* ------------------------------------------------------------------ */
+static double sgn(double a) { return a > 0 ? 1.0 : a < 0 ? -1.0 : 0.0; }
+
+/* F = sum_i g_i H_i for the ACA (solver 0) or SKS (solver 1) chain at the
+ * set s16.  *b1 = the first-order bound u sum |dF/d(event)| C; *dev = F
+ * re-evaluated with every event at sign(dF/d(event)) times its bound,
+ * minus F of the exact chain (to first order *dev equals *b1).  Returns
+ * the whole bound: *b1 plus the allowance for products of events. */
+double oracle_fp32_chain_corner(int solver, const double *s16, const double *g9, double *dev, double *b1)
+{
+    tape *t = (tape *)malloc(sizeof(tape)), *tp = (tape *)malloc(sizeof(tape));
+    double *adj = (double *)malloc(sizeof(double) * TAPE_MAX);
+    double *pert = (double *)calloc(TAPE_MAX, sizeof(double));
+    int H[9], Hp[9];
+    tape_init(t, NULL);
+    if (solver) sks_chain(t, s16, H); else aca_chain(t, s16, H);
+    sweep(t, H, g9, 9, adj);
+    *b1 = event_sum(t, adj);
+    for (int k = 0; k < t->len; ++k) pert[k] = sgn(adj[k]);
+    sweep_abs(t, H, g9, 9, adj);
+    const double b = *b1 + second_order(n_events(t), event_sum(t, adj));
+    tape_init(tp, pert);
+    if (solver) sks_chain(tp, s16, Hp); else aca_chain(tp, s16, Hp);
+    double F = 0, Fp = 0;
+    for (int i = 0; i < 9; ++i) {
+        F += g9[i] * t->n[H[i]].v;
+        Fp += g9[i] * tp->n[Hp[i]].v;
+    }
+    *dev = Fp - F;
+    free(pert);
+    free(adj);
+    free(tp);
+    free(t);
+    return b;
+}
+
+/* The inlier test at an exact FP32 H (the nine values H9, no solve
+ * events): per point the exact E and the bound of the test's own events,
+ * completed with the squares of the bounds of du, dv, w' as in the scorer. */
+void oracle_score_bound_E_fixed(const double *H9, const float *corr, int64_t N, double thr, double *E, double *B)
+{
+    tape *t = (tape *)malloc(sizeof(tape));
+    double adj[TAPE_MAX];
+    for (int64_t i = 0; i < N; ++i) {
+        int Hn[9], tgt[4];
+        tape_init(t, NULL);
+        test_chain(t, H9, thr, corr + 4 * i, Hn, tgt);
+        E[i] = t->n[tgt[0]].v;
+        double b[4];
+        const int nev = n_events(t);
+        for (int q = 0; q < 4; ++q) {
+            const double one = 1.0;
+            sweep(t, &tgt[q], &one, 1, adj);
+            b[q] = event_sum(t, adj);
+            sweep_abs(t, &tgt[q], &one, 1, adj);
+            b[q] += second_order(nev, event_sum(t, adj));
+        }
+        B[i] = b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
+    }
+    free(t);
+}
+
+/* The inlier test at point c under the hypothesis of the minimal set s16,
+ * solve included.  *B1 = the first-order bound of e (the test's own events
+ * plus the solve's, through dH/d(event)); *dev = e re-evaluated with the
+ * solve's events and then the test's at the signs of their first-order
+ * weights, minus the exact E (*E). */
+void oracle_score_corner(const double *s16, const float *c, double thr, double *B1, double *dev, double *E)
+{
+    hyp_model h;
+    hyp_model_init(&h, s16);
+    tape *tt = (tape *)malloc(sizeof(tape)), *tp = (tape *)malloc(sizeof(tape));
+    double *adj_t = (double *)malloc(sizeof(double) * TAPE_MAX), *adj_s = (double *)malloc(sizeof(double) * TAPE_MAX);
+    double *pert_t = (double *)calloc(TAPE_MAX, sizeof(double)), *pert_s = (double *)calloc(TAPE_MAX, sizeof(double));
+    int Hn[9], tgt[4], Hp[9];
+    double Hval[9], g[9];
+    for (int k = 0; k < 9; ++k) Hval[k] = h.t->n[h.H[k]].v;
+    tape_init(tt, NULL);
+    test_chain(tt, Hval, thr, c, Hn, tgt);
+    *E = tt->n[tgt[0]].v;
+    const double one = 1.0;
+    sweep(tt, &tgt[0], &one, 1, adj_t);
+    for (int k = 0; k < 9; ++k) g[k] = adj_t[Hn[k]];
+    sweep(h.t, h.H, g, 9, adj_s);
+    *B1 = event_sum(tt, adj_t) + event_sum(h.t, adj_s);
+    for (int k = 0; k < h.t->len; ++k) pert_s[k] = sgn(adj_s[k]);
+    for (int k = 0; k < tt->len; ++k) pert_t[k] = sgn(adj_t[k]);
+    tape_init(tp, pert_s);
+    aca_chain(tp, s16, Hp);
+    for (int k = 0; k < 9; ++k) Hval[k] = tp->n[Hp[k]].v;
+    tape_init(tp, pert_t);
+    test_chain(tp, Hval, thr, c, Hn, tgt);
+    *dev = tp->n[tgt[0]].v - *E;
+    free(pert_s);
+    free(pert_t);
+    free(adj_s);
+    free(adj_t);
+    free(tp);
+    free(tt);
     hyp_model_free(&h);
 }

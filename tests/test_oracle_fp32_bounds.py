@@ -16,7 +16,16 @@ here against arithmetic other than their own:
    values are the H of the paper's ACA and SKS up to scale;
 3. the inlier test: the host's FP32 test value lies within the bound of the
    exact E = w^2 (r^2 - thr^2) at every point, and every point decided
-   otherwise than by the exact test lies inside the derived band."""
+   otherwise than by the exact test lies inside the derived band;
+4. the bound as a worst case over the set of rounding corners (every event
+   at plus or minus its bound): the chains re-run at the corner the reverse
+   sweep names as the worst land on the first-order bound to within the
+   allowance for products of events, so a wrong partial derivative, a
+   dropped path or a bound scaled up fails; and, for the inlier test at an
+   exact FP32 H, an exhaustive enumeration of all 2^17 corners of its own
+   17 rounding events, in an evaluation written out here, never exceeds the
+   bound and comes within a few percent of it, so a dropped event or a bound
+   too narrow or too wide fails."""
 import ctypes
 import os
 import shutil
@@ -307,3 +316,95 @@ def test_band_in_pixels_near_the_threshold():
     med = float(np.median(px))
     print(f"band near the threshold: median {med:.2e} px, p99 {np.quantile(px, 0.99):.2e} px")
     assert 1e-5 < med < 1e-3
+
+
+# ------------------------------------------------- the worst rounding corner
+def _config0_sets(n):
+    ms = workloads.minimal_sets(n, seed=0)
+    return ms.pts
+
+
+@pytest.mark.parametrize("solver", ["aca", "sks"])
+def test_chain_bound_is_attained_at_its_worst_corner(solver):
+    # F = sum g_i H_i for random g: re-running the chain with every event at
+    # the sign of its weight times its bound moves F by the first-order bound
+    # b1, up to the products of events (at most bound - b1); never beyond
+    pts = _config0_sets(384)
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for i in range(pts.shape[1]):
+        b1, dev, bound = oracle.fp32_chain_corner(solver, pts[:, i], rng.standard_normal(9))
+        assert abs(dev - b1) <= bound - b1, (i, dev / b1)
+        assert dev <= bound
+        worst = max(worst, abs(dev / b1 - 1))
+    print(f"{solver}: worst corner within {worst:.1e} of the first-order bound")
+
+
+def test_inlier_test_bound_is_attained_at_its_worst_corner():
+    # the test with its hypothesis's solve: the solve's events and then the
+    # test's at the signs of their weights move e by at most the bound B and
+    # by at least 0.9 B (the rest of B is the token and the squares of the
+    # bounds of du, dv, w')
+    rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=0)
+    c = np.ascontiguousarray(rp.corr, np.float32)
+    ratios = []
+    for h in range(48):
+        idx = oracle.sample4(2024, 0, h, 2000)
+        s = np.concatenate([c[idx, :2].astype(np.float64).ravel(), c[idx, 2:].astype(np.float64).ravel()])
+        if oracle.sample_degenerate(s):
+            continue
+        _, B = oracle.score_bound_E(s, c[::40], 3.0)
+        for j, i in enumerate(range(0, 2000, 40)):
+            b1, dev, _ = oracle.score_corner(s, c[i], 3.0)
+            assert abs(dev) <= B[j], (h, i, dev / B[j])
+            ratios.append(dev / B[j])
+    ratios = np.asarray(ratios)
+    print(f"inlier test worst corner / bound: min {ratios.min():.4f}, max {ratios.max():.6f}")
+    assert ratios.min() > 0.9
+
+
+def _test_corners(H, thr, c, d):
+    """The inlier test's FP32 evaluation order (Sec. 6.2 test, threshold
+    folded in) with each of its 17 roundings replaced by a factor (1 + d_k):
+    d (17, m) holds m corners.  The inputs (H, thr, the point) are exact."""
+    x, y, X, Y = (float(v) for v in c)
+    rt = (1.0 / thr) * (1 + d[0])
+    Xs, Ys = X * rt * (1 + d[1]), Y * rt * (1 + d[2])
+    G6, G7, G8 = thr * H[6] * (1 + d[3]), thr * H[7] * (1 + d[4]), thr * H[8] * (1 + d[5])
+    w = (G6 * x + (G7 * y + G8) * (1 + d[6])) * (1 + d[7])
+    nu = (-H[0] * x + (-H[1] * y - H[2]) * (1 + d[8])) * (1 + d[9])
+    nv = (-H[3] * x + (-H[4] * y - H[5]) * (1 + d[10])) * (1 + d[11])
+    du, dv = (Xs * w + nu) * (1 + d[12]), (Ys * w + nv) * (1 + d[13])
+    p = (w * -w) * (1 + d[14])
+    return (du * du + (dv * dv + p) * (1 + d[15])) * (1 + d[16])
+
+
+def test_inlier_test_bound_covers_every_corner_of_its_own_events():
+    k = 17
+    bits = (np.arange(1 << k)[None, :] >> np.arange(k)[:, None]) & 1
+    d = (2.0 * bits - 1.0) * U                       # all 2^17 corners, (17, 2^17)
+    zero = np.zeros((k, 1))
+    rp = workloads.ransac_problem(2000, 0.6, 1.0, seed=0)
+    c = np.ascontiguousarray(rp.corr, np.float32)
+    x, y = c[:, 0].astype(np.float64), c[:, 1].astype(np.float64)
+    near, other = [], []
+    for h in range(8):
+        idx = oracle.sample4(2024, 0, h, 2000)
+        s = np.concatenate([c[idx, :2].astype(np.float64).ravel(), c[idx, 2:].astype(np.float64).ravel()])
+        if oracle.sample_degenerate(s):
+            continue
+        H = oracle.aca(s.reshape(16, 1))[0]
+        H = (H / np.abs(H).max()).astype(np.float32).astype(np.float64)       # an exact FP32 H
+        _, B = oracle.score_bound_E_fixed(H, c, 3.0)
+        w = H[6] * x + H[7] * y + H[8]
+        r = np.hypot(c[:, 2] - (H[0] * x + H[1] * y + H[2]) / w, c[:, 3] - (H[3] * x + H[4] * y + H[5]) / w)
+        order = np.argsort(np.abs(r - 3.0))
+        rest = np.random.default_rng(h).choice(2000, 12, replace=False)
+        for j, i in enumerate(list(order[:12]) + list(rest)):
+            E = _test_corners(H, 3.0, c[i], zero)[0]
+            m = float(np.max(np.abs(_test_corners(H, 3.0, c[i], d) - E)))
+            assert m <= B[i], (h, i, m / B[i])
+            (near if j < 12 else other).append(m / B[i])
+    print(f"all corners / bound: near the threshold min {min(near):.4f}, elsewhere min {min(other):.4f}, "
+          f"max {max(near + other):.7f}")
+    assert min(near + other) > 0.9
