@@ -20,8 +20,10 @@ ambiguity band of the RANSAC counts follow.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (exact agreement with an independent DLT, invariants, special cases, cuRAND's
-Philox, brute-force enumeration; the bounds against exact rational arithmetic
-and an FP32 host evaluation).  None is "parity unpinned".
+Philox, brute-force enumeration; the bounds against exact rational arithmetic,
+an FP32 host evaluation and their worst rounding corners).  None is "parity
+unpinned", and tests/test_oracle_mutations.py checks that planted mistakes
+fail the pins.
 """
 from __future__ import annotations
 

@@ -309,8 +309,8 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 //   in K it only enters as a term.  The quantities of each side are first
 //   scaled by one power of two (exact) so that f_S lies in [1, 2): H_K is
 //   invariant under it and the products stay far from overflow;
-//   H = H_S2^-1 K H_S1 (Eq. 14) composed in the M frames in double-float,
-//   rounded once per entry, then translated back in FP32.
+//   H = H_S2^-1 K H_S1 (Eq. 14) composed in the M frames in FP32 (the
+//   local map's two zero entries not formed), then translated back in FP32.
 // Differences are exact (TwoSum) and dot / cross products of them carry
 // their remainders.
 // ---------------------------------------------------------------------------
