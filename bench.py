@@ -619,7 +619,7 @@ def row_sks(torch, _lib, pts, H, flags, n, reps, stream, ctx):
         sks()
     t = time_region(torch, sks, reps, stream)
     out["sks_solve"] = {"value": n / (t * 1e-3), "unit": "H/s", "ms": t,
-                        "roofline": roofline_hbm("sks_solve", BYTES_PER_SET * n, t, ctx, "solve_vec4_kernel<SKS>"),
+                        "roofline": roofline_hbm("sks_solve", BYTES_PER_SET * n, t, ctx, "solve_ring_kernel<SKS>"),
                         "cpu_baseline": cpu_rate(lambda: oracle.lib().oracle_sks(aos.ctypes.data_as(oracle._d),
                                                                                    buf.ctypes.data_as(oracle._d), chunk),
                                                  chunk, ctx["cpu_s"], "H/s",

@@ -84,9 +84,12 @@ aca_status aca_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int6
 /*
  * sks_solve - batched SKS minimal solve (Sec. 3, Eq. 4-14: two similarities
  * from the anchor pair M, N, a 4-parameter kernel H_K from P and Q).  Same
- * layout, flags and normalisations as aca_solve.  SKS divides (by P3.y,
- * Q3.y and Q7.x^2 - Q7.y^2): sets with M, N and P or Q collinear, or with
- * P, Q and M or N collinear, give non-finite H (flag bit ACA_FLAG_NON_FINITE).
+ * layout, flags and normalisations as aca_solve.  The paper's SKS divides
+ * by P3.y, Q3.y and Q7.x^2 - Q7.y^2; the library evaluates Eq. 11-13 over
+ * their common denominator without a division, so a set where one of them
+ * vanishes (M, N and P or Q collinear, or P, Q and M or N collinear, on
+ * either side) gives a finite but degenerate H.  Such sets are near
+ * collinear triples, which the flag bits report as for aca_solve.
  */
 aca_status sks_solve(const float *pts, float *H, uint8_t *flags, int64_t n, int64_t ld, int32_t norm,
                      void *stream);

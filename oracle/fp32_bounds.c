@@ -51,9 +51,10 @@
  * (t1 as cross(N1P1, N1Q1)) each from exact differences, the core of
  * Eq. 28-29 and the local-frame product of Eq. 24 in double-float rounded
  * once per entry, the translation back in FP32; SKS (Eq. 4-14) with exact
- * differences, the similarity images P3, Q3 as compensated dot and cross
- * products, each side scaled by a power of two, the division-free form of
- * Eq. 11-13 over their common denominator, the composition of
+ * differences, the similarity images P3, Q3, f_S and cross(ON, QP) as
+ * double-float dot and cross products, n7, n8 of Eq. 10-11 formed from them
+ * and rounded once, each side scaled by a power of two, the division-free
+ * form of Eq. 11-13 over their common denominator, the composition of
  * Eq. 14 in the M frames in FP32 (the local map's zero entries not formed)
  * and the translation back in FP32; the inlier test in its threshold-folded
  * form.  A bound that fails
@@ -226,6 +227,21 @@ static int cross_x(tape *t, int ux, int uy, int vx, int vy)
     dep(t, k, vx, -V(uy));
     return k;
 }
+/* ux vy - uy vx of exact differences (value + remainder) as a double-float:
+ * the exact products of the values, their difference by TwoSum, plus the
+ * remainder products; only the low part is rounded, at the level of u^2
+ * times the products' magnitude */
+static int cross_df(tape *t, int ux, int uy, int vx, int vy)
+{
+    const double A = fabs(V(ux) * V(vy)) + fabs(V(uy) * V(vx));
+    const double v = V(ux) * V(vy) - V(uy) * V(vx);
+    const int k = push(t, v, A, 16.0 * U * A);
+    dep(t, k, ux, V(vy));
+    dep(t, k, vy, V(ux));
+    dep(t, k, uy, -V(vx));
+    dep(t, k, vx, -V(uy));
+    return k;
+}
 /* double-float steps: exact value, event of size 16 u m with m the
  * magnitude accumulated within the double-float chain (an FP32 operand
  * enters it with m = |value|) */
@@ -383,7 +399,8 @@ static void aca_chain(tape *t, const double *s, int H[9])
 typedef struct {
     int onx, ony;        /* ON = MN / 2, exact (value + remainder) */
     int fS_df, fS;       /* |ON|^2: double-float, and rounded */
-    int P3x, P3y, Q3x, Q3y, cQP;
+    int P3x_df, P3y_df, Q3x_df, Q3y_df, cQP_df;   /* double-float */
+    int P3x, P3y, Q3y;   /* rounded once */
 } sks_side_t;
 
 static void sks_side(tape *t, int Mx, int My, int Nx, int Ny, int Px, int Py, int Qx, int Qy, sks_side_t *o)
@@ -393,12 +410,15 @@ static void sks_side(tape *t, int Mx, int My, int Nx, int Ny, int Px, int Py, in
     const int mpx = xsub(t, Px, Mx), mpy = xsub(t, Py, My), mqx = xsub(t, Qx, Mx), mqy = xsub(t, Qy, My);
     const int qpx = xsub(t, Px, Qx), qpy = xsub(t, Py, Qy);
     o->fS_df = dot_x(t, o->onx, o->ony, o->onx, o->ony);
+    o->P3y_df = cross_df(t, o->onx, o->ony, mpx, mpy);
+    o->Q3y_df = cross_df(t, o->onx, o->ony, mqx, mqy);
+    o->P3x_df = dfsub(t, dot_x(t, o->onx, o->ony, mpx, mpy), o->fS_df);
+    o->Q3x_df = dfsub(t, dot_x(t, o->onx, o->ony, mqx, mqy), o->fS_df);
+    o->cQP_df = cross_df(t, o->onx, o->ony, qpx, qpy);
     o->fS = rn(t, o->fS_df);
-    o->P3y = cross_x(t, o->onx, o->ony, mpx, mpy);
-    o->Q3y = cross_x(t, o->onx, o->ony, mqx, mqy);
-    o->P3x = rn(t, dfsub(t, dot_x(t, o->onx, o->ony, mpx, mpy), o->fS_df));
-    o->Q3x = rn(t, dfsub(t, dot_x(t, o->onx, o->ony, mqx, mqy), o->fS_df));
-    o->cQP = cross_x(t, o->onx, o->ony, qpx, qpy);
+    o->P3x = rn(t, o->P3x_df);
+    o->P3y = rn(t, o->P3y_df);
+    o->Q3y = rn(t, o->Q3y_df);
 }
 
 static void sks_chain(tape *t, const double *s, int H[9])
@@ -408,16 +428,21 @@ static void sks_chain(tape *t, const double *s, int H[9])
     sks_side_t a, b;
     sks_side(t, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], &a);
     sks_side(t, x[8], x[9], x[10], x[11], x[12], x[13], x[14], x[15], &b);
-    /* each side's P3, Q3, f_S, cross(ON, QP) scaled by the power of two
-     * that brings f_S (as rounded to FP32) into [1, 2) (exact) */
+    /* each side's rounded P3, Q3, f_S scaled by the power of two k that
+     * brings f_S (as rounded to FP32) into [1, 2) (exact) */
     const double ka = pow2_inv((float)V(a.fS)), kb = pow2_inv((float)V(b.fS));
-    const int aP3x = xscale(t, a.P3x, ka), aP3y = xscale(t, a.P3y, ka), aQ3x = xscale(t, a.Q3x, ka);
-    const int aQ3y = xscale(t, a.Q3y, ka), afS = xscale(t, a.fS, ka), acQP = xscale(t, a.cQP, ka);
-    const int bP3x = xscale(t, b.P3x, kb), bP3y = xscale(t, b.P3y, kb), bQ3x = xscale(t, b.Q3x, kb);
-    const int bQ3y = xscale(t, b.Q3y, kb), bfS = xscale(t, b.fS, kb), bcQP = xscale(t, b.cQP, kb);
-    /* Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11) */
-    const int n7x = det2(t, aQ3x, aP3x, aQ3y, aP3y), n7y = mul(t, afS, acQP);
-    const int n8x = det2(t, bQ3x, bP3x, bQ3y, bP3y), n8y = mul(t, bfS, bcQP);
+    const int aP3x = xscale(t, a.P3x, ka), aP3y = xscale(t, a.P3y, ka);
+    const int aQ3y = xscale(t, a.Q3y, ka), afS = xscale(t, a.fS, ka);
+    const int bP3x = xscale(t, b.P3x, kb), bP3y = xscale(t, b.P3y, kb);
+    const int bQ3y = xscale(t, b.Q3y, kb), bfS = xscale(t, b.fS, kb);
+    /* Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11) from the
+     * double-float sides: Kahan's determinant of the leading parts plus the
+     * low parts' first-order terms (the cross-product rule), and a
+     * double-float product rounded once; then scaled by k^2 (exact) */
+    const int n7x = xscale(t, cross_x(t, a.Q3x_df, a.P3x_df, a.Q3y_df, a.P3y_df), ka * ka);
+    const int n8x = xscale(t, cross_x(t, b.Q3x_df, b.P3x_df, b.Q3y_df, b.P3y_df), kb * kb);
+    const int n7y = xscale(t, rn(t, dfmul(t, a.fS_df, a.cQP_df)), ka * ka);
+    const int n8y = xscale(t, rn(t, dfmul(t, b.fS_df, b.cQP_df)), kb * kb);
     /* Eq. 11 and Eq. 13 over the common denominator Q4.y P4.y m */
     const int A = det2(t, n8x, n8y, n7y, n7x), B = det2(t, n8y, n8x, n7y, n7x);
     const int m = mul(t, sub(t, n7x, n7y), add(t, n7x, n7y));

@@ -306,9 +306,14 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 //   the same H up to scale without a single division.  m, the determinant
 //   of Eq. 11, vanishes where the SKS parameterisation (not the map) is
 //   singular; dividing by it there amplified the rounding of P3, Q3, while
-//   in K it only enters as a term.  The quantities of each side are first
-//   scaled by one power of two (exact) so that f_S lies in [1, 2): H_K is
-//   invariant under it and the products stay far from overflow;
+//   in K it only enters as a term.  P3, Q3, f_S and ON x QP are kept as
+//   double-floats, and n7, n8 are formed from them and rounded once: where
+//   Q7 and Q8 are nearly parallel, B cancels to a small part of its terms
+//   and magnifies the rounding of its inputs (on the set of the 4096-set
+//   test workload where this is worst, 1.99e-4 of |H| with FP32 sides,
+//   7.5e-5 with these).  The quantities of each side are scaled by one
+//   power of two k (exact), n7 and n8 by k^2, so that f_S lies in [1, 2):
+//   H_K is invariant under it and the products stay far from overflow;
 //   H = H_S2^-1 K H_S1 (Eq. 14) composed in the M frames in FP32 (the
 //   local map's two zero entries not formed), then translated back in FP32.
 // Differences are exact (TwoSum) and dot / cross products of them carry
@@ -317,9 +322,10 @@ ACA_HD uint8_t aca_flags(const Set &s, const AcaParts &p, const float H[9])
 template <class V>
 struct SksSide {
     DiffT<V> onx, ony;       // ON = M N / 2
-    V fS;                    // |ON|^2
-    V P3x, P3y, Q3x, Q3y;
-    V cQP;                   // ON x Q P (= P3.y - Q3.y)
+    DFT<V> fS2;              // |ON|^2
+    DFT<V> P3x2, P3y2, Q3x2, Q3y2;
+    DFT<V> cQP2;             // ON x Q P (= P3.y - Q3.y)
+    V fS, P3x, P3y, Q3y;     // the same, rounded once
 };
 
 template <class V>
@@ -330,13 +336,16 @@ ACA_HD void sks_side(V Mx, V My, V Nx, V Ny, V Px, V Py, V Qx, V Qy, SksSide<V> 
     const DiffT<V> mpx = diff(Px, Mx), mpy = diff(Py, My);
     const DiffT<V> mqx = diff(Qx, Mx), mqy = diff(Qy, My);
     const DiffT<V> qpx = diff(Px, Qx), qpy = diff(Py, Qy);
-    const DFT<V> fS = dot2x_df(o.onx, o.ony, o.onx, o.ony);
-    o.fS = df_round(fS);
-    o.P3y = cross2x(o.onx, o.ony, mpx, mpy);
-    o.Q3y = cross2x(o.onx, o.ony, mqx, mqy);
-    o.P3x = df_round(df_sub(dot2x_df(o.onx, o.ony, mpx, mpy), fS));
-    o.Q3x = df_round(df_sub(dot2x_df(o.onx, o.ony, mqx, mqy), fS));
-    o.cQP = cross2x(o.onx, o.ony, qpx, qpy);
+    o.fS2 = dot2x_df(o.onx, o.ony, o.onx, o.ony);
+    o.P3y2 = cross2x_df(o.onx, o.ony, mpx, mpy);
+    o.Q3y2 = cross2x_df(o.onx, o.ony, mqx, mqy);
+    o.P3x2 = df_sub(dot2x_df(o.onx, o.ony, mpx, mpy), o.fS2);
+    o.Q3x2 = df_sub(dot2x_df(o.onx, o.ony, mqx, mqy), o.fS2);
+    o.cQP2 = cross2x_df(o.onx, o.ony, qpx, qpy);
+    o.fS = df_round(o.fS2);
+    o.P3x = df_round(o.P3x2);
+    o.P3y = df_round(o.P3y2);
+    o.Q3y = df_round(o.Q3y2);
 }
 
 template <class V>
@@ -345,16 +354,17 @@ ACA_HD void sks_solve(const SetT<V> &s, V H[9])
     SksSide<V> a, b;
     sks_side(s.M1x, s.M1y, s.N1x, s.N1y, s.P1x, s.P1y, s.Q1x, s.Q1y, a);
     sks_side(s.M2x, s.M2y, s.N2x, s.N2y, s.P2x, s.P2y, s.Q2x, s.Q2y, b);
-    // each side's P3, Q3, f_S, cross(ON, QP) scaled by one power of two
-    // (H_K is invariant); the unscaled f_S1 stays for H_S1 below
+    // each side's P3, Q3, f_S scaled by one power of two k (H_K is
+    // invariant); the unscaled f_S1 stays for H_S1 below
     const V ka = vpow2_inv_scale(a.fS), kb = vpow2_inv_scale(b.fS);
-    const V aP3x = vmul(a.P3x, ka), aP3y = vmul(a.P3y, ka), aQ3x = vmul(a.Q3x, ka), aQ3y = vmul(a.Q3y, ka);
-    const V afS = vmul(a.fS, ka), acQP = vmul(a.cQP, ka);
-    const V bP3x = vmul(b.P3x, kb), bP3y = vmul(b.P3y, kb), bQ3x = vmul(b.Q3x, kb), bQ3y = vmul(b.Q3y, kb);
-    const V bfS = vmul(b.fS, kb), bcQP = vmul(b.cQP, kb);
-    // Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11)
-    const V n7x = det2(aQ3x, aP3x, aQ3y, aP3y), n7y = vmul(afS, acQP);
-    const V n8x = det2(bQ3x, bP3x, bQ3y, bP3y), n8y = vmul(bfS, bcQP);
+    const V ka2 = vmul(ka, ka), kb2 = vmul(kb, kb);
+    const V aP3x = vmul(a.P3x, ka), aP3y = vmul(a.P3y, ka), aQ3y = vmul(a.Q3y, ka), afS = vmul(a.fS, ka);
+    const V bP3x = vmul(b.P3x, kb), bP3y = vmul(b.P3y, kb), bQ3y = vmul(b.Q3y, kb), bfS = vmul(b.fS, kb);
+    // Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11), of degree 2
+    // in a side's quantities: each formed from the double-float sides,
+    // rounded once, then scaled by k^2 (exact)
+    const V n7x = vmul(det2_df(a.Q3x2, a.P3x2, a.Q3y2, a.P3y2), ka2), n7y = vmul(df_mul_round(a.fS2, a.cQP2), ka2);
+    const V n8x = vmul(det2_df(b.Q3x2, b.P3x2, b.Q3y2, b.P3y2), kb2), n8y = vmul(df_mul_round(b.fS2, b.cQP2), kb2);
     // Eq. 11 and Eq. 13 over the common denominator Q4.y P4.y m
     const V A = det2(n8x, n8y, n7y, n7x), B = det2(n8y, n8x, n7y, n7x);
     const V m = vmul(vsub(n7x, n7y), vadd(n7x, n7y));

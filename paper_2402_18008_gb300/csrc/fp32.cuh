@@ -225,6 +225,41 @@ ACA_HD DFT<V> dot2x_df(DiffT<V> ux, DiffT<V> uy, DiffT<V> vx, DiffT<V> vy)
     return DFT<V>{s.h, vadd(s.l, c)};
 }
 
+// cross(u, v) of two exact differences as a double-float: the exact
+// products of the leading parts, their difference by TwoSum, plus the
+// first-order remainder terms (what cross2x rounds, kept unrounded).
+template <class V>
+ACA_HD DFT<V> cross2x_df(DiffT<V> ux, DiffT<V> uy, DiffT<V> vx, DiffT<V> vy)
+{
+    const DFT<V> s = df_sub(df_prod(ux.h, vy.h), df_prod(uy.h, vx.h));
+    const V nuyh = vneg(uy.h);
+    const V c = vfma(ux.h, vy.l, vfma(ux.l, vy.h, vfma(nuyh, vx.l, vmul(vneg(uy.l), vx.h))));
+    return DFT<V>{s.h, vadd(s.l, c)};
+}
+
+// a*d - b*c of four double-floats, rounded once: Kahan's determinant of the
+// leading parts plus the first-order terms of the low parts.
+template <class V>
+ACA_HD V det2_df(DFT<V> a, DFT<V> b, DFT<V> c, DFT<V> d)
+{
+    const V nbh = vneg(b.h);
+    const V w = vmul(b.h, c.h);
+    const V e = vfma(nbh, c.h, w);
+    const V f = vfma(a.h, d.h, vneg(w));
+    const V r = vfma(a.h, d.l, vfma(a.l, d.h, vfma(nbh, c.l, vmul(vneg(b.l), c.h))));
+    return vadd(f, vadd(e, r));
+}
+
+// x * y of two double-floats, rounded once (TwoProduct of the leading parts
+// plus the first-order terms of the low parts).
+template <class V>
+ACA_HD V df_mul_round(DFT<V> x, DFT<V> y)
+{
+    const V p = vmul(x.h, y.h);
+    const V e = vfma(x.h, y.l, vfma(x.l, y.h, vfma(x.h, y.h, vneg(p))));
+    return vadd(p, e);
+}
+
 template <class V>
 ACA_HD DiffT<V> half(DiffT<V> d)
 {

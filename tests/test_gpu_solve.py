@@ -159,6 +159,7 @@ def test_sks_config0_parity():
     err = unit_aligned_err(planes_to_rows(H, 4096), oracle.sks(ms.pts))
     print(f"sks config0: max {err.max():.3e} median {np.median(err):.3e} >1e-4: {(err > 1e-4).sum()}")
     assert np.median(err) < 1e-6
+    assert err.max() < H_TOL
     bound_gate(err, oracle.sks_fp32_bound(ms.pts), "sks config0")
 
 
