@@ -35,6 +35,10 @@
  *       few u m with m the magnitude accumulated within the double-float
  *       chain, are added with one or two roundings)
  *   rounding a double-float to FP32                    C = |v|
+ *   determinant a d - b c of double-float operands (low part at most 3u
+ *   times the operand's magnitude M), rounded once
+ *                                  C = 2 |v| + 48 u (M(a) M(d) + M(b) M(c))
+ *   product of two such operands, before its rounding  C = 32 u M(a) M(b)
  * Each output gets a token event of 64 u |v|.  The products of two or more
  * events, which the first-order sum neglects, get an allowance of
  * n u / (1 - n u) times the same sum taken over the absolute values of the
@@ -242,6 +246,36 @@ static int cross_df(tape *t, int ux, int uy, int vx, int vy)
     dep(t, k, vx, -V(uy));
     return k;
 }
+/* a d - b c of four double-float operands (value + low part, the low part
+ * at most 3u times the operand's magnitude M, as the dot and cross products
+ * above and their sums leave it), as Kahan's determinant of the values plus
+ * the low parts' first-order terms, rounded once: C = 2 |v| + 48 u S with
+ * S = M(a) M(d) + M(b) M(c) (the dropped low-by-low products are at most
+ * 9 u^2 S, the four low-part products sum to at most 6 u S and take four
+ * roundings, the two final additions add u |v| plus u^2 terms) */
+static int det2_dfin(tape *t, int a, int b, int c, int d)
+{
+    const double S = M(a) * M(d) + M(b) * M(c);
+    const double v = V(a) * V(d) - V(b) * V(c);
+    const int k = push(t, v, fabs(v), 2.0 * fabs(v) + 48.0 * U * S);
+    dep(t, k, a, V(d));
+    dep(t, k, d, V(a));
+    dep(t, k, b, -V(c));
+    dep(t, k, c, -V(b));
+    return k;
+}
+/* the product of two such double-float operands before its rounding:
+ * TwoProduct of the values plus the two first-order low-part products,
+ * C = 32 u m with m = M(a) M(b) (the dropped low-by-low product is at most
+ * 9 u^2 m, the three roundings of the low part at most 18 u^2 m) */
+static int dfmul2(tape *t, int a, int b)
+{
+    const double m = M(a) * M(b);
+    const int k = push(t, V(a) * V(b), m, 32.0 * U * m);
+    dep(t, k, a, V(b));
+    dep(t, k, b, V(a));
+    return k;
+}
 /* double-float steps: exact value, event of size 16 u m with m the
  * magnitude accumulated within the double-float chain (an FP32 operand
  * enters it with m = |value|) */
@@ -436,13 +470,12 @@ static void sks_chain(tape *t, const double *s, int H[9])
     const int bP3x = xscale(t, b.P3x, kb), bP3y = xscale(t, b.P3y, kb);
     const int bQ3y = xscale(t, b.Q3y, kb), bfS = xscale(t, b.fS, kb);
     /* Q7 = (n7x, n7y) / d7, Q8 = (n8x, n8y) / d8 (Eq. 10-11) from the
-     * double-float sides: Kahan's determinant of the leading parts plus the
-     * low parts' first-order terms (the cross-product rule), and a
-     * double-float product rounded once; then scaled by k^2 (exact) */
-    const int n7x = xscale(t, cross_x(t, a.Q3x_df, a.P3x_df, a.Q3y_df, a.P3y_df), ka * ka);
-    const int n8x = xscale(t, cross_x(t, b.Q3x_df, b.P3x_df, b.Q3y_df, b.P3y_df), kb * kb);
-    const int n7y = xscale(t, rn(t, dfmul(t, a.fS_df, a.cQP_df)), ka * ka);
-    const int n8y = xscale(t, rn(t, dfmul(t, b.fS_df, b.cQP_df)), kb * kb);
+     * double-float sides: a determinant of double-floats and a product of
+     * double-floats, each rounded once; then scaled by k^2 (exact) */
+    const int n7x = xscale(t, det2_dfin(t, a.Q3x_df, a.P3x_df, a.Q3y_df, a.P3y_df), ka * ka);
+    const int n8x = xscale(t, det2_dfin(t, b.Q3x_df, b.P3x_df, b.Q3y_df, b.P3y_df), kb * kb);
+    const int n7y = xscale(t, rn(t, dfmul2(t, a.fS_df, a.cQP_df)), ka * ka);
+    const int n8y = xscale(t, rn(t, dfmul2(t, b.fS_df, b.cQP_df)), kb * kb);
     /* Eq. 11 and Eq. 13 over the common denominator Q4.y P4.y m */
     const int A = det2(t, n8x, n8y, n7y, n7x), B = det2(t, n8y, n8x, n7y, n7x);
     const int m = mul(t, sub(t, n7x, n7y), add(t, n7x, n7y));
@@ -815,7 +848,11 @@ void oracle_score_band_px(const double *s16, const float *corr, int64_t N, doubl
  * cross product of the exact differences (a0 - a1, a2 - a3) and
  * (a4 - a5, a6 - a7) (8 operands), 6 = the double-float product
  * (a0 a1) a2 (TwoProduct, then a double-float times FP32 product) rounded
- * once.  *v = exact value, returns the bound on |fl - v|. */
+ * once, 7 and 8 = n7x and n7y of SKS (Eq. 10-11) for one side whose
+ * points M, N, P, Q are (a0, a1) ... (a6, a7): the determinant and the
+ * product of the side's double-floats, rounded once, 9 = the cross product of
+ * op 5 kept as a double-float (its high plus low part against the exact
+ * value).  *v = exact value, returns the bound on |fl - v|. */
 double oracle_fp32_rule_bound(int op, const double *a, double *v)
 {
     tape tt;
@@ -831,6 +868,14 @@ double oracle_fp32_rule_bound(int op, const double *a, double *v)
     case 3: r = dv(t, x[0], x[1]); break;
     case 4: r = det2(t, x[0], x[1], x[2], x[3]); break;
     case 5: r = cross_x(t, xsub(t, x[0], x[1]), xsub(t, x[2], x[3]), xsub(t, x[4], x[5]), xsub(t, x[6], x[7])); break;
+    case 7:
+    case 8: {
+        sks_side_t o;
+        sks_side(t, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], &o);
+        r = op == 7 ? det2_dfin(t, o.Q3x_df, o.P3x_df, o.Q3y_df, o.P3y_df) : rn(t, dfmul2(t, o.fS_df, o.cQP_df));
+        break;
+    }
+    case 9: r = cross_df(t, xsub(t, x[0], x[1]), xsub(t, x[2], x[3]), xsub(t, x[4], x[5]), xsub(t, x[6], x[7])); break;
     default: r = rn(t, dfmul(t, dfmul(t, x[0], x[1]), x[2])); break;
     }
     *v = t->n[r].v;

@@ -107,6 +107,90 @@ def _df_prod_mul_round(a, b, c):
     return rn32(q + ql)
 
 
+def _two_prod(a, b):
+    p = rn32(a * b)
+    return p, rn32(a * b - p)
+
+
+def _df_add(x, y):
+    s = rn32(x[0] + y[0])
+    bv = rn32(s - x[0])
+    av = rn32(s - bv)
+    e = rn32(rn32(x[0] - av) + rn32(y[0] - bv))
+    return s, rn32(e + rn32(x[1] + y[1]))
+
+
+def _cross2x_df(u, v):
+    """cross(u, v) of exact differences kept as a double-float, in the
+    library's order: exact products of the values, their difference by
+    TwoSum, plus the four remainder products."""
+    (uxh, uxl), (uyh, uyl) = u
+    (vxh, vxl), (vyh, vyl) = v
+    a, b = _two_prod(uxh, vyh), _two_prod(uyh, vxh)
+    s = _df_add(a, (-b[0], -b[1]))
+    c = rn32(uxh * vyl + rn32(uxl * vyh + rn32(-uyh * vxl + rn32(-uyl * vxh))))
+    return s[0], rn32(s[1] + c)
+
+
+def _det2_df(a, b, c, d):
+    """a d - b c of four double-floats (value, low part), rounded once, in
+    the library's order: Kahan's determinant of the values plus the low
+    parts' first-order terms."""
+    w = rn32(b[0] * c[0])
+    e = rn32(-b[0] * c[0] + w)
+    f = rn32(a[0] * d[0] - w)
+    r = rn32(a[0] * d[1] + rn32(a[1] * d[0] + rn32(-b[0] * c[1] + rn32(-b[1] * c[0]))))
+    return rn32(f + rn32(e + r))
+
+
+def _df_mul_round(x, y):
+    p = rn32(x[0] * y[0])
+    e = rn32(x[0] * y[1] + rn32(x[1] * y[0] + rn32(x[0] * y[0] - p)))
+    return rn32(p + e)
+
+
+def _dot2x_df(u, v):
+    """u . v of exact differences as a double-float, in the library's order."""
+    (uxh, uxl), (uyh, uyl) = u
+    (vxh, vxl), (vyh, vyl) = v
+    s = _df_add(_two_prod(uxh, vxh), _two_prod(uyh, vyh))
+    c = rn32(uxh * vxl + rn32(uxl * vxh + rn32(uyh * vyl + rn32(uyl * vyh))))
+    return s[0], rn32(s[1] + c)
+
+
+def _sks_side(M, N, P, Q):
+    """One side of the SKS kernel up to n7x, n7y (Eq. 6-11), in the library's
+    order: ON = MN / 2 and the edges as exact differences, f_S, P3, Q3 and
+    cross(ON, QP) as double-floats, then n7x as a determinant and n7y as a
+    product of double-floats, each rounded once."""
+    half = Fr(1, 2)
+    onx = tuple(half * x for x in _diff(N[0], M[0]))
+    ony = tuple(half * x for x in _diff(N[1], M[1]))
+    on = (onx, ony)
+    mp = (_diff(P[0], M[0]), _diff(P[1], M[1]))
+    mq = (_diff(Q[0], M[0]), _diff(Q[1], M[1]))
+    qp = (_diff(P[0], Q[0]), _diff(P[1], Q[1]))
+    fS = _dot2x_df(on, on)
+    P3y, Q3y = _cross2x_df(on, mp), _cross2x_df(on, mq)
+    d = _dot2x_df(on, mp)
+    P3x = _df_add(d, (-fS[0], -fS[1]))
+    d = _dot2x_df(on, mq)
+    Q3x = _df_add(d, (-fS[0], -fS[1]))
+    cQP = _cross2x_df(on, qp)
+    return _det2_df(Q3x, P3x, Q3y, P3y), _df_mul_round(fS, cQP)
+
+
+def _side_points(rng, i):
+    p = _f32(rng, 8, 0, 640)
+    if i % 3 == 1:        # P close to the line MN: P3.y small against its terms
+        t = rng.uniform(-1, 2)
+        q = p[0:2] + t * (p[2:4] - p[0:2])
+        p[4:6] = (q + rng.uniform(-0.5, 0.5, 2)).astype(np.float32)
+    if i % 3 == 2:        # P and Q nearly aligned with ON's normal: n7x cancels
+        p[6:8] = (p[4:6] + rng.uniform(-1, 1, 2) * 1e-2 * (p[2:4] - p[0:2])).astype(np.float32)
+    return p
+
+
 def _f32(rng, n, lo=-700.0, hi=700.0):
     return rng.uniform(lo, hi, n).astype(np.float32)
 
@@ -170,6 +254,52 @@ def test_double_float_product_within_its_rule():
     for _ in range(400):
         a, b, c = _f32(rng, 3, -3e3, 3e3)
         _check_rule(6, [a, b, c], _df_prod_mul_round(Fr(float(a)), Fr(float(b)), Fr(float(c))))
+
+
+def _rule_on_df(op, pairs, emulated):
+    v, b = oracle.fp32_rule_bound(op, [float(x) for p in pairs for x in p])
+    assert abs(float(emulated) - v) <= b * (1 + 1e-12) + 1e-300, (op, pairs, float(emulated), v, b)
+    return abs(float(emulated) - v) / b if b > 0 else 0.0
+
+
+def test_sks_n7_of_double_float_sides_within_their_rules():
+    # n7x = Q3.x P3.y - P3.x Q3.y and n7y = f_S cross(ON, QP) of one side,
+    # formed in the library's order from the double-float sides, on random
+    # and cancellation-heavy point sets
+    rng = np.random.default_rng(7)
+    worst = [0.0, 0.0]
+    for i in range(900):
+        p = _side_points(rng, i)
+        F = [Fr(float(x)) for x in p]
+        n7x, n7y = _sks_side((F[0], F[1]), (F[2], F[3]), (F[4], F[5]), (F[6], F[7]))
+        for k, (op, got) in enumerate(((7, n7x), (8, n7y))):
+            v, b = oracle.fp32_rule_bound(op, p)
+            if v == 0:
+                continue
+            assert abs(float(got) - v) <= b * (1 + 1e-12), (i, op, float(got), v, b)
+            worst[k] = max(worst[k], abs(float(got) - v) / b)
+    print(f"n7x worst error / bound {worst[0]:.3f}, n7y {worst[1]:.3f}")
+    assert min(worst) > 0.1
+
+
+def test_cross_product_kept_as_a_double_float_within_its_rule():
+    # P3.y, Q3.y, cross(ON, QP) of the SKS kernel: the pair's value against
+    # the exact cross product of the exact differences
+    rng = np.random.default_rng(9)
+    for i in range(600):
+        p = _f32(rng, 6, 0, 640)
+        if i % 2 == 0:
+            t = rng.uniform(-2, 2)
+            n = np.array([-(p[3] - p[1]), p[2] - p[0]], np.float64)
+            n /= np.linalg.norm(n)
+            q = p[:2] + t * (p[2:4] - p[:2]) + n * rng.uniform(-1e-2, 1e-2)
+            p[4:6] = q.astype(np.float32)
+        M, N, P = (Fr(float(p[0])), Fr(float(p[1]))), (Fr(float(p[2])), Fr(float(p[3]))), (Fr(float(p[4])), Fr(float(p[5])))
+        u = (_diff(N[0], M[0]), _diff(N[1], M[1]))
+        w = (_diff(P[0], M[0]), _diff(P[1], M[1]))
+        h, lo = _cross2x_df(u, w)
+        v, b = oracle.fp32_rule_bound(9, [p[2], p[0], p[3], p[1], p[4], p[0], p[5], p[1]])
+        assert abs(float(h + lo - Fr(v))) <= b * (1 + 1e-12) + 1e-300, (i, float(h + lo), v, b)
 
 
 # ---------------------------------------------------------------- whole chains
