@@ -186,8 +186,10 @@ def _side_points(rng, i):
         t = rng.uniform(-1, 2)
         q = p[0:2] + t * (p[2:4] - p[0:2])
         p[4:6] = (q + rng.uniform(-0.5, 0.5, 2)).astype(np.float32)
-    if i % 3 == 2:        # P and Q nearly aligned with ON's normal: n7x cancels
-        p[6:8] = (p[4:6] + rng.uniform(-1, 1, 2) * 1e-2 * (p[2:4] - p[0:2])).astype(np.float32)
+    if i % 3 == 2:        # Q close to the line through O (the midpoint of MN) and P: P3, Q3
+        o = 0.5 * (p[0:2].astype(np.float64) + p[2:4])      # nearly parallel, n7x cancels
+        q = o + rng.uniform(0.3, 2.0) * (p[4:6] - o)
+        p[6:8] = (q + rng.uniform(-1e-3, 1e-3, 2)).astype(np.float32)
     return p
 
 
