@@ -378,9 +378,9 @@ ACA_HD void sks_solve(const SetT<V> &s, V H[9])
     const V o1x = a.onx.h, o1y = a.ony.h, o2x = b.onx.h, o2y = b.ony.h;
     // K R1 (rows); row 1 of K R1 is dK (-o1y, o1x, 0).  The composition is
     // plain FP32: carried in double-float it changed no aggregate of the
-    // error against the FP64 oracle (config 0: max 1.97e-4 against 1.99e-4,
-    // one set above 1e-4 either way; 2^18 sets: the same 56 above 1e-4, max
-    // 1.87e-3 against 1.86e-3), whose size comes from the sides and the kernel.
+    // error against the FP64 oracle (measured with FP32 sides: config 0 max
+    // 1.97e-4 against 1.99e-4; 2^18 sets: the same 56 above 1e-4, max 1.87e-3
+    // against 1.86e-3), whose size comes from the sides and the kernel.
     const V A00 = vfma(aK, o1x, vneg(vmul(uK, o1y)));
     const V A01 = vfma(aK, o1y, vmul(uK, o1x));
     const V A20 = vfma(bK, o1x, vneg(vmul(vK, o1y)));
