@@ -134,6 +134,30 @@ def _need(t, name, dtype, rows=None, host_ok=False):
             raise ValueError(f"{name} must be ({rows}, ld) with unit stride along ld")
 
 
+def _planes(t, name, dtype, rows, host_ok=False):
+    """_need for a (rows, ld) plane tensor, reading its shape and strides
+    once: returns (row length, leading dimension)."""
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise ValueError(f"{name} must be a CUDA tensor" + (" or a pinned host tensor" if host_ok else ""))
+    if t.dtype is not dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    sh, st = t.shape, t.stride()
+    if len(sh) != 2 or sh[0] != rows or st[1] != 1:
+        raise ValueError(f"{name} must be ({rows}, ld) with unit stride along ld")
+    return sh[1], st[0]
+
+
+def _shared_ld(*cols_lds):
+    """The leading dimension that (row length, ld) pairs share."""
+    ld = cols_lds[0][1]
+    for cols, l in cols_lds:
+        if l != ld:
+            raise ValueError("all planes must share one leading dimension (row stride)")
+        if cols > ld:
+            raise ValueError("row length exceeds the leading dimension")
+    return ld
+
+
 def _ld(*ts):
     ld = None
     for t in ts:
@@ -152,34 +176,37 @@ def _ld(*ts):
 def aca_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
     """C ABI aca_solve on (16, ld) float32 planes -> (9, ld) float32.  Each
     tensor may be on the GPU or in pinned host memory (zero-copy)."""
-    _need(pts, "pts", torch.float32, 16, host_ok=True)
-    _need(H, "H", torch.float32, 9, host_ok=True)
+    p = _planes(pts, "pts", _F32, 16, host_ok=True)
+    ld = _shared_ld(p, _planes(H, "H", _F32, 9, host_ok=True))
     if flags is not None:
         _need(flags, "flags", torch.uint8, host_ok=True)
-    ld = _ld(pts, H)
-    n = pts.shape[1] if n is None else n
-    _check(_L().aca_solve(pts.data_ptr(), H.data_ptr(), _ptr(flags), n, ld, norm, _stream(stream, pts)))
+    r = _L().aca_solve(pts.data_ptr(), H.data_ptr(), _ptr(flags), p[0] if n is None else n, ld, norm,
+                       _stream(stream, pts))
+    if r:
+        _check(r)
 
 
 def sks_solve(pts, H, flags=None, n=None, norm=ACA_NORM_NONE, stream=None):
     """C ABI sks_solve on (16, ld) float32 planes -> (9, ld) float32."""
-    _need(pts, "pts", torch.float32, 16)
-    _need(H, "H", torch.float32, 9)
+    p = _planes(pts, "pts", _F32, 16)
+    ld = _shared_ld(p, _planes(H, "H", _F32, 9))
     if flags is not None:
         _need(flags, "flags", torch.uint8)
-    ld = _ld(pts, H)
-    n = pts.shape[1] if n is None else n
-    _check(_L().sks_solve(pts.data_ptr(), H.data_ptr(), _ptr(flags), n, ld, norm, _stream(stream, pts)))
+    r = _L().sks_solve(pts.data_ptr(), H.data_ptr(), _ptr(flags), p[0] if n is None else n, ld, norm,
+                       _stream(stream, pts))
+    if r:
+        _check(r)
 
 
 def aca_rect_solve(tgt, rect, H, n=None, stream=None):
     """C ABI aca_rect_solve: rect = (x0, y0, w, r)."""
-    _need(tgt, "tgt", torch.float32, 8)
-    _need(H, "H", torch.float32, 9)
-    ld = _ld(tgt, H)
-    n = tgt.shape[1] if n is None else n
+    p = _planes(tgt, "tgt", _F32, 8)
+    ld = _shared_ld(p, _planes(H, "H", _F32, 9))
     x0, y0, w, r = (float(v) for v in rect)
-    _check(_L().aca_rect_solve(tgt.data_ptr(), x0, y0, w, r, H.data_ptr(), n, ld, _stream(stream, tgt)))
+    st = _L().aca_rect_solve(tgt.data_ptr(), x0, y0, w, r, H.data_ptr(), p[0] if n is None else n, ld,
+                             _stream(stream, tgt))
+    if st:
+        _check(st)
 
 
 def aca_affine_solve(pts, H, n=None, norm=ACA_NORM_NONE, stream=None):
@@ -193,24 +220,23 @@ def aca_affine_solve(pts, H, n=None, norm=ACA_NORM_NONE, stream=None):
 
 def aca_backward(pts, grad_H, grad_tgt, n=None, stream=None):
     """C ABI aca_backward: (16, ld) sets, (9, ld) dL/dH -> (8, ld) dL/dtgt."""
-    _need(pts, "pts", torch.float32, 16)
-    _need(grad_H, "grad_H", torch.float32, 9)
-    _need(grad_tgt, "grad_tgt", torch.float32, 8)
-    ld = _ld(pts, grad_H, grad_tgt)
-    n = pts.shape[1] if n is None else n
-    _check(_L().aca_backward(pts.data_ptr(), grad_H.data_ptr(), grad_tgt.data_ptr(), n, ld, _stream(stream, pts)))
+    p = _planes(pts, "pts", _F32, 16)
+    ld = _shared_ld(p, _planes(grad_H, "grad_H", _F32, 9), _planes(grad_tgt, "grad_tgt", _F32, 8))
+    r = _L().aca_backward(pts.data_ptr(), grad_H.data_ptr(), grad_tgt.data_ptr(), p[0] if n is None else n, ld,
+                          _stream(stream, pts))
+    if r:
+        _check(r)
 
 
 def aca_rect_backward(tgt, rect, grad_H, grad_tgt, n=None, stream=None):
     """C ABI aca_rect_backward."""
-    _need(tgt, "tgt", torch.float32, 8)
-    _need(grad_H, "grad_H", torch.float32, 9)
-    _need(grad_tgt, "grad_tgt", torch.float32, 8)
-    ld = _ld(tgt, grad_H, grad_tgt)
-    n = tgt.shape[1] if n is None else n
+    p = _planes(tgt, "tgt", _F32, 8)
+    ld = _shared_ld(p, _planes(grad_H, "grad_H", _F32, 9), _planes(grad_tgt, "grad_tgt", _F32, 8))
     x0, y0, w, r = (float(v) for v in rect)
-    _check(_L().aca_rect_backward(tgt.data_ptr(), x0, y0, w, r, grad_H.data_ptr(), grad_tgt.data_ptr(), n, ld,
-                                  _stream(stream, tgt)))
+    st = _L().aca_rect_backward(tgt.data_ptr(), x0, y0, w, r, grad_H.data_ptr(), grad_tgt.data_ptr(),
+                                p[0] if n is None else n, ld, _stream(stream, tgt))
+    if st:
+        _check(st)
 
 
 class Prepared:
