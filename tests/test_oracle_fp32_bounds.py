@@ -258,12 +258,6 @@ def test_double_float_product_within_its_rule():
         _check_rule(6, [a, b, c], _df_prod_mul_round(Fr(float(a)), Fr(float(b)), Fr(float(c))))
 
 
-def _rule_on_df(op, pairs, emulated):
-    v, b = oracle.fp32_rule_bound(op, [float(x) for p in pairs for x in p])
-    assert abs(float(emulated) - v) <= b * (1 + 1e-12) + 1e-300, (op, pairs, float(emulated), v, b)
-    return abs(float(emulated) - v) / b if b > 0 else 0.0
-
-
 def test_sks_n7_of_double_float_sides_within_their_rules():
     # n7x = Q3.x P3.y - P3.x Q3.y and n7y = f_S cross(ON, QP) of one side,
     # formed in the library's order from the double-float sides, on random
