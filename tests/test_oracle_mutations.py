@@ -31,6 +31,21 @@ MUTATIONS = [
      "r1[6] = Y * x;", "r1[6] = -Y * x;", "test_oracle_aca.py"),
     ("SKS: Q7.y adds P5.y (Eq. 10)", "oracle.c",
      "Q7y = Q3[2] / Q3[1] - P5y;", "Q7y = Q3[2] / Q3[1] + P5y;", "test_oracle_sks_rect_jac.py"),
+    ("affine: H_A2^-1 with M2N2 and M2P2 exchanged (Eq. 38)", "oracle.c",
+     "mat3_mul(L1, T1, HA1);\n    const double HA2inv[9] = {MN2x, MP2x, M2x, MN2y, MP2y, M2y, 0, 0, 1};\n    mat3_mul(HA2inv, HA1, H);",
+     "mat3_mul(L1, T1, HA1);\n    const double HA2inv[9] = {MP2x, MN2x, M2x, MP2y, MN2y, M2y, 0, 0, 1};\n    mat3_mul(HA2inv, HA1, H);",
+     "test_oracle_aca.py"),
+    ("rectangle: Eq. 42's y0 term without the aspect ratio", "oracle.c",
+     "-r * Q4y * y0, t2", "-Q4y * y0, t2", "test_oracle_sks_rect_jac.py"),
+    ("RANSAC argmax: a tie takes the later hypothesis", "oracle.c",
+     "        for (int32_t h = 0; h < k; ++h)\n            if (cnt[h] > bc) {\n                bc = cnt[h];\n                bh = h;\n            }\n        if (bc < 0) {",
+     "        for (int32_t h = 0; h < k; ++h)\n            if (cnt[h] >= bc) {\n                bc = cnt[h];\n                bh = h;\n            }\n        if (bc < 0) {",
+     "test_oracle_sampling_scoring.py"),
+    ("degenerate samples: the triple (N, P, Q) not tested", "oracle.c",
+     "triple_degenerate(MNx, MNy, MQx, MQy) || triple_degenerate(NPx, NPy, NQx, NQy);",
+     "triple_degenerate(MNx, MNy, MQx, MQy);", "test_oracle_sampling_scoring.py"),
+    ("normalisation: h33 made negative", "oracle.c",
+     "(H[8] > 0 ? 1.0 : -1.0)", "(H[8] > 0 ? -1.0 : 1.0)", "test_oracle_sampling_scoring.py"),
     ("Jacobian: the dual chain's t1 drops Q3.y", "oracle.c",
      "const dual t1 = dsub(dsub(fA1, Q3x), Q3y);", "const dual t1 = dsub(fA1, Q3x);", "test_oracle_sks_rect_jac.py"),
     ("Philox: a key increment off by one", "oracle.c",

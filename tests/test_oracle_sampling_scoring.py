@@ -201,6 +201,37 @@ def test_ambiguity_band_is_the_fixed_band_united_with_the_derived_fp32_band():
     assert np.mean((bi + bo)[c == 300] == 0) > 0.9
 
 
+def test_each_collinear_triple_alone_makes_a_sample_degenerate():
+    # reading 10: a sample is degenerate when, on either side, any of its
+    # triples (M,N,P), (M,Q,P), (M,N,Q), (N,P,Q) has sine of the angle at
+    # its first point at most 1e-3; one triple made collinear at a time
+    ms = workloads.minimal_sets(4, seed=8)
+    base = oracle.sets_aos(ms.pts)
+    for b in base:
+        assert not oracle.sample_degenerate(b)
+        for side in (0, 8):
+            P = {k: b[side + 2 * i: side + 2 * i + 2].copy() for i, k in enumerate("MNPQ")}
+            for moved, a, c in (("P", "M", "N"), ("Q", "M", "P"), ("Q", "M", "N"), ("Q", "N", "P")):
+                t = b.copy()
+                i = "MNPQ".index(moved)
+                t[side + 2 * i: side + 2 * i + 2] = P[a] + 1.7 * (P[c] - P[a])
+                assert oracle.sample_degenerate(t), (side, moved, a, c)
+
+
+def test_degenerate_sample_threshold_is_a_sine_of_1e3():
+    # the angle at M between MN and MP just below and just above sine 1e-3
+    ms = workloads.minimal_sets(1, seed=9)
+    b = oracle.sets_aos(ms.pts)[0]
+    M, N = b[0:2], b[2:4]
+    u = (N - M) / np.linalg.norm(N - M)
+    v = np.array([-u[1], u[0]])
+    assert not oracle.sample_degenerate(b)
+    for sine, expect in ((0.9e-3, True), (1.1e-3, False)):
+        t = b.copy()
+        t[4:6] = M + 200.0 * (np.sqrt(1 - sine * sine) * u + sine * v)
+        assert oracle.sample_degenerate(t) == expect, sine
+
+
 def test_a_sample_with_a_non_finite_coordinate_is_degenerate():
     ms = workloads.minimal_sets(8, seed=3)
     s = oracle.sets_aos(ms.pts)

@@ -82,6 +82,19 @@ def test_rect_alg1_and_eq42_agree_in_fp64():
     assert np.allclose(Ha1, -H42, rtol=1e-12, atol=1e-9 * np.abs(H42).max())
 
 
+def test_oracle_rect_forms_on_rectangles_of_any_aspect_and_offset():
+    # the C oracle's Eq. 42 and Algorithm 1 against its general ACA on
+    # rectangles of every aspect ratio and offset (the 4-point-offset patch
+    # of the differentiable workload is square, where the r and y0 terms of
+    # Eq. 42 would go unseen)
+    for s, (x0, y0, w, r) in _rect_sets(30, 31):
+        tgt = np.array(s[8:], dtype=np.float64).reshape(8, 1)
+        rect = (float(x0), float(y0), float(w), float(r))
+        Hg = _unit(oracle.aca(np.array(s, dtype=np.float64).reshape(16, 1)))
+        assert np.max(np.abs(_unit(oracle.aca_rect(tgt, rect)) - Hg)) < 1e-10, rect
+        assert np.max(np.abs(_unit(oracle.aca_rect_alg1(tgt, rect)) - Hg)) < 1e-10, rect
+
+
 def test_all_24_rectangle_corner_orders_give_the_same_h():
     # Appendix B: a pivot-free elimination fails for 8 of the 24 orders of a
     # rectangle's corners; ACA must give one H for all of them.
