@@ -61,6 +61,10 @@ MUTATIONS = [
      "if (i >= kreq) return i;", "if (i > kreq) return i;", "test_oracle_adaptive.py"),
     ("refit: Hartley scale to mean distance 2, not sqrt(2)", "inlier_refit.py",
      "SQRT2 = np.sqrt(2.0)", "SQRT2 = 2.0", "test_oracle_refit.py"),
+    ("refit: the DLT's second row with the wrong sign of y2 (Eq. 2)", "inlier_refit.py",
+     "A[1:2 * len(x):2, 6:9] = X[:, 1:2] * xh", "A[1:2 * len(x):2, 6:9] = -X[:, 1:2] * xh", "test_oracle_refit.py"),
+    ("refit: a wrong Jacobian entry of the LM residual", "inlier_refit.py",
+     "J[1::2, 6] = -v * x[:, 0] / w", "J[1::2, 6] = -u * x[:, 0] / w", "test_oracle_refit.py"),
     ("bound: the rounding of X / thr left out", "fp32_bounds.c",
      "const int Xs = mul(t, X, rt), Ys = mul(t, Y, rt);", "const int Xs = xscale(t, X, V(rt)), Ys = mul(t, Y, rt);",
      "test_oracle_fp32_bounds.py"),
