@@ -300,10 +300,10 @@ static aca_status launch_solve(const float *pts, float *H, uint8_t *flags, int64
     // threads per SM.  With the flags (~490 instructions) the arithmetic
     // leads and a third block per SM pays (58.8 against 55.1 G sets/s with
     // direct loads).  SKS without flags, division-free and packed, runs best
-    // on the ring with 4 blocks per SM (2^26 sets: 46.98 G sets/s, against
-    // 46.48 at 3 blocks, 45.26 at 2 and 45.55 with direct loads in
-    // 256-thread blocks); with flags it takes its sets one by one on direct
-    // loads.
+    // on a ring grid of 4 blocks per SM, 3 resident (2^26 sets: 60.3 G sets/s
+    // against 59.8 at 3; first measured 46.98 against 46.48 at 3, 45.26 at
+    // 2 and 45.55 with direct loads); with flags it takes its sets one by
+    // one on direct loads.
     constexpr bool kRing = SOLVER == kAca || !FLAGS;
     constexpr int kRingBlocks = SOLVER == kSks ? 4 : (FLAGS ? 3 : kRingBlocksPerSm);
     if (kRing && vec) {
