@@ -55,6 +55,8 @@ MUTATIONS = [
     ("scoring: w takes h13 for h33", "oracle.c",
      "const double w = H[6] * x + H[7] * y + H[8];\n    if (w == 0) {",
      "const double w = H[6] * x + H[7] * y + H[2];\n    if (w == 0) {", "test_oracle_sampling_scoring.py"),
+    ("scoring: the threshold test made strict", "oracle.c",
+     "    return r <= thr;", "    return r < thr;", "test_oracle_sampling_scoring.py"),
     ("adaptive K: w^3 for w^4 (Sec. 6.2)", "oracle.c",
      "const double w4 = (w * w) * (w * w);", "const double w4 = (w * w) * w;", "test_oracle_adaptive.py"),
     ("adaptive stop: one hypothesis past K", "oracle.c",

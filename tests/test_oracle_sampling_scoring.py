@@ -232,6 +232,24 @@ def test_degenerate_sample_threshold_is_a_sine_of_1e3():
         assert oracle.sample_degenerate(t) == expect, sine
 
 
+def test_inlier_test_is_inclusive_at_the_threshold():
+    # reading 11: the oracle's test is ||x2 - pi(H x1)|| <= thr, inclusive.
+    # Seven small integer points moved by an integer translation, and one
+    # point moved 3 px further along x: every hypothesis drawn from four of
+    # the seven is that translation, with integer entries small enough that
+    # FP64 holds every product of the chain exactly, so every residual is
+    # exact; it counts the eighth point at thr = 3 but not a hair below.
+    src = np.array([[1, 2], [17, 3], [4, 15], [19, 12], [9, 8], [14, 18], [2, 11], [12, 1]], dtype=np.float32)
+    dst = src + np.array([5, -2], dtype=np.float32)
+    dst[7, 0] += 3
+    corr = np.ascontiguousarray(np.c_[src, dst], dtype=np.float32)
+    exact = [h for h in range(400) if 7 not in oracle.sample4(5, 0, h, 8)]
+    assert len(exact) > 50
+    for thr, count in ((3.0, 8), (2.999, 7)):
+        c = oracle.ransac(corr, [0, 8], [400], thr, 5, band_px=0.0)["hyp_counts"]
+        assert all(int(c[h]) == count for h in exact), (thr, sorted(set(int(c[h]) for h in exact)))
+
+
 def test_a_sample_with_a_non_finite_coordinate_is_degenerate():
     ms = workloads.minimal_sets(8, seed=3)
     s = oracle.sets_aos(ms.pts)
