@@ -48,6 +48,8 @@ MUTATIONS = [
      "(H[8] > 0 ? 1.0 : -1.0)", "(H[8] > 0 ? -1.0 : 1.0)", "test_oracle_sampling_scoring.py"),
     ("Jacobian: the dual chain's t1 drops Q3.y", "oracle.c",
      "const dual t1 = dsub(dsub(fA1, Q3x), Q3y);", "const dual t1 = dsub(fA1, Q3x);", "test_oracle_sks_rect_jac.py"),
+    ("rectangle Jacobian: the dual chain's y0 term without the aspect ratio", "oracle.c",
+     "dneg(dmul(dmul(R, Q4y), Y0))", "dneg(dmul(Q4y, Y0))", "test_oracle_sks_rect_jac.py"),
     ("Philox: a key increment off by one", "oracle.c",
      "k0 += 0x9E3779B9u;", "k0 += 0x9E3779B8u;", "test_oracle_sampling_scoring.py"),
     ("sampling: a rank steps over strictly smaller earlier draws only", "oracle.c",
