@@ -150,3 +150,12 @@ def test_fma_probe_rejects_bad_arguments_before_launch():
     assert b"steps" in L.aca_last_error()
     assert L.aca_fma_probe(1, 4, 256, 4096, None, None) == -1     # null sink
     assert L.aca_fma_probe_flops(1, 608, 256, 4096) == 608 * 256 * 4096 * 8 * 2 * 2
+
+
+def test_binding_leading_dimension_rules():
+    # the plane bindings' shared leading-dimension check (host logic only)
+    assert _lib._shared_ld((5, 8), (8, 8), (0, 8)) == 8
+    with pytest.raises(ValueError, match="one leading dimension"):
+        _lib._shared_ld((5, 8), (5, 12))
+    with pytest.raises(ValueError, match="exceeds the leading dimension"):
+        _lib._shared_ld((9, 8), (5, 8))
