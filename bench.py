@@ -724,6 +724,22 @@ def row_ransac1(torch, api, rp, stream, dev, ctx, fixed=None):
     for _ in range(5):
         plan2.replay()
     t = time_region(torch, plan2.replay, 200, stream)
+    # eight such RANSACs back to back in one graph, each with its own buffers:
+    # the cost of one more RANSAC once the graph launch is shared
+    plans8 = [make2(**best2) for _ in range(8)]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for p in plans8:
+            p.run()
+    torch.cuda.current_stream().wait_stream(side)
+    g8 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g8):
+        for p in plans8:
+            p.run()
+    for _ in range(3):
+        g8.replay()
+    t8 = time_region(torch, g8.replay, 100, stream)
     tests = 4096 * 2000
     import oracle
     cnt = np.empty(4096, np.int32)
@@ -732,6 +748,7 @@ def row_ransac1(torch, api, rp, stream, dev, ctx, fixed=None):
                                                     cnt.ctypes.data_as(oracle._i32), None, None, 0.0)
     out["ransac_fused_one_pair"] = {
         "value": tests / (t * 1e-3), "unit": "hyp*pts/s", "ms_per_ransac": t,
+        "ms_per_ransac_8_in_one_graph": t8 / 8, "ms_per_added_ransac": (t8 - t) / 7,
         "tflops_fp32": tests * FLOPS_PER_TEST / (t * 1e-3) / 1e12, "tuning": best2,
         "roofline": roofline_alu("ransac_fused_one_pair", tests * FLOPS_PER_TEST, t, ctx, "ransac_fused_kernel",
                                  note="whole RANSAC per graph replay (one launch): sampling, solve, scoring, argmax, "
